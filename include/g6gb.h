@@ -1,0 +1,301 @@
+/*
+ * g6gb.h -- GRAPE-6-style direct-summation force library for GB300 (sm_103a).
+ *
+ * Method: Gaburov, Harfst & Portegies Zwart, "SAPPORO: A way to turn your
+ * graphics cards into a GRAPE-6" (arXiv:0902.4463).  The library evaluates
+ * the data-parallel hot path of a 4th-order Hermite block-time-step N-body
+ * integrator (Sect. 2): it predicts every j-particle to the block time
+ * (Sect. 2.2, Eq. 1 and Eq. 2), then for each active i-particle sums the
+ * softened acceleration, jerk and potential over all j-particles and finds the
+ * nearest neighbour and, optionally, the neighbour list (Sect. 2.3, 2.5, 4).
+ *
+ * Precision (Sect. 2.2, 2.3): bulk pair arithmetic in FP32; positions are
+ * double-single (hi + lo floats) and separations use the simplified DS
+ * difference of Eq. 3; predicted positions are formed in FP64 and split into
+ * DS; partial sums are carried as compensated FP32 pairs and reduced in FP64.
+ * g6x_set_precision(cid, G6X_PREC_FP64) selects an all-FP64 path instead.
+ *
+ * Units: G = 1.  pot is the negative physical potential, -sum m_j/sqrt(r^2+eps2).
+ * Self-interaction is excluded by index: the j-particle whose `index` equals
+ * the i-particle's index does not act on it.  Indices must be >= 0.
+ *
+ * Calling sequence (Sect. 2.1, Sect. 2.5; the same order as GRAPE-6):
+ *   g6_open(cid);
+ *   per block step:  g6_set_j_particle(...) for each particle corrected last
+ *                    step; g6_set_ti(cid, t_blk);
+ *                    g6calc_firsthalf(...); g6calc_lasthalf(...) [or 2];
+ *                    optionally g6_read_neighbour_list / g6_get_neighbour_list;
+ *   g6_close(cid);
+ *
+ * Ownership: every array argument is owned by the caller.  g6_set_j_particle
+ * and g6calc_firsthalf copy what they need before returning, so the caller may
+ * reuse its arrays at once.  g6calc_lasthalf writes into the caller's arrays.
+ *
+ * Errors: functions return 0 on success or a negative G6_E* code.
+ * g6calc_firsthalf returns void (as in GRAPE-6): its error is latched and
+ * returned by the next g6calc_lasthalf.  A context is not thread-safe; use one
+ * context (cluster id) per thread.  Nothing in this library traps or aborts.
+ */
+#ifndef G6GB_H
+#define G6GB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- limits */
+#define G6_MAX_CLUSTERS   16     /* cluster ids 0 .. 15                          */
+#define G6_NPIPES_DEFAULT 256    /* i-particles per call (Sect. 2.5 footnote)    */
+#define G6_MAXNB          256    /* neighbour-list length (Sect. 4)              */
+#define G6_NJ_DEFAULT     (1 << 21) /* default j-memory capacity of g6_open      */
+
+/* ----------------------------------------------------------- error codes */
+#define G6_OK          0
+#define G6_EINVAL    (-22)  /* bad argument: cluster id, address, count, eps2 */
+#define G6_ENOTOPEN  (-19)  /* cluster id not open                            */
+#define G6_EBUSY     (-16)  /* cluster id already open / call out of order    */
+#define G6_ENOMEM    (-12)  /* device or pinned host allocation failed        */
+#define G6_EIO        (-5)  /* CUDA runtime error                             */
+#define G6_ETIMEDOUT (-110) /* a device-side bounded wait gave up             */
+#define G6_ENODEV    (-6)   /* no CUDA device / library built for another GPU */
+#define G6_EOVERFLOW  (1)   /* g6_read_neighbour_list: some list overflowed   */
+
+/* ------------------------------------------------ GRAPE-6 compatible API */
+
+/* Allocate a context for cluster id `clusterid` on the current CUDA device,
+ * with room for G6_NJ_DEFAULT j-particles (env G6GB_NJ overrides) and
+ * g6_npipes() i-particles per call.  Returns 0 or G6_EINVAL / G6_EBUSY /
+ * G6_ENOMEM / G6_EIO / G6_ENODEV. */
+int g6_open(int clusterid);
+
+/* Free everything the context owns.  Returns 0 or G6_EINVAL / G6_ENOTOPEN. */
+int g6_close(int clusterid);
+
+/* Maximum i-particles per g6calc call: 256 (Sect. 2.5 footnote), or the
+ * value of env G6GB_NPIPES when set. */
+int g6_npipes(void);
+
+/* GRAPE-6 fixed-point scale settings.  This library works in floating point,
+ * so both are accepted and ignored.  Return 0. */
+int g6_set_tunit(int newtunit);
+int g6_set_xunit(int newxunit);
+
+/* Set the block time t_blk to which the j-particles are predicted by the
+ * next g6calc_firsthalf (Sect. 2.2).  Cheap; marks the prediction stale. */
+int g6_set_ti(int clusterid, double ti);
+
+/* Store one j-particle in j-memory slot `address` (0 <= address < capacity)
+ * (Sect. 2.1: only corrected particles are sent each step).
+ *   index : particle id (>= 0) used for self-exclusion and returned by the
+ *           nearest-neighbour and neighbour-list calls;
+ *   tj    : time of this state; prediction uses dt = t_blk - tj (Sect. 2.2);
+ *   dtj   : the particle's own step (accepted, unused);
+ *   mass  : m_j;
+ *   k18   : snap / 18 (accepted, ignored: the predictor is 3rd order, Eq. 1);
+ *   j6    : jerk / 6;   a2: acceleration / 2 (pre-scaled Taylor terms);
+ *   v, x  : velocity and position at tj.
+ * The record is staged on the host and uploaded by the next firsthalf.
+ * Returns 0 or G6_EINVAL / G6_ENOTOPEN / G6_ENOMEM. */
+int g6_set_j_particle(int clusterid, int address, int index, double tj,
+                      double dtj, double mass, const double k18[3],
+                      const double j6[3], const double a2[3],
+                      const double v[3], const double x[3]);
+
+/* Start the force on ni i-particles (ni <= the context's ni_max, default
+ * g6_npipes()) from j-slots 0 .. nj-1 (Sect. 2.3).  xi, vi are the
+ * i-particles' predicted FP64 state at t_blk (the host predicts i-particles,
+ * Sect. 2.1); index[] their ids; eps2 >= 0 the softening of this i-block
+ * (Sect. 2.5); h2[] (may be NULL) the squared neighbour radius per i.  aold,
+ * j6old, phiold are accepted and ignored (no fixed-point scaling is needed).
+ * Asynchronous: uploads pending j updates and the i-data, predicts the
+ * j-particles if t_blk or j-memory changed, launches the force and the
+ * reduction, and starts the copy back.  Errors are latched for lasthalf. */
+void g6calc_firsthalf(int clusterid, int nj, int ni, const int index[],
+                      const double xi[][3], const double vi[][3],
+                      const double aold[][3], const double j6old[][3],
+                      const double phiold[], double eps2, const double h2[]);
+
+/* Wait for the force started by firsthalf and write acc, jerk, pot (ni
+ * entries each).  The argument list repeats firsthalf's as in GRAPE-6; nj,
+ * ni and index must match.  Returns 0, the latched firsthalf error, or
+ * G6_EIO / G6_ETIMEDOUT. */
+int g6calc_lasthalf(int clusterid, int nj, int ni, const int index[],
+                    const double xi[][3], const double vi[][3], double eps2,
+                    const double h2[], double acc[][3], double jerk[][3],
+                    double pot[]);
+
+/* As g6calc_lasthalf, plus nnbindex[i] = index of the nearest j-particle
+ * (smallest unsoftened |r|^2, ties to the lower j-slot), or -1 if none
+ * (Sect. 2.5). */
+int g6calc_lasthalf2(int clusterid, int nj, int ni, const int index[],
+                     const double xi[][3], const double vi[][3], double eps2,
+                     const double h2[], double acc[][3], double jerk[][3],
+                     double pot[], int nnbindex[]);
+
+/* Copy the neighbour lists of the last calculation to the host (Sect. 4):
+ * for each i the j-particles with unsoftened |r|^2 < h2[i], excluding
+ * itself, in ascending j-slot order, at most G6_MAXNB of them.  Returns 0,
+ * G6_EOVERFLOW (1) if some list was longer than G6_MAXNB (it is truncated),
+ * or a negative error.  Lists exist only if firsthalf got h2 != NULL. */
+int g6_read_neighbour_list(int clusterid);
+
+/* Neighbour list of i-particle number ipipe (0 <= ipipe < ni) of the last
+ * calculation: *nblen = list length, nbl[0 .. min(*nblen, maxlength)-1] =
+ * particle indices.  Returns 0, G6_EOVERFLOW if *nblen > maxlength or the
+ * list overflowed G6_MAXNB, or a negative error. */
+int g6_get_neighbour_list(int clusterid, int ipipe, int maxlength, int *nblen,
+                          int nbl[]);
+
+/* ------------------------------------------------------------ extensions */
+
+#define G6X_PREC_DS   0   /* FP32 + double-single (default, Sect. 2.2-2.3) */
+#define G6X_PREC_FP64 1   /* all-FP64 prediction and force                 */
+
+/* As g6_open with an explicit j capacity and i-per-call limit. */
+int g6x_open_ex(int clusterid, int nj_max, int ni_max);
+
+/* Select the arithmetic of later calculations (G6X_PREC_*). */
+int g6x_set_precision(int clusterid, int mode);
+
+/* Raise (or lower) the i-per-call limit above g6_npipes(). */
+int g6x_set_ni_max(int clusterid, int ni_max);
+
+/* Run the context's work on this cudaStream_t (NULL: the context's own
+ * stream).  The stream is borrowed, not owned. */
+int g6x_set_stream(int clusterid, void *stream);
+
+/* Device allocator hook used by every later g6_open (NULL, NULL: plain
+ * cudaMalloc / cudaFree).  alloc(bytes, user) returns a device pointer or
+ * NULL; release(ptr, user) frees it. */
+typedef void *(*g6x_alloc_fn)(size_t bytes, void *user);
+typedef void (*g6x_free_fn)(void *ptr, void *user);
+int g6x_set_allocator(g6x_alloc_fn alloc, g6x_free_fn release, void *user);
+
+/* Bulk form of g6_set_j_particle for n particles (arrays of n entries;
+ * j6, a2, v, x are n x 3).  Stops at the first error and returns it. */
+int g6x_set_j_particles(int clusterid, int n, const int address[],
+                        const int index[], const double tj[],
+                        const double mass[], const double j6[][3],
+                        const double a2[][3], const double v[][3],
+                        const double x[][3]);
+
+/* Human-readable text for a G6_E* code (static storage). */
+const char *g6x_strerror(int code);
+
+/* --------------------------------------- device-resident entry points --
+ * The same work on records already in device memory (caller-owned device
+ * pointers), asynchronous on the context's stream, no host copies. */
+
+/* One j-particle update, 120 bytes, same meaning as g6_set_j_particle. */
+typedef struct {
+    double x[3], v[3], a2[3], j6[3];
+    double mass, tj;
+    int address, index;
+} g6x_jrec;
+
+/* One i-particle, 64 bytes: predicted FP64 state, squared neighbour radius
+ * (<= 0: no list entries) and id. */
+typedef struct {
+    double x[3], v[3];
+    double h2;
+    int index, pad;
+} g6x_irec;
+
+/* One result, 64 bytes: acceleration, jerk, potential, nearest-neighbour
+ * index (-1 if none) and its unsoftened |r|^2 as computed by the kernel. */
+typedef struct {
+    double acc[3], jerk[3];
+    double pot;
+    int nnb;
+    float nnr2;
+} g6x_out;
+
+/* Scatter n device-resident j records into j-memory (the j-store update). */
+int g6x_set_j_dev(int clusterid, int n, const g6x_jrec *d_rec);
+
+/* Predict j-slots 0 .. nj-1 to time ti if stale (Eq. 1, Eq. 2), then force
+ * on ni device-resident i records and reduce into ni device-resident
+ * results.  nl != 0 also builds neighbour lists (read back with
+ * g6_read_neighbour_list).  Returns 0 or a negative error; completion is
+ * ordered on the context's stream. */
+int g6x_calc_dev(int clusterid, double ti, int nj, int ni,
+                 const g6x_irec *d_irec, double eps2, int nl, g6x_out *d_out);
+
+/* Read back the predicted j-particles of the current precision mode for
+ * checking: hi[nj][4], lo[nj][4] (DS mode; lo unused in FP64 mode) as float,
+ * or x64[nj][4], v64[nj][4] as double.  Pointers may be NULL.  Synchronous. */
+int g6x_get_predicted(int clusterid, int nj, float *hi, float *lo, float *vel,
+                      double *x64, double *v64);
+
+/* Wait for the context's stream and report a device-side error recorded by
+ * an earlier g6x_calc_dev (G6_ETIMEDOUT) or a CUDA error.  Returns 0 or the
+ * code.  Not allowed between firsthalf and lasthalf (G6_EBUSY). */
+int g6x_sync(int clusterid);
+
+/* Pin the force-kernel variant (0 .. variant count - 1; -1: automatic) and
+ * the grid size (<= 0: automatic) of later calculations, for tuning. */
+int g6x_set_variant(int clusterid, int variant, int grid);
+
+/* Per-kernel CUDA-event timing on the context's stream.  enable != 0 resets
+ * the counters and brackets every later launch with events; 0 stops. */
+int g6x_set_timing(int clusterid, int enable);
+
+/* Device time (ms, summed) and launch count per phase since timing was
+ * enabled: [0] j-memory scatter, [1] predictor, [2] force, [3] reduction.
+ * Synchronises the stream.  Either pointer may be NULL. */
+int g6x_get_timing(int clusterid, double ms[4], long long count[4]);
+
+/* Launch statistics of the last calculation: kernel variant id, threads
+ * along i and j, i-particles per thread, grid size and j-tiles.  Any pointer
+ * may be NULL. */
+int g6x_last_config(int clusterid, int *variant, int *ti, int *tj, int *ni_per,
+                    int *grid, int *jtiles);
+
+/* Number of kernels launched on the context's stream since g6_open. */
+long long g6x_launch_count(int clusterid);
+
+/* ----------------------------------- Hermite block-time-step driver ----
+ * A plain C++ 4th-order Hermite predictor-corrector with power-of-two block
+ * time steps (Sect. 2, Sect. 2.1) that drives the g6_* calls above: it
+ * predicts the active i-particles on the host, corrects them (Makino &
+ * Aarseth 1992), picks their next steps (Aarseth 1985 criterion, cited in
+ * Sect. 3.1-3.2) and sends them back with g6_set_j_particle. */
+
+typedef struct g6h_sim g6h_sim;
+
+/* Create a simulation of n particles (masses m[n], positions x[n][3],
+ * velocities v[n][3], copied) on cluster id `clusterid` (opened by the
+ * caller).  eta: accuracy parameter; eta_s: initial-step parameter (<= 0:
+ * eta / 10); dt_max: largest step (a power of two); dt_min: smallest.
+ * Computes the initial force with one full sweep.  Returns NULL on error
+ * (*err receives the code when err != NULL). */
+g6h_sim *g6h_create(int clusterid, int n, const double *m, const double *x,
+                    const double *v, double eps2, double eta, double eta_s,
+                    double dt_max, double dt_min, int *err);
+
+/* Advance block steps until every particle reaches t_end (a multiple of
+ * dt_max).  Returns 0 or a negative error. */
+int g6h_run(g6h_sim *s, double t_end);
+
+/* Copy the current state out (any pointer may be NULL): x, v, acc, jerk
+ * [n][3]; t, dt [n]. */
+int g6h_get_state(const g6h_sim *s, double *x, double *v, double *acc,
+                  double *jerk, double *t, double *dt);
+
+/* Kinetic + potential energy of the synchronised system, the potential
+ * from one full force sweep through the library.  Returns 0 or an error. */
+int g6h_energy(g6h_sim *s, double *e_kin, double *e_pot);
+
+/* Counters: block steps, sum of block sizes, and a 64-bin histogram of
+ * floor(log2(block size)) (hist may be NULL). */
+int g6h_stats(const g6h_sim *s, long long *nblocks, long long *nactive,
+              long long *hist);
+
+void g6h_destroy(g6h_sim *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* G6GB_H */

@@ -1,0 +1,1065 @@
+// g6gb_api.cu -- C ABI of the GRAPE-6-style force library (arXiv:0902.4463,
+// Sect. 2.5: the library keeps the GRAPE-6 calling sequence so that N-body
+// codes only relink).  Host side of the hot path: contexts, j-memory staging,
+// the prediction bookkeeping of Sect. 2.1-2.2 (j-particles are predicted once
+// per block time), launches and the copy back.  All arithmetic of the method
+// runs in the kernels of g6gb_kernels.cu; this file only moves data.
+#include "g6gb_internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <utility>
+#include <vector>
+
+namespace {
+
+using g6::ForceConfig;
+using g6::JT;
+using g6::Partial;
+
+g6x_alloc_fn g_alloc = nullptr;
+g6x_free_fn g_free = nullptr;
+void *g_alloc_user = nullptr;
+
+void *dev_alloc(size_t bytes)
+{
+    if (bytes == 0)
+        bytes = 16;
+    if (g_alloc)
+        return g_alloc(bytes, g_alloc_user);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(void *p)
+{
+    if (!p)
+        return;
+    if (g_free)
+        g_free(p, g_alloc_user);
+    else
+        cudaFree(p);
+}
+
+void *host_alloc(size_t bytes)
+{
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, bytes ? bytes : 16, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void host_free(void *p)
+{
+    if (p)
+        cudaFreeHost(p);
+}
+
+int env_int(const char *name, int dflt)
+{
+    const char *s = std::getenv(name);
+    if (!s || !*s)
+        return dflt;
+    long v = std::strtol(s, nullptr, 10);
+    return v > 0 ? (int)v : dflt;
+}
+
+int round_up(int n, int k) { return (n + k - 1) / k * k; }
+
+struct Ctx {
+    bool open = false;
+    int dev = 0, sm_count = 0;
+    cudaStream_t own = nullptr;
+    cudaStream_t stream = nullptr;
+    int cap = 0, ni_max = 0, prec = G6X_PREC_DS;
+    g6::JStore js{};
+    g6::Pred pred{};
+    // j-memory updates staged on the host, uploaded by the next calculation
+    g6x_jrec *h_jst = nullptr, *d_jst = nullptr;
+    int n_jst = 0, jst_cap = 0;
+    std::vector<int> slot_of;
+    cudaEvent_t ev_jst = nullptr;
+    bool jst_inflight = false;
+    // i-data and results of the GRAPE path
+    g6x_irec *h_irec = nullptr, *d_irec = nullptr;
+    g6x_out *h_out = nullptr, *d_out = nullptr;
+    int io_cap = 0;
+    // partial results
+    Partial *d_part = nullptr;
+    size_t part_cap = 0;
+    int *d_nbl_part = nullptr, *d_nbc_part = nullptr;
+    size_t nbp_cap = 0;
+    int *d_nbl = nullptr, *d_nblen = nullptr, *h_nbl = nullptr, *h_nblen = nullptr;
+    size_t nbo_cap = 0;
+    int *d_err = nullptr, *h_err = nullptr;
+    // prediction bookkeeping per precision mode
+    double t_set = 0.0;
+    double t_pred[2] = {NAN, NAN};
+    int nj_pred[2] = {-1, -1};
+    long long ver = 0, ver_pred[2] = {-1, -1};
+    // calculation in flight
+    bool pending = false;
+    int latched = 0;
+    int calc_ni = 0, calc_nj = 0;
+    bool lists_ready = false, lists_host = false;
+    int list_ni = 0;
+    cudaEvent_t ev_done = nullptr;
+    ForceConfig last_cfg{};
+    long long launches = 0;
+    int force_variant = -1, force_grid = 0;
+    // optional per-phase event timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[4];
+    double t_ms[4] = {0, 0, 0, 0};
+    long long t_cnt[4] = {0, 0, 0, 0};
+};
+
+Ctx g_ctx[G6_MAX_CLUSTERS];
+
+enum Phase { PH_SCATTER = 0, PH_PREDICT = 1, PH_FORCE = 2, PH_REDUCE = 3 };
+
+cudaEvent_t pool_event(Ctx &c)
+{
+    if (!c.ev_pool.empty()) {
+        cudaEvent_t e = c.ev_pool.back();
+        c.ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Bracket one launch with events when timing is on.
+struct PhaseTimer {
+    Ctx &c;
+    int ph;
+    cudaEvent_t e0 = nullptr;
+    PhaseTimer(Ctx &cc, int p) : c(cc), ph(p)
+    {
+        if (c.timing && (e0 = pool_event(c)) != nullptr)
+            cudaEventRecord(e0, c.stream);
+    }
+    ~PhaseTimer()
+    {
+        if (!e0)
+            return;
+        cudaEvent_t e1 = pool_event(c);
+        if (!e1) {
+            c.ev_pool.push_back(e0);
+            return;
+        }
+        cudaEventRecord(e1, c.stream);
+        c.ev_pending[ph].push_back({e0, e1});
+    }
+};
+
+void resolve_timing(Ctx &c)
+{
+    for (int p = 0; p < 4; ++p) {
+        for (auto &pr : c.ev_pending[p]) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+                c.t_ms[p] += ms;
+                c.t_cnt[p] += 1;
+            } else {
+                cudaGetLastError();
+            }
+            c.ev_pool.push_back(pr.first);
+            c.ev_pool.push_back(pr.second);
+        }
+        c.ev_pending[p].clear();
+    }
+}
+
+Ctx *get(int cid, int *err)
+{
+    if (cid < 0 || cid >= G6_MAX_CLUSTERS) {
+        *err = G6_EINVAL;
+        return nullptr;
+    }
+    if (!g_ctx[cid].open) {
+        *err = G6_ENOTOPEN;
+        return nullptr;
+    }
+    *err = 0;
+    return &g_ctx[cid];
+}
+
+int cuda_err(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return 0;
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation)
+        return G6_ENOMEM;
+    if (e == cudaErrorNoKernelImageForDevice || e == cudaErrorNoDevice
+        || e == cudaErrorInsufficientDriver)
+        return G6_ENODEV;
+    return G6_EIO;
+}
+
+void free_ctx(Ctx &c)
+{
+    if (c.stream)
+        cudaStreamSynchronize(c.stream);
+    g6::JStore &js = c.js;
+    void *dptrs[] = {js.x0, js.t0, js.v0m, js.a2f, js.j6f, js.v64, js.a264, js.j664,
+                     js.idx, c.pred.ph, c.pred.pl, c.pred.pv, c.pred.p64, c.pred.v64,
+                     c.d_jst, c.d_irec, c.d_out, c.d_part, c.d_nbl_part, c.d_nbc_part,
+                     c.d_nbl, c.d_nblen, c.d_err};
+    for (void *p : dptrs)
+        dev_free(p);
+    void *hptrs[] = {c.h_jst, c.h_irec, c.h_out, c.h_nbl, c.h_nblen, c.h_err};
+    for (void *p : hptrs)
+        host_free(p);
+    for (int p = 0; p < 4; ++p)
+        for (auto &pr : c.ev_pending[p]) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+    for (cudaEvent_t e : c.ev_pool)
+        cudaEventDestroy(e);
+    if (c.ev_jst)
+        cudaEventDestroy(c.ev_jst);
+    if (c.ev_done)
+        cudaEventDestroy(c.ev_done);
+    if (c.own)
+        cudaStreamDestroy(c.own);
+    c = Ctx();
+}
+
+// Grow a device buffer to at least `need` elements (contents not kept).
+template <class T>
+int grow_dev(T *&p, size_t &cap, size_t need)
+{
+    if (need <= cap && p)
+        return 0;
+    size_t n = need + need / 4 + 64;
+    T *q = (T *)dev_alloc(n * sizeof(T));
+    if (!q)
+        return G6_ENOMEM;
+    dev_free(p);
+    p = q;
+    cap = n;
+    return 0;
+}
+
+int ensure_io(Ctx &c, int n)
+{
+    if (n <= c.io_cap && c.h_irec)
+        return 0;
+    int cap = n < 16 ? 16 : n;
+    g6x_irec *hi = (g6x_irec *)host_alloc(sizeof(g6x_irec) * cap);
+    g6x_out *ho = (g6x_out *)host_alloc(sizeof(g6x_out) * cap);
+    g6x_irec *di = (g6x_irec *)dev_alloc(sizeof(g6x_irec) * cap);
+    g6x_out *dout = (g6x_out *)dev_alloc(sizeof(g6x_out) * cap);
+    if (!hi || !ho || !di || !dout) {
+        host_free(hi);
+        host_free(ho);
+        dev_free(di);
+        dev_free(dout);
+        return G6_ENOMEM;
+    }
+    host_free(c.h_irec);
+    host_free(c.h_out);
+    dev_free(c.d_irec);
+    dev_free(c.d_out);
+    c.h_irec = hi;
+    c.h_out = ho;
+    c.d_irec = di;
+    c.d_out = dout;
+    c.io_cap = cap;
+    return 0;
+}
+
+int ensure_jstage(Ctx &c, int need)
+{
+    if (need <= c.jst_cap)
+        return 0;
+    int cap = c.jst_cap ? c.jst_cap : 1024;
+    while (cap < need)
+        cap *= 2;
+    if (cap > c.cap)
+        cap = c.cap;
+    g6x_jrec *h = (g6x_jrec *)host_alloc(sizeof(g6x_jrec) * cap);
+    g6x_jrec *d = (g6x_jrec *)dev_alloc(sizeof(g6x_jrec) * cap);
+    if (!h || !d) {
+        host_free(h);
+        dev_free(d);
+        return G6_ENOMEM;
+    }
+    if (c.jst_inflight) {
+        cudaEventSynchronize(c.ev_jst);
+        c.jst_inflight = false;
+    }
+    if (c.n_jst)
+        std::memcpy(h, c.h_jst, sizeof(g6x_jrec) * c.n_jst);
+    host_free(c.h_jst);
+    dev_free(c.d_jst);
+    c.h_jst = h;
+    c.d_jst = d;
+    c.jst_cap = cap;
+    return 0;
+}
+
+// Upload staged j updates and scatter them into j-memory (K0).
+int flush_jstage(Ctx &c)
+{
+    if (c.n_jst == 0)
+        return 0;
+    cudaError_t e = cudaMemcpyAsync(c.d_jst, c.h_jst, sizeof(g6x_jrec) * c.n_jst,
+                                    cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) {
+        PhaseTimer pt(c, PH_SCATTER);
+        e = g6::launch_scatter(c.d_jst, c.n_jst, c.js, c.stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaEventRecord(c.ev_jst, c.stream);
+    if (e != cudaSuccess)
+        return cuda_err(e);
+    c.launches += 1;
+    c.jst_inflight = true;
+    for (int k = 0; k < c.n_jst; ++k)
+        c.slot_of[c.h_jst[k].address] = -1;
+    c.n_jst = 0;
+    c.ver += 1;
+    return 0;
+}
+
+// Predict j-slots 0 .. nj-1 to t_set unless this mode already holds exactly
+// that prediction (Sect. 2.1: the O(n) predictor runs once per block time).
+int predict_if_stale(Ctx &c, int nj)
+{
+    int m = c.prec;
+    if (c.t_pred[m] == c.t_set && c.nj_pred[m] == nj && c.ver_pred[m] == c.ver)
+        return 0;
+    int nj_pad = round_up(nj > 0 ? nj : 1, JT);
+    cudaError_t e;
+    {
+        PhaseTimer pt(c, PH_PREDICT);
+        e = g6::launch_predict(m, c.js, c.pred, nj, nj_pad, c.t_set, c.sm_count, c.stream);
+    }
+    if (e != cudaSuccess)
+        return cuda_err(e);
+    c.launches += 1;
+    c.t_pred[m] = c.t_set;
+    c.nj_pred[m] = nj;
+    c.ver_pred[m] = c.ver;
+    return 0;
+}
+
+// Output neighbour lists for ni i-particles (device and pinned host copies).
+int grow_nb_out(Ctx &c, int ni)
+{
+    if ((size_t)ni <= c.nbo_cap && c.d_nbl)
+        return 0;
+    size_t n = (size_t)(ni > 16 ? ni : 16);
+    int *dl = (int *)dev_alloc(n * G6_MAXNB * sizeof(int));
+    int *dn = (int *)dev_alloc(n * sizeof(int));
+    int *hl = (int *)host_alloc(n * G6_MAXNB * sizeof(int));
+    int *hn = (int *)host_alloc(n * sizeof(int));
+    if (!dl || !dn || !hl || !hn) {
+        dev_free(dl);
+        dev_free(dn);
+        host_free(hl);
+        host_free(hn);
+        return G6_ENOMEM;
+    }
+    dev_free(c.d_nbl);
+    dev_free(c.d_nblen);
+    host_free(c.h_nbl);
+    host_free(c.h_nblen);
+    c.d_nbl = dl;
+    c.d_nblen = dn;
+    c.h_nbl = hl;
+    c.h_nblen = hn;
+    c.nbo_cap = n;
+    return 0;
+}
+
+// Force + reduction on ni i records already on the device.
+int run_force(Ctx &c, int nj, int ni, const g6x_irec *d_irec, double eps2, bool list,
+              g6x_out *d_out)
+{
+    int nj_pad = round_up(nj > 0 ? nj : 1, JT);
+    ForceConfig cfg = g6::choose_config(c.prec, ni, nj_pad, list ? 1 : 0, c.sm_count,
+                                        c.force_variant, c.force_grid);
+    size_t slots = g6::partial_slots(cfg);
+    int rc = grow_dev(c.d_part, c.part_cap, slots);
+    if (rc)
+        return rc;
+    if (cfg.list) {
+        size_t cap_old = c.nbp_cap;
+        rc = grow_dev(c.d_nbc_part, c.nbp_cap, slots);
+        if (rc)
+            return rc;
+        if (c.nbp_cap != cap_old || !c.d_nbl_part) {
+            dev_free(c.d_nbl_part);
+            c.d_nbl_part = (int *)dev_alloc(c.nbp_cap * G6_MAXNB * sizeof(int));
+            if (!c.d_nbl_part) {
+                c.nbp_cap = 0;
+                dev_free(c.d_nbc_part);
+                c.d_nbc_part = nullptr;
+                return G6_ENOMEM;
+            }
+        }
+        rc = grow_nb_out(c, ni);
+        if (rc)
+            return rc;
+    }
+    cudaError_t e;
+    {
+        PhaseTimer pt(c, PH_FORCE);
+        e = g6::launch_force(cfg, c.pred, d_irec, ni, eps2, c.d_part, c.d_nbl_part,
+                             c.d_nbc_part, c.d_err, c.stream);
+    }
+    if (e == cudaSuccess) {
+        PhaseTimer pt(c, PH_REDUCE);
+        e = g6::launch_reduce(cfg, c.d_part, c.d_nbl_part, c.d_nbc_part, c.js.idx, ni, d_out,
+                              c.d_nbl, c.d_nblen, c.stream);
+    }
+    if (e != cudaSuccess)
+        return cuda_err(e);
+    c.launches += 2;
+    c.last_cfg = cfg;
+    c.lists_ready = cfg.list != 0;
+    c.lists_host = false;
+    c.list_ni = ni;
+    return 0;
+}
+
+int check_eps2(double eps2)
+{
+    return (eps2 >= 0.0 && std::isfinite(eps2)) ? 0 : G6_EINVAL;
+}
+
+}  // namespace
+
+extern "C" {
+
+int g6_npipes(void) { return env_int("G6GB_NPIPES", G6_NPIPES_DEFAULT); }
+
+int g6_set_tunit(int) { return 0; }
+int g6_set_xunit(int) { return 0; }
+
+int g6x_set_allocator(g6x_alloc_fn alloc, g6x_free_fn release, void *user)
+{
+    if ((alloc == nullptr) != (release == nullptr))
+        return G6_EINVAL;
+    for (auto &c : g_ctx)
+        if (c.open)
+            return G6_EBUSY;
+    g_alloc = alloc;
+    g_free = release;
+    g_alloc_user = user;
+    return 0;
+}
+
+int g6x_open_ex(int cid, int nj_max, int ni_max)
+{
+    if (cid < 0 || cid >= G6_MAX_CLUSTERS || nj_max < 1 || ni_max < 1)
+        return G6_EINVAL;
+    Ctx &c = g_ctx[cid];
+    if (c.open)
+        return G6_EBUSY;
+    c = Ctx();
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return G6_ENODEV;
+    }
+    if (cudaGetDevice(&c.dev) != cudaSuccess)
+        return G6_ENODEV;
+    cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, c.dev);
+    if (c.sm_count < 1)
+        return G6_ENODEV;
+    if (g6::variant_occupancy(0) < 1) {      // kernels not loadable on this GPU
+        cudaGetLastError();
+        return G6_ENODEV;
+    }
+    c.open = true;                         // so that free_ctx releases partial work
+    int rc = 0;
+    if (cudaStreamCreateWithFlags(&c.own, cudaStreamNonBlocking) != cudaSuccess
+        || cudaEventCreateWithFlags(&c.ev_jst, cudaEventDisableTiming) != cudaSuccess
+        || cudaEventCreateWithFlags(&c.ev_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        return G6_EIO;
+    }
+    c.stream = c.own;
+    c.cap = round_up(nj_max, JT);
+    c.ni_max = ni_max;
+    size_t n = (size_t)c.cap;
+    g6::JStore &js = c.js;
+    js.cap = c.cap;
+    js.x0 = (double *)dev_alloc(3 * n * sizeof(double));
+    js.t0 = (double *)dev_alloc(n * sizeof(double));
+    js.v0m = (float4 *)dev_alloc(n * sizeof(float4));
+    js.a2f = (float4 *)dev_alloc(n * sizeof(float4));
+    js.j6f = (float4 *)dev_alloc(n * sizeof(float4));
+    js.v64 = (double4 *)dev_alloc(n * sizeof(double4));
+    js.a264 = (double4 *)dev_alloc(n * sizeof(double4));
+    js.j664 = (double4 *)dev_alloc(n * sizeof(double4));
+    js.idx = (int *)dev_alloc(n * sizeof(int));
+    c.pred.ph = (float4 *)dev_alloc(n * sizeof(float4));
+    c.pred.pl = (float4 *)dev_alloc(n * sizeof(float4));
+    c.pred.pv = (float4 *)dev_alloc(n * sizeof(float4));
+    c.pred.p64 = (double4 *)dev_alloc(n * sizeof(double4));
+    c.pred.v64 = (double4 *)dev_alloc(n * sizeof(double4));
+    c.d_err = (int *)dev_alloc(sizeof(int));
+    c.h_err = (int *)host_alloc(sizeof(int));
+    if (!js.x0 || !js.t0 || !js.v0m || !js.a2f || !js.j6f || !js.v64 || !js.a264
+        || !js.j664 || !js.idx || !c.pred.ph || !c.pred.pl || !c.pred.pv || !c.pred.p64
+        || !c.pred.v64 || !c.d_err || !c.h_err)
+        rc = G6_ENOMEM;
+    if (!rc)
+        rc = ensure_io(c, ni_max < 4096 ? ni_max : 4096);
+    if (!rc)
+        rc = ensure_jstage(c, 1024 < c.cap ? 1024 : c.cap);
+    if (!rc) {
+        try {
+            c.slot_of.assign(n, -1);
+        } catch (...) {
+            rc = G6_ENOMEM;
+        }
+    }
+    if (!rc) {
+        cudaError_t e = cudaMemsetAsync(c.d_err, 0, sizeof(int), c.stream);
+        if (e == cudaSuccess)
+            e = g6::launch_init_store(js, c.stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(c.stream);
+        rc = cuda_err(e);
+        c.launches += 1;
+    }
+    if (rc) {
+        free_ctx(c);
+        return rc;
+    }
+    return 0;
+}
+
+int g6_open(int cid)
+{
+    return g6x_open_ex(cid, env_int("G6GB_NJ", G6_NJ_DEFAULT), g6_npipes());
+}
+
+int g6_close(int cid)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    free_ctx(*c);
+    return 0;
+}
+
+int g6x_set_precision(int cid, int mode)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (mode != G6X_PREC_DS && mode != G6X_PREC_FP64)
+        return G6_EINVAL;
+    c->prec = mode;
+    return 0;
+}
+
+int g6x_set_ni_max(int cid, int ni_max)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (ni_max < 1 || c->pending)
+        return G6_EINVAL;
+    c->ni_max = ni_max;
+    return 0;
+}
+
+int g6x_set_stream(int cid, void *stream)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (c->pending)
+        return G6_EBUSY;
+    cudaStreamSynchronize(c->stream);
+    c->stream = stream ? (cudaStream_t)stream : c->own;
+    return 0;
+}
+
+int g6x_set_variant(int cid, int variant, int grid)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (variant >= g6::variant_count())
+        return G6_EINVAL;
+    c->force_variant = variant;
+    c->force_grid = grid > 0 ? grid : 0;
+    return 0;
+}
+
+int g6_set_ti(int cid, double ti)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (!std::isfinite(ti))
+        return G6_EINVAL;
+    c->t_set = ti;
+    return 0;
+}
+
+int g6_set_j_particle(int cid, int address, int index, double tj, double dtj,
+                      double mass, const double k18[3], const double j6[3],
+                      const double a2[3], const double v[3], const double x[3])
+{
+    (void)dtj;
+    (void)k18;
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (address < 0 || address >= c->cap || index < 0 || !j6 || !a2 || !v || !x)
+        return G6_EINVAL;
+    if (c->jst_inflight) {             // staging buffer still being uploaded
+        cudaEventSynchronize(c->ev_jst);
+        c->jst_inflight = false;
+    }
+    int slot = c->slot_of[address];
+    if (slot < 0) {
+        int rc = ensure_jstage(*c, c->n_jst + 1);
+        if (rc)
+            return rc;
+        slot = c->n_jst++;
+        c->slot_of[address] = slot;
+    }
+    g6x_jrec &r = c->h_jst[slot];
+    for (int d = 0; d < 3; ++d) {
+        r.x[d] = x[d];
+        r.v[d] = v[d];
+        r.a2[d] = a2[d];
+        r.j6[d] = j6[d];
+    }
+    r.mass = mass;
+    r.tj = tj;
+    r.address = address;
+    r.index = index;
+    return 0;
+}
+
+void g6calc_firsthalf(int cid, int nj, int ni, const int index[],
+                      const double xi[][3], const double vi[][3],
+                      const double aold[][3], const double j6old[][3],
+                      const double phiold[], double eps2, const double h2[])
+{
+    (void)aold;
+    (void)j6old;
+    (void)phiold;
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return;
+    if (c->pending) {                  // previous calculation never collected
+        cudaEventSynchronize(c->ev_done);
+        c->pending = false;
+    }
+    c->latched = 0;
+    c->calc_ni = ni;
+    c->calc_nj = nj;
+    if (nj < 0 || nj > c->cap || ni < 0 || ni > c->ni_max || check_eps2(eps2)
+        || (ni > 0 && (!index || !xi || !vi))) {
+        c->latched = G6_EINVAL;
+        c->pending = true;
+        return;
+    }
+    int rc = ensure_io(*c, ni);
+    bool list = false;
+    for (int k = 0; !rc && k < ni; ++k) {
+        if (index[k] < 0) {
+            rc = G6_EINVAL;
+            break;
+        }
+        g6x_irec &r = c->h_irec[k];
+        for (int d = 0; d < 3; ++d) {
+            r.x[d] = xi[k][d];
+            r.v[d] = vi[k][d];
+        }
+        r.h2 = h2 ? h2[k] : 0.0;
+        r.index = index[k];
+        r.pad = 0;
+        if (h2 && h2[k] > 0.0)
+            list = true;
+    }
+    if (!rc)
+        rc = flush_jstage(*c);
+    if (!rc)
+        rc = predict_if_stale(*c, nj);
+    if (!rc && ni > 0) {
+        cudaError_t e = cudaMemcpyAsync(c->d_irec, c->h_irec, sizeof(g6x_irec) * ni,
+                                        cudaMemcpyHostToDevice, c->stream);
+        rc = cuda_err(e);
+        if (!rc)
+            rc = run_force(*c, nj, ni, c->d_irec, eps2, list, c->d_out);
+        if (!rc && h2 && !list) {
+            // every radius is <= 0: no list can have entries; skip the list
+            // kernel and publish empty lists
+            rc = grow_nb_out(*c, ni);
+            if (!rc)
+                rc = cuda_err(cudaMemsetAsync(c->d_nblen, 0, sizeof(int) * ni, c->stream));
+            if (!rc) {
+                c->lists_ready = true;
+                c->list_ni = ni;
+            }
+        }
+        if (!rc) {
+            e = cudaMemcpyAsync(c->h_out, c->d_out, sizeof(g6x_out) * ni,
+                                cudaMemcpyDeviceToHost, c->stream);
+            rc = cuda_err(e);
+        }
+    }
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int),
+                                        cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(c->ev_done, c->stream);
+        rc = cuda_err(e);
+    }
+    c->latched = rc;
+    c->pending = true;
+}
+
+static int lasthalf_common(int cid, int nj, int ni, double acc[][3], double jerk[][3],
+                           double pot[], int nnb[])
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (!c->pending)
+        return G6_EBUSY;
+    c->pending = false;
+    if (c->latched)
+        return c->latched;
+    if (ni != c->calc_ni || nj != c->calc_nj)
+        return G6_EINVAL;
+    cudaError_t e = cudaEventSynchronize(c->ev_done);
+    if (e != cudaSuccess)
+        return cuda_err(e);
+    if (*c->h_err) {
+        int code = *c->h_err;
+        *c->h_err = 0;
+        cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+        return code < 0 ? code : G6_EIO;
+    }
+    for (int k = 0; k < ni; ++k) {
+        const g6x_out &o = c->h_out[k];
+        for (int d = 0; d < 3; ++d) {
+            if (acc)
+                acc[k][d] = o.acc[d];
+            if (jerk)
+                jerk[k][d] = o.jerk[d];
+        }
+        if (pot)
+            pot[k] = o.pot;
+        if (nnb)
+            nnb[k] = o.nnb;
+    }
+    return 0;
+}
+
+int g6calc_lasthalf(int cid, int nj, int ni, const int index[], const double xi[][3],
+                    const double vi[][3], double eps2, const double h2[],
+                    double acc[][3], double jerk[][3], double pot[])
+{
+    (void)index;
+    (void)xi;
+    (void)vi;
+    (void)eps2;
+    (void)h2;
+    return lasthalf_common(cid, nj, ni, acc, jerk, pot, nullptr);
+}
+
+int g6calc_lasthalf2(int cid, int nj, int ni, const int index[], const double xi[][3],
+                     const double vi[][3], double eps2, const double h2[],
+                     double acc[][3], double jerk[][3], double pot[], int nnbindex[])
+{
+    (void)index;
+    (void)xi;
+    (void)vi;
+    (void)eps2;
+    (void)h2;
+    return lasthalf_common(cid, nj, ni, acc, jerk, pot, nnbindex);
+}
+
+int g6_read_neighbour_list(int cid)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (c->pending || !c->lists_ready)
+        return G6_EINVAL;
+    int n = c->list_ni;
+    cudaError_t e = cudaMemcpyAsync(c->h_nblen, c->d_nblen, sizeof(int) * n,
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->h_nbl, c->d_nbl, sizeof(int) * (size_t)n * G6_MAXNB,
+                            cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return cuda_err(e);
+    c->lists_host = true;
+    for (int k = 0; k < n; ++k)
+        if (c->h_nblen[k] > G6_MAXNB)
+            return G6_EOVERFLOW;
+    return 0;
+}
+
+int g6_get_neighbour_list(int cid, int ipipe, int maxlength, int *nblen, int nbl[])
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (!c->lists_host || ipipe < 0 || ipipe >= c->list_ni || maxlength < 0 || !nblen)
+        return G6_EINVAL;
+    int len = c->h_nblen[ipipe];
+    *nblen = len;
+    int keep = len < G6_MAXNB ? len : G6_MAXNB;
+    if (keep > maxlength)
+        keep = maxlength;
+    if (keep > 0 && !nbl)
+        return G6_EINVAL;
+    for (int k = 0; k < keep; ++k)
+        nbl[k] = c->h_nbl[(size_t)ipipe * G6_MAXNB + k];
+    return (len > G6_MAXNB || len > maxlength) ? G6_EOVERFLOW : 0;
+}
+
+int g6x_set_j_particles(int cid, int n, const int address[], const int index[],
+                        const double tj[], const double mass[], const double j6[][3],
+                        const double a2[][3], const double v[][3], const double x[][3])
+{
+    if (n < 0 || (n > 0 && (!address || !index || !tj || !mass || !j6 || !a2 || !v || !x)))
+        return G6_EINVAL;
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (c->n_jst + n > c->jst_cap) {
+        int rc = ensure_jstage(*c, c->n_jst + n < c->cap ? c->n_jst + n : c->cap);
+        if (rc)
+            return rc;
+    }
+    for (int k = 0; k < n; ++k) {
+        int rc = g6_set_j_particle(cid, address[k], index[k], tj[k], 0.0, mass[k], nullptr,
+                                   j6[k], a2[k], v[k], x[k]);
+        if (rc)
+            return rc;
+    }
+    return 0;
+}
+
+int g6x_set_j_dev(int cid, int n, const g6x_jrec *d_rec)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (n < 0 || (n > 0 && !d_rec) || c->pending)
+        return G6_EINVAL;
+    int rc = flush_jstage(*c);
+    if (rc)
+        return rc;
+    if (n == 0)
+        return 0;
+    cudaError_t e;
+    {
+        PhaseTimer pt(*c, PH_SCATTER);
+        e = g6::launch_scatter(d_rec, n, c->js, c->stream);
+    }
+    if (e != cudaSuccess)
+        return cuda_err(e);
+    c->launches += 1;
+    c->ver += 1;
+    return 0;
+}
+
+int g6x_calc_dev(int cid, double ti, int nj, int ni, const g6x_irec *d_irec, double eps2,
+                 int nl, g6x_out *d_out)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (c->pending || nj < 0 || nj > c->cap || ni < 0 || check_eps2(eps2)
+        || !std::isfinite(ti) || (ni > 0 && (!d_irec || !d_out)))
+        return G6_EINVAL;
+    c->t_set = ti;
+    int rc = flush_jstage(*c);
+    if (!rc)
+        rc = predict_if_stale(*c, nj);
+    if (!rc && ni > 0)
+        rc = run_force(*c, nj, ni, d_irec, eps2, nl != 0, d_out);
+    return rc;
+}
+
+int g6x_sync(int cid)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (c->pending)
+        return G6_EBUSY;
+    cudaError_t e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost,
+                                    c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return cuda_err(e);
+    if (*c->h_err) {
+        int code = *c->h_err;
+        *c->h_err = 0;
+        cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+        return code < 0 ? code : G6_EIO;
+    }
+    return 0;
+}
+
+int g6x_get_predicted(int cid, int nj, float *hi, float *lo, float *vel, double *x64,
+                      double *v64)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (c->pending || nj < 0 || nj > c->cap)
+        return G6_EINVAL;
+    int rc = flush_jstage(*c);
+    if (!rc)
+        rc = predict_if_stale(*c, nj);
+    if (rc)
+        return rc;
+    cudaError_t e = cudaSuccess;
+    size_t f4 = sizeof(float4) * (size_t)nj, d4 = sizeof(double4) * (size_t)nj;
+    if (c->prec == G6X_PREC_DS) {
+        if (hi && e == cudaSuccess)
+            e = cudaMemcpyAsync(hi, c->pred.ph, f4, cudaMemcpyDeviceToHost, c->stream);
+        if (lo && e == cudaSuccess)
+            e = cudaMemcpyAsync(lo, c->pred.pl, f4, cudaMemcpyDeviceToHost, c->stream);
+        if (vel && e == cudaSuccess)
+            e = cudaMemcpyAsync(vel, c->pred.pv, f4, cudaMemcpyDeviceToHost, c->stream);
+    } else {
+        if (x64 && e == cudaSuccess)
+            e = cudaMemcpyAsync(x64, c->pred.p64, d4, cudaMemcpyDeviceToHost, c->stream);
+        if (v64 && e == cudaSuccess)
+            e = cudaMemcpyAsync(v64, c->pred.v64, d4, cudaMemcpyDeviceToHost, c->stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    return cuda_err(e);
+}
+
+int g6x_set_timing(int cid, int enable)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    cudaStreamSynchronize(c->stream);
+    resolve_timing(*c);
+    for (int p = 0; p < 4; ++p) {
+        c->t_ms[p] = 0.0;
+        c->t_cnt[p] = 0;
+    }
+    c->timing = enable != 0;
+    return 0;
+}
+
+int g6x_get_timing(int cid, double ms[4], long long count[4])
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return cuda_err(e);
+    resolve_timing(*c);
+    for (int p = 0; p < 4; ++p) {
+        if (ms)
+            ms[p] = c->t_ms[p];
+        if (count)
+            count[p] = c->t_cnt[p];
+    }
+    return 0;
+}
+
+int g6x_last_config(int cid, int *variant, int *ti, int *tj, int *ni_per, int *grid,
+                    int *jtiles)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    const ForceConfig &f = c->last_cfg;
+    if (variant)
+        *variant = f.variant;
+    if (ti)
+        *ti = f.ti;
+    if (tj)
+        *tj = f.tj;
+    if (ni_per)
+        *ni_per = f.nper;
+    if (grid)
+        *grid = f.grid;
+    if (jtiles)
+        *jtiles = f.jtiles;
+    return 0;
+}
+
+long long g6x_launch_count(int cid)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    return c ? c->launches : (long long)err;
+}
+
+const char *g6x_strerror(int code)
+{
+    switch (code) {
+    case G6_OK: return "ok";
+    case G6_EINVAL: return "invalid argument";
+    case G6_ENOTOPEN: return "cluster id not open";
+    case G6_EBUSY: return "cluster id busy or call out of order";
+    case G6_ENOMEM: return "out of device or pinned host memory";
+    case G6_EIO: return "CUDA runtime error";
+    case G6_ETIMEDOUT: return "device-side bounded wait timed out";
+    case G6_ENODEV: return "no usable CUDA device for this library";
+    case G6_EOVERFLOW: return "neighbour list overflow";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// g6gb_internal.h -- declarations shared by the kernels and the C-ABI layer
+// of the GRAPE-6-style force library (arXiv:0902.4463).  Not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "g6gb.h"
+
+namespace g6 {
+
+// j-particles per shared-memory tile and padding unit of j-memory.  The
+// force kernels stream j in tiles of this size; j-memory is padded to a
+// multiple of it with massless particles far away (Sect. 2.3, Fig. accMP:
+// each thread block stages j-particles in shared memory and loops over them).
+constexpr int JT = 256;
+
+// One partial result of a (work segment, i-particle) pair: sums over the
+// j-range the segment covers, in FP64 (Sect. 2.3: partial forces of the P
+// blocks are reduced on the GPU before the copy back).  72 bytes.
+struct Partial {
+    double acc[3], jerk[3], pot;  // pot accumulates +m/r; negated in K3
+    double nnr2;                  // smallest unsoftened |r|^2 seen
+    int nnj;                      // its j-slot, -1 if none
+    int pad;
+};
+
+// j-memory (the j-store), structure of arrays, capacity `cap` (multiple of JT).
+struct JStore {
+    double *x0;        // 3 planes of cap doubles: x, y, z at t0
+    double *t0;        // time of the stored state
+    float4 *v0m;       // (vx, vy, vz, m)              FP32 copy
+    float4 *a2f;       // (ax/2, ay/2, az/2, 0)         FP32 copy
+    float4 *j6f;       // (jx/6, jy/6, jz/6, 0)         FP32 copy
+    double4 *v64;      // (vx, vy, vz, m)              FP64 copy
+    double4 *a264;     // (ax/2, ay/2, az/2, 0)
+    double4 *j664;     // (jx/6, jy/6, jz/6, 0)
+    int *idx;          // particle index (-1: empty slot)
+    int cap;
+};
+
+// Predicted j-particles (force-kernel input).
+struct Pred {
+    float4 *ph;        // DS: (x_hi, y_hi, z_hi, m)
+    float4 *pl;        // DS: (x_lo, y_lo, z_lo, 0)
+    float4 *pv;        // DS: (vx, vy, vz, index bits)
+    double4 *p64;      // FP64: (x, y, z, m)
+    double4 *v64;      // FP64: (vx, vy, vz, index)
+};
+
+// A force launch: kernel variant, CTA shape and the work partition.  The
+// work line is n_itile * J (i-tile, j-tile) pairs cut into `grid` equal
+// contiguous ranges, one per CTA (Sect. 2.3: j split over the
+// multiprocessors, i split into segments, j split again for small blocks).
+struct ForceConfig {
+    int variant;       // index into the variant table
+    int ti, tj, nper;  // threads along i, along j, i-particles per thread
+    int itile;         // ti * nper
+    int grid;          // CTAs
+    int jtiles;        // J
+    int n_itile;
+    long long work;    // n_itile * J
+    int smem;          // dynamic shared memory bytes
+    int list;          // builds neighbour lists
+    int prec;          // G6X_PREC_*
+};
+
+// Shape of one compiled force-kernel variant.
+struct VariantInfo {
+    int ti, tj, nper, list, prec;
+};
+
+int variant_count();
+VariantInfo variant_info(int v);
+// Resident CTAs per SM of variant v (0 on error).
+int variant_occupancy(int v);
+// Pick a variant and grid for ni i-particles against nj_pad j-particles.
+ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
+                          int force_variant, int force_grid);
+// Number of Partial slots a launch with this configuration writes.
+size_t partial_slots(const ForceConfig &cfg);
+
+cudaError_t launch_scatter(const g6x_jrec *d_rec, int n, JStore js,
+                           cudaStream_t s);
+cudaError_t launch_init_store(JStore js, cudaStream_t s);
+cudaError_t launch_predict(int prec, JStore js, Pred p, int nj, int nj_pad,
+                           double t, int sm_count, cudaStream_t s);
+cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
+                         const g6x_irec *d_irec, int ni, double eps2,
+                         Partial *part, int *nbl_part, int *nbc_part,
+                         int *d_err, cudaStream_t s);
+cudaError_t launch_reduce(const ForceConfig &cfg, const Partial *part,
+                          const int *nbl_part, const int *nbc_part,
+                          const int *jidx, int ni, g6x_out *d_out,
+                          int *d_nbl, int *d_nblen, cudaStream_t s);
+
+}  // namespace g6

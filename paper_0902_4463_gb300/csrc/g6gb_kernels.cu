@@ -1,0 +1,943 @@
+// g6gb_kernels.cu -- sm_103a kernels of the direct-summation hot path
+// (Gaburov, Harfst & Portegies Zwart, arXiv:0902.4463):
+//
+//   K0 k_scatter      j-memory update from staged records      (Sect. 2.1)
+//   K1 k_predict_*    j-particle prediction, Eq. 1 and Eq. 2   (Sect. 2.2)
+//   K2 k_force_ds     FP32 pair forces with double-single separations,
+//                     Eq. 3, nearest neighbour, neighbour lists (Sect. 2.3, 2.5, 4)
+//   K2d k_force_64    the same in FP64
+//   K3 k_reduce       FP64 reduction of the partial forces     (Sect. 2.3)
+//
+// Work partition of K2/K2d.  The paper spreads the j-particles over the
+// multiprocessors, gives every block all i-particles, cuts i into serial
+// segments when there are too many, and splits j again inside a block when
+// the active block is small (Sect. 2.3, Figs. accGPU, accMP, accMP1).  Here
+// the (i-tile, j-tile) pairs form one work line that is cut into `grid`
+// equal contiguous ranges, one per resident CTA, so every SM gets the same
+// number of pair tiles whatever m and n are.  A CTA that crosses an i-tile
+// boundary writes one partial per i-tile it touched; K3 sums the partials of
+// each i in FP64.  Inside a CTA, TJ thread groups split each j-tile when m is
+// small (the split-j of Fig. accMP1).
+//
+// j-tiles are staged in shared memory by bulk asynchronous copies
+// (cp.async.bulk, completion on an mbarrier) issued by one thread, in a
+// NSTAGE-deep ring, so the loads of later tiles overlap the pair loop.  Every
+// mbarrier wait is bounded; on expiry the kernel records G6_ETIMEDOUT in the
+// error word, waits (bounded) for its own copies in flight and returns.
+#include "g6gb_internal.h"
+
+#include <climits>
+#include <cmath>
+
+namespace g6 {
+
+namespace {
+
+constexpr int NSTAGE = 3;
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s per mbarrier wait
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
+                 :: "r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of an mbarrier for at most WAIT_LIMIT_NS.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        for (int k = 0; k < 32; ++k)
+            if (mbar_try_wait(bar, parity))
+                return true;
+        if (global_ns() - t0 > WAIT_LIMIT_NS)
+            return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src,
+                                         uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes"
+                 " [%0], [%1], %2, [%3];"
+                 :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Knuth's TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Work line helpers: CTA c owns [begin(c), begin(c+1)).
+__device__ __forceinline__ long long work_begin(long long c, long long W, long long G)
+{
+    return c * W / G;
+}
+
+// Largest c with work_begin(c) <= p, i.e. the CTA that owns position p.
+__device__ __forceinline__ long long work_owner(long long p, long long W, long long G)
+{
+    return ((p + 1) * G - 1) / W;
+}
+
+// Far-away massless stand-in for padding and empty j-slots: every pair term
+// it produces is exactly zero (r^2 overflows to +inf, rsqrt(+inf) = 0).
+constexpr double FAR = 1e30;
+
+}  // namespace
+
+// ----------------------------------------------------------------- K0 ---
+
+__global__ void k_init_store(JStore js)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < js.cap;
+         k += gridDim.x * blockDim.x) {
+        js.x0[k] = FAR;
+        js.x0[js.cap + k] = FAR;
+        js.x0[2 * js.cap + k] = FAR;
+        js.t0[k] = 0.0;
+        js.v0m[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        js.a2f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        js.j6f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        js.v64[k] = make_double4(0.0, 0.0, 0.0, 0.0);
+        js.a264[k] = make_double4(0.0, 0.0, 0.0, 0.0);
+        js.j664[k] = make_double4(0.0, 0.0, 0.0, 0.0);
+        js.idx[k] = -1;
+    }
+}
+
+// j-memory update (Sect. 2.1: only the corrected particles travel to the
+// GPU each step).  One thread per record; addresses within one launch are
+// distinct (the host staging keeps one record per address).
+__global__ void k_scatter(const g6x_jrec *__restrict__ rec, int n, JStore js)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n)
+        return;
+    const g6x_jrec &r = rec[k];
+    int a = r.address;
+    if (a < 0 || a >= js.cap)
+        return;
+    js.x0[a] = r.x[0];
+    js.x0[js.cap + a] = r.x[1];
+    js.x0[2 * js.cap + a] = r.x[2];
+    js.t0[a] = r.tj;
+    js.v0m[a] = make_float4((float)r.v[0], (float)r.v[1], (float)r.v[2], (float)r.mass);
+    js.a2f[a] = make_float4((float)r.a2[0], (float)r.a2[1], (float)r.a2[2], 0.f);
+    js.j6f[a] = make_float4((float)r.j6[0], (float)r.j6[1], (float)r.j6[2], 0.f);
+    js.v64[a] = make_double4(r.v[0], r.v[1], r.v[2], r.mass);
+    js.a264[a] = make_double4(r.a2[0], r.a2[1], r.a2[2], 0.0);
+    js.j664[a] = make_double4(r.j6[0], r.j6[1], r.j6[2], 0.0);
+    js.idx[a] = r.index;
+}
+
+// ----------------------------------------------------------------- K1 ---
+
+// Eq. 1 and Eq. 2 with the DS position of Sect. 2.2: the Taylor increment
+// dt (v + dt (a/2 + dt j/6)) is formed in FP32, added to the FP64 x0, and the
+// sum is split into hi = rn(x), lo = rn(x - hi).  The velocity is FP32.
+__global__ void __launch_bounds__(256) k_predict_ds(JStore js, Pred p, int nj,
+                                                    int nj_pad, double t)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nj_pad;
+         k += gridDim.x * blockDim.x) {
+        if (k < nj) {
+            double dt = t - js.t0[k];
+            float h = (float)dt;
+            float4 v = js.v0m[k], a = js.a2f[k], j = js.j6f[k];
+            float dx = h * fmaf(h, fmaf(h, j.x, a.x), v.x);
+            float dy = h * fmaf(h, fmaf(h, j.y, a.y), v.y);
+            float dz = h * fmaf(h, fmaf(h, j.z, a.z), v.z);
+            double px = js.x0[k] + (double)dx;
+            double py = js.x0[js.cap + k] + (double)dy;
+            double pz = js.x0[2 * js.cap + k] + (double)dz;
+            float hx = __double2float_rn(px), hy = __double2float_rn(py),
+                  hz = __double2float_rn(pz);
+            float lx = __double2float_rn(px - (double)hx);
+            float ly = __double2float_rn(py - (double)hy);
+            float lz = __double2float_rn(pz - (double)hz);
+            float h3 = 3.0f * h;
+            float vx = fmaf(h, fmaf(h3, j.x, 2.0f * a.x), v.x);
+            float vy = fmaf(h, fmaf(h3, j.y, 2.0f * a.y), v.y);
+            float vz = fmaf(h, fmaf(h3, j.z, 2.0f * a.z), v.z);
+            p.ph[k] = make_float4(hx, hy, hz, v.w);
+            p.pl[k] = make_float4(lx, ly, lz, 0.f);
+            p.pv[k] = make_float4(vx, vy, vz, __int_as_float(js.idx[k]));
+        } else {
+            p.ph[k] = make_float4((float)FAR, (float)FAR, (float)FAR, 0.f);
+            p.pl[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            p.pv[k] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+        }
+    }
+}
+
+// Eq. 1 and Eq. 2 entirely in FP64.
+__global__ void __launch_bounds__(256) k_predict_64(JStore js, Pred p, int nj,
+                                                    int nj_pad, double t)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nj_pad;
+         k += gridDim.x * blockDim.x) {
+        if (k < nj) {
+            double h = t - js.t0[k];
+            double4 v = js.v64[k], a = js.a264[k], j = js.j664[k];
+            double px = js.x0[k] + h * fma(h, fma(h, j.x, a.x), v.x);
+            double py = js.x0[js.cap + k] + h * fma(h, fma(h, j.y, a.y), v.y);
+            double pz = js.x0[2 * js.cap + k] + h * fma(h, fma(h, j.z, a.z), v.z);
+            double h3 = 3.0 * h;
+            double vx = fma(h, fma(h3, j.x, 2.0 * a.x), v.x);
+            double vy = fma(h, fma(h3, j.y, 2.0 * a.y), v.y);
+            double vz = fma(h, fma(h3, j.z, 2.0 * a.z), v.z);
+            p.p64[k] = make_double4(px, py, pz, v.w);
+            p.v64[k] = make_double4(vx, vy, vz, (double)js.idx[k]);
+        } else {
+            p.p64[k] = make_double4(FAR, FAR, FAR, 0.0);
+            p.v64[k] = make_double4(0.0, 0.0, 0.0, -1.0);
+        }
+    }
+}
+
+// ----------------------------------------------------------------- K2 ---
+
+struct ForceArgs {
+    const float4 *ph, *pl, *pv;       // DS predicted j
+    const double4 *p64, *v64;         // FP64 predicted j
+    const g6x_irec *irec;
+    Partial *part;
+    int *nbl;                         // list entries  [slot][maxnb]
+    int *nbc;                         // list counts   [slot]
+    int *err;
+    long long W;
+    int J;
+    int ni;
+    double eps2;
+};
+
+// Pair forces on NI i-particles per thread in FP32 with the DS separation of
+// Eq. 3 (Sect. 2.3).  Per pair:
+//   dx   = (xj_hi - xi_hi) + (xj_lo - xi_lo)                       Eq. 3
+//   r2u  = |dx|^2  (nearest neighbour and lists use it unsoftened)
+//   key  = r2u, or +inf for the i-particle's own j (index match)
+//   1/r  = rsqrt(key + eps2)            (+inf -> 0: the pair adds nothing)
+//   acc  += m r^-3 dx
+//   jerk += m r^-3 (dv - 3 (dx.dv) r^-2 dx)
+//   pot  += m r^-1                      (negated in K3)
+// Sums run in FP32 over each j-tile and are folded into compensated
+// (TwoSum) FP32 pairs every ~128 pairs, so the rounding of long sums does
+// not grow with n; the pairs are combined in FP64 when partials are written.
+template <int TI, int TJ, int NI, bool LIST>
+__global__ void __launch_bounds__(TI * TJ) k_force_ds(const ForceArgs a)
+{
+    constexpr int NT = TI * TJ;
+    constexpr int ITILE = TI * NI;
+    constexpr int JPT = JT / TJ;
+    constexpr int FLUSH = (128 + JPT - 1) / JPT;
+    static_assert(TJ == 1 || NI == 1, "split-j variants carry one i per thread");
+    static_assert(!LIST || TJ == 1, "neighbour lists need whole j-tiles per thread");
+    static_assert(JT % TJ == 0, "j-tile must split evenly");
+
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    float4 *stage_buf = reinterpret_cast<float4 *>(dyn_smem);
+    __shared__ __align__(8) uint64_t bar[NSTAGE];
+    __shared__ int s_abort;
+    __shared__ double red[TJ > 1 ? 8 * NT : 1];
+    __shared__ int redj[TJ > 1 ? NT : 1];
+
+    const int tid = threadIdx.x;
+    const int ti = tid % TI, tj = tid / TI;
+    const long long G = gridDim.x, c = blockIdx.x;
+    const long long wb = work_begin(c, a.W, G), we = work_begin(c + 1, a.W, G);
+    const int ntile = (int)(we - wb);
+    if (ntile <= 0)
+        return;
+
+    if (tid == 0) {
+        for (int s = 0; s < NSTAGE; ++s)
+            mbar_init(&bar[s], 1);
+        fence_barrier_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    auto issue = [&](int q) {
+        long long p = wb + q;
+        int jt = (int)(p % a.J);
+        int s = q % NSTAGE;
+        float4 *dst = stage_buf + (size_t)s * 3 * JT;
+        mbar_expect_tx(&bar[s], 3u * JT * sizeof(float4));
+        bulk_g2s(dst, a.ph + (size_t)jt * JT, JT * sizeof(float4), &bar[s]);
+        bulk_g2s(dst + JT, a.pl + (size_t)jt * JT, JT * sizeof(float4), &bar[s]);
+        bulk_g2s(dst + 2 * JT, a.pv + (size_t)jt * JT, JT * sizeof(float4), &bar[s]);
+    };
+    if (tid == 0)
+        for (int q = 0; q < NSTAGE && q < ntile; ++q)
+            issue(q);
+
+    const float eps2 = (float)a.eps2;
+    float xh[NI][3], xl[NI][3], vi[NI][3], h2[NI];
+    int iid[NI];
+    float ta[NI][7], hs[NI][7], ls[NI][7];
+    float nnr[NI];
+    int nnj[NI], nbn[NI];
+    int cur_t = -1;
+    int since_flush = 0;
+
+    auto flush = [&]() {
+#pragma unroll
+        for (int k = 0; k < NI; ++k)
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                float s, e;
+                two_sum(hs[k][q], ta[k][q], s, e);
+                hs[k][q] = s;
+                ls[k][q] = __fadd_rn(ls[k][q], e);
+                ta[k][q] = 0.f;
+            }
+    };
+
+    auto load_i = [&](int t) {
+#pragma unroll
+        for (int k = 0; k < NI; ++k) {
+            int il = k * TI + ti;
+            long long gi = (long long)t * ITILE + il;
+            if (gi < a.ni) {
+                const g6x_irec &r = a.irec[gi];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    double x = r.x[d];
+                    float hi = __double2float_rn(x);
+                    xh[k][d] = hi;
+                    xl[k][d] = __double2float_rn(x - (double)hi);
+                    vi[k][d] = (float)r.v[d];
+                }
+                h2[k] = (float)r.h2;
+                iid[k] = r.index;
+            } else {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    xh[k][d] = 0.f;
+                    xl[k][d] = 0.f;
+                    vi[k][d] = 0.f;
+                }
+                h2[k] = 0.f;
+                iid[k] = -2;
+            }
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                ta[k][q] = 0.f;
+                hs[k][q] = 0.f;
+                ls[k][q] = 0.f;
+            }
+            nnr[k] = __int_as_float(0x7f800000);
+            nnj[k] = -1;
+            nbn[k] = 0;
+        }
+        since_flush = 0;
+    };
+
+    auto finalize = [&](int t) {
+        flush();
+        const long long seg = c + t;
+        if constexpr (TJ == 1) {
+#pragma unroll
+            for (int k = 0; k < NI; ++k) {
+                int il = k * TI + ti;
+                Partial *P = a.part + (size_t)seg * ITILE + il;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    P->acc[d] = (double)hs[k][d] + (double)ls[k][d];
+                    P->jerk[d] = (double)hs[k][3 + d] + (double)ls[k][3 + d];
+                }
+                P->pot = (double)hs[k][6] + (double)ls[k][6];
+                P->nnr2 = (double)nnr[k];
+                P->nnj = nnj[k];
+                if constexpr (LIST)
+                    a.nbc[(size_t)seg * ITILE + il] = nbn[k];
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 7; ++q)
+                red[q * NT + tid] = (double)hs[0][q] + (double)ls[0][q];
+            red[7 * NT + tid] = (double)nnr[0];
+            redj[tid] = nnj[0];
+            __syncthreads();
+            if (tid < TI) {
+                double s[7];
+#pragma unroll
+                for (int q = 0; q < 7; ++q)
+                    s[q] = 0.0;
+                double br = red[7 * NT + tid];
+                int bj = redj[tid];
+                for (int g = 0; g < TJ; ++g) {
+                    int o = g * TI + tid;
+#pragma unroll
+                    for (int q = 0; q < 7; ++q)
+                        s[q] += red[q * NT + o];
+                    double r = red[7 * NT + o];
+                    int jj = redj[o];
+                    if (r < br || (r == br && jj >= 0 && (bj < 0 || jj < bj))) {
+                        br = r;
+                        bj = jj;
+                    }
+                }
+                Partial *P = a.part + (size_t)seg * ITILE + tid;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    P->acc[d] = s[d];
+                    P->jerk[d] = s[3 + d];
+                }
+                P->pot = s[6];
+                P->nnr2 = br;
+                P->nnj = bj;
+            }
+            __syncthreads();
+        }
+    };
+
+    for (int q = 0; q < ntile; ++q) {
+        const long long p = wb + q;
+        const int t = (int)(p / a.J);
+        const int jt = (int)(p - (long long)t * a.J);
+        if (t != cur_t) {
+            if (cur_t >= 0)
+                finalize(cur_t);
+            load_i(t);
+            cur_t = t;
+        }
+        const int s = q % NSTAGE;
+        const uint32_t par = (uint32_t)((q / NSTAGE) & 1);
+        const bool ready = mbar_wait_bounded(&bar[s], par);
+        if (!ready) {
+            s_abort = 1;
+        } else {
+            const float4 *sph = stage_buf + (size_t)s * 3 * JT;
+            const float4 *spl = sph + JT;
+            const float4 *spv = spl + JT;
+            const int jbase = jt * JT;
+#pragma unroll 2
+            for (int kk = 0; kk < JPT; ++kk) {
+                const int jj = tj + kk * TJ;
+                const float4 pj = sph[jj];
+                const float4 lj = spl[jj];
+                const float4 vj = spv[jj];
+                const int jid = __float_as_int(vj.w);
+#pragma unroll
+                for (int k = 0; k < NI; ++k) {
+                    const float dx = (pj.x - xh[k][0]) + (lj.x - xl[k][0]);
+                    const float dy = (pj.y - xh[k][1]) + (lj.y - xl[k][1]);
+                    const float dz = (pj.z - xh[k][2]) + (lj.z - xl[k][2]);
+                    const float ux = vj.x - vi[k][0];
+                    const float uy = vj.y - vi[k][1];
+                    const float uz = vj.z - vi[k][2];
+                    const float r2u = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    const float key = (jid == iid[k]) ? __int_as_float(0x7f800000) : r2u;
+                    const float ri = rsqrt_approx(key + eps2);
+                    const float rv = fmaf(dz, uz, fmaf(dy, uy, dx * ux));
+                    const float ri2 = ri * ri;
+                    const float mr = pj.w * ri;
+                    const float mr3 = mr * ri2;
+                    const float sc = -3.0f * (rv * ri2);
+                    ta[k][6] += mr;
+                    ta[k][0] = fmaf(mr3, dx, ta[k][0]);
+                    ta[k][1] = fmaf(mr3, dy, ta[k][1]);
+                    ta[k][2] = fmaf(mr3, dz, ta[k][2]);
+                    ta[k][3] = fmaf(mr3, fmaf(sc, dx, ux), ta[k][3]);
+                    ta[k][4] = fmaf(mr3, fmaf(sc, dy, uy), ta[k][4]);
+                    ta[k][5] = fmaf(mr3, fmaf(sc, dz, uz), ta[k][5]);
+                    if (key < nnr[k]) {
+                        nnr[k] = key;
+                        nnj[k] = jbase + jj;
+                    }
+                    if constexpr (LIST) {
+                        if (key < h2[k]) {
+                            if (nbn[k] < G6_MAXNB) {
+                                int il = k * TI + ti;
+                                a.nbl[((size_t)(c + t) * ITILE + il) * G6_MAXNB + nbn[k]] =
+                                    jbase + jj;
+                            }
+                            ++nbn[k];
+                        }
+                    }
+                }
+            }
+            if (++since_flush >= FLUSH) {
+                flush();
+                since_flush = 0;
+            }
+        }
+        __syncthreads();
+        if (s_abort) {
+            // Give up: wait (bounded) for this CTA's copies still in flight so
+            // none lands in shared memory after exit, then report.
+            if (tid == 0) {
+                for (int r = q; r < q + NSTAGE && r < ntile; ++r)
+                    mbar_wait_bounded(&bar[r % NSTAGE], (uint32_t)((r / NSTAGE) & 1));
+                atomicCAS(a.err, 0, G6_ETIMEDOUT);
+            }
+            return;
+        }
+        if (tid == 0 && q + NSTAGE < ntile)
+            issue(q + NSTAGE);
+    }
+    finalize(cur_t);
+}
+
+// The same pair sum entirely in FP64, one i-particle per thread, j-tiles
+// staged in shared memory by plain cooperative loads.
+template <bool LIST>
+__global__ void __launch_bounds__(128) k_force_64(const ForceArgs a)
+{
+    constexpr int TI = 128;
+    __shared__ double4 sp[JT], sv[JT];
+    const int tid = threadIdx.x;
+    const long long G = gridDim.x, c = blockIdx.x;
+    const long long wb = work_begin(c, a.W, G), we = work_begin(c + 1, a.W, G);
+    if (we <= wb)
+        return;
+    double xi[3] = {0, 0, 0}, vi[3] = {0, 0, 0}, h2 = 0.0;
+    int iid = -2;
+    double s[7];
+    double nnr = 0.0;
+    int nnj = -1, nbn = 0;
+    int cur_t = -1;
+    const double INF = __longlong_as_double(0x7ff0000000000000ll);
+
+    auto finalize = [&](int t) {
+        const long long seg = c + t;
+        Partial *P = a.part + (size_t)seg * TI + tid;
+        for (int d = 0; d < 3; ++d) {
+            P->acc[d] = s[d];
+            P->jerk[d] = s[3 + d];
+        }
+        P->pot = s[6];
+        P->nnr2 = nnr;
+        P->nnj = nnj;
+        if constexpr (LIST)
+            a.nbc[(size_t)seg * TI + tid] = nbn;
+    };
+
+    for (long long p = wb; p < we; ++p) {
+        const int t = (int)(p / a.J);
+        const int jt = (int)(p - (long long)t * a.J);
+        if (t != cur_t) {
+            if (cur_t >= 0)
+                finalize(cur_t);
+            long long gi = (long long)t * TI + tid;
+            if (gi < a.ni) {
+                const g6x_irec &r = a.irec[gi];
+                for (int d = 0; d < 3; ++d) {
+                    xi[d] = r.x[d];
+                    vi[d] = r.v[d];
+                }
+                h2 = r.h2;
+                iid = r.index;
+            } else {
+                iid = -2;
+            }
+            for (int q = 0; q < 7; ++q)
+                s[q] = 0.0;
+            nnr = INF;
+            nnj = -1;
+            nbn = 0;
+            cur_t = t;
+        }
+        __syncthreads();
+        for (int k = tid; k < JT; k += TI) {
+            sp[k] = a.p64[(size_t)jt * JT + k];
+            sv[k] = a.v64[(size_t)jt * JT + k];
+        }
+        __syncthreads();
+        const int jbase = jt * JT;
+        for (int jj = 0; jj < JT; ++jj) {
+            const double4 pj = sp[jj], vj = sv[jj];
+            const double dx = pj.x - xi[0], dy = pj.y - xi[1], dz = pj.z - xi[2];
+            const double ux = vj.x - vi[0], uy = vj.y - vi[1], uz = vj.z - vi[2];
+            const double r2u = dx * dx + dy * dy + dz * dz;
+            const double key = ((int)vj.w == iid) ? INF : r2u;
+            const double ri = rsqrt(key + a.eps2);
+            const double rv = dx * ux + dy * uy + dz * uz;
+            const double ri2 = ri * ri;
+            const double mr = pj.w * ri;
+            const double mr3 = mr * ri2;
+            const double sc = -3.0 * rv * ri2;
+            s[6] += mr;
+            s[0] += mr3 * dx;
+            s[1] += mr3 * dy;
+            s[2] += mr3 * dz;
+            s[3] += mr3 * (ux + sc * dx);
+            s[4] += mr3 * (uy + sc * dy);
+            s[5] += mr3 * (uz + sc * dz);
+            if (key < nnr) {
+                nnr = key;
+                nnj = jbase + jj;
+            }
+            if constexpr (LIST) {
+                if (key < h2) {
+                    if (nbn < G6_MAXNB)
+                        a.nbl[((size_t)(c + t) * TI + tid) * G6_MAXNB + nbn] = jbase + jj;
+                    ++nbn;
+                }
+            }
+        }
+    }
+    finalize(cur_t);
+}
+
+// ----------------------------------------------------------------- K3 ---
+
+struct ReduceArgs {
+    const Partial *part;
+    const int *nbl, *nbc;
+    const int *jidx;
+    g6x_out *out;
+    int *nbl_out, *nblen_out;
+    long long W;
+    int J, G, ni, itile, list;
+};
+
+// One warp per i-particle: lanes take the partials of the CTAs that touched
+// its i-tile, sum them in FP64 and combine with warp shuffles; the nearest
+// neighbour is the smallest |r|^2, ties to the lower j-slot (Sect. 2.3, 2.5).
+// Neighbour lists are concatenated in segment order, which is ascending j,
+// and truncated at G6_MAXNB (Sect. 4).
+__global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= a.ni)
+        return;
+    const int t = (int)(i / a.itile), il = (int)(i % a.itile);
+    const long long p0 = (long long)t * a.J, p1 = p0 + a.J;
+    const long long clo = work_owner(p0, a.W, a.G), chi = work_owner(p1 - 1, a.W, a.G);
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
+    double br = __longlong_as_double(0x7ff0000000000000ll);
+    int bj = -1;
+    for (long long cc = clo + lane; cc <= chi; cc += 32) {
+        long long b = max(work_begin(cc, a.W, a.G), p0);
+        long long e = min(work_begin(cc + 1, a.W, a.G), p1);
+        if (e <= b)
+            continue;
+        const Partial &P = a.part[(size_t)(cc + t) * a.itile + il];
+        for (int d = 0; d < 3; ++d) {
+            s[d] += P.acc[d];
+            s[3 + d] += P.jerk[d];
+        }
+        s[6] += P.pot;
+        if (P.nnj >= 0 && (P.nnr2 < br || (P.nnr2 == br && (bj < 0 || P.nnj < bj)))) {
+            br = P.nnr2;
+            bj = P.nnj;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q)
+            s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+        double r = __shfl_xor_sync(0xffffffffu, br, off);
+        int jj = __shfl_xor_sync(0xffffffffu, bj, off);
+        if (jj >= 0 && (bj < 0 || r < br || (r == br && jj < bj))) {
+            br = r;
+            bj = jj;
+        }
+    }
+    if (lane == 0) {
+        g6x_out o;
+        for (int d = 0; d < 3; ++d) {
+            o.acc[d] = s[d];
+            o.jerk[d] = s[3 + d];
+        }
+        o.pot = -s[6];
+        o.nnb = bj >= 0 ? a.jidx[bj] : -1;
+        o.nnr2 = bj >= 0 ? (float)br : __int_as_float(0x7f800000);
+        a.out[i] = o;
+    }
+    if (!a.list)
+        return;
+    long long base = 0, total = 0;
+    for (long long c0 = clo; c0 <= chi; c0 += 32) {
+        long long cc = c0 + lane;
+        int cnt = 0;
+        if (cc <= chi) {
+            long long b = max(work_begin(cc, a.W, a.G), p0);
+            long long e = min(work_begin(cc + 1, a.W, a.G), p1);
+            if (e > b)
+                cnt = a.nbc[(size_t)(cc + t) * a.itile + il];
+        }
+        int kept = min(cnt, G6_MAXNB);
+        int incl = kept;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off)
+                incl += v;
+        }
+        long long pos0 = base + incl - kept;
+        const int *src = a.nbl + ((size_t)(cc + t) * a.itile + il) * G6_MAXNB;
+        for (int e = 0; e < kept && pos0 + e < G6_MAXNB; ++e)
+            a.nbl_out[(size_t)i * G6_MAXNB + pos0 + e] = a.jidx[src[e]];
+        long long ctot = cnt;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            ctot += __shfl_xor_sync(0xffffffffu, ctot, off);
+        total += ctot;
+        base += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0)
+        a.nblen_out[i] = (int)min(total, (long long)INT_MAX);
+}
+
+// ------------------------------------------------------------ variants ---
+
+namespace {
+
+using ForceFn = void (*)(const ForceArgs);
+
+struct Variant {
+    VariantInfo info;
+    ForceFn fn;
+    int threads;
+    int smem;
+};
+
+constexpr int DS_SMEM = NSTAGE * 3 * JT * (int)sizeof(float4);
+
+const Variant kVariants[] = {
+    {{128, 1, 4, 0, G6X_PREC_DS}, k_force_ds<128, 1, 4, false>, 128, DS_SMEM},
+    {{128, 1, 2, 0, G6X_PREC_DS}, k_force_ds<128, 1, 2, false>, 128, DS_SMEM},
+    {{128, 1, 1, 0, G6X_PREC_DS}, k_force_ds<128, 1, 1, false>, 128, DS_SMEM},
+    {{32, 8, 1, 0, G6X_PREC_DS}, k_force_ds<32, 8, 1, false>, 256, DS_SMEM},
+    {{16, 16, 1, 0, G6X_PREC_DS}, k_force_ds<16, 16, 1, false>, 256, DS_SMEM},
+    {{128, 1, 1, 1, G6X_PREC_DS}, k_force_ds<128, 1, 1, true>, 128, DS_SMEM},
+    {{32, 1, 1, 1, G6X_PREC_DS}, k_force_ds<32, 1, 1, true>, 32, DS_SMEM},
+    {{128, 1, 1, 0, G6X_PREC_FP64}, k_force_64<false>, 128, 0},
+    {{128, 1, 1, 1, G6X_PREC_FP64}, k_force_64<true>, 128, 0},
+};
+constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+
+int g_occ[kNumVariants];
+bool g_smem_set[kNumVariants];
+
+cudaError_t prepare_variant(int v)
+{
+    if (!g_smem_set[v]) {
+        if (kVariants[v].smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(
+                kVariants[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                kVariants[v].smem);
+            if (e != cudaSuccess)
+                return e;
+        }
+        g_smem_set[v] = true;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+int variant_count() { return kNumVariants; }
+
+VariantInfo variant_info(int v) { return kVariants[v].info; }
+
+int variant_occupancy(int v)
+{
+    if (v < 0 || v >= kNumVariants)
+        return 0;
+    if (g_occ[v] == 0) {
+        if (prepare_variant(v) != cudaSuccess)
+            return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &n, kVariants[v].fn, kVariants[v].threads, kVariants[v].smem) != cudaSuccess)
+            return 0;
+        g_occ[v] = n;
+    }
+    return g_occ[v];
+}
+
+ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
+                          int force_variant, int force_grid)
+{
+    int v;
+    if (force_variant >= 0 && force_variant < kNumVariants) {
+        v = force_variant;
+    } else if (prec == G6X_PREC_FP64) {
+        v = list ? 8 : 7;
+    } else if (list) {
+        v = ni <= 32 ? 6 : 5;
+    } else if (ni <= 16) {
+        v = 4;
+    } else if (ni <= 32) {
+        v = 3;
+    } else if (ni <= 4096) {
+        v = 2;
+    } else if (ni <= 16384) {
+        v = 1;
+    } else {
+        v = 0;
+    }
+    const VariantInfo &vi = kVariants[v].info;
+    ForceConfig c{};
+    c.variant = v;
+    c.ti = vi.ti;
+    c.tj = vi.tj;
+    c.nper = vi.nper;
+    c.itile = vi.ti * vi.nper;
+    c.jtiles = nj_pad / JT;
+    c.n_itile = (ni + c.itile - 1) / c.itile;
+    c.work = (long long)c.n_itile * c.jtiles;
+    c.smem = kVariants[v].smem;
+    c.list = vi.list;
+    c.prec = vi.prec;
+    int occ = variant_occupancy(v);
+    if (occ < 1)
+        occ = 1;
+    long long g = force_grid > 0 ? force_grid : (long long)sm_count * occ;
+    if (g > c.work)
+        g = c.work;
+    if (g < 1)
+        g = 1;
+    c.grid = (int)g;
+    return c;
+}
+
+size_t partial_slots(const ForceConfig &cfg)
+{
+    return (size_t)(cfg.grid + cfg.n_itile) * cfg.itile;
+}
+
+cudaError_t launch_init_store(JStore js, cudaStream_t s)
+{
+    int blocks = (js.cap + 255) / 256;
+    if (blocks > 65535)
+        blocks = 65535;
+    k_init_store<<<blocks, 256, 0, s>>>(js);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const g6x_jrec *d_rec, int n, JStore js, cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    k_scatter<<<(n + 127) / 128, 128, 0, s>>>(d_rec, n, js);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predict(int prec, JStore js, Pred p, int nj, int nj_pad,
+                           double t, int sm_count, cudaStream_t s)
+{
+    int blocks = (nj_pad + 255) / 256;
+    int cap = sm_count * 8;
+    if (blocks > cap)
+        blocks = cap;
+    if (blocks < 1)
+        blocks = 1;
+    if (prec == G6X_PREC_FP64)
+        k_predict_64<<<blocks, 256, 0, s>>>(js, p, nj, nj_pad, t);
+    else
+        k_predict_ds<<<blocks, 256, 0, s>>>(js, p, nj, nj_pad, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
+                         const g6x_irec *d_irec, int ni, double eps2,
+                         Partial *part, int *nbl_part, int *nbc_part,
+                         int *d_err, cudaStream_t s)
+{
+    if (cfg.work <= 0)
+        return cudaSuccess;
+    cudaError_t e = prepare_variant(cfg.variant);
+    if (e != cudaSuccess)
+        return e;
+    ForceArgs a;
+    a.ph = p.ph;
+    a.pl = p.pl;
+    a.pv = p.pv;
+    a.p64 = p.p64;
+    a.v64 = p.v64;
+    a.irec = d_irec;
+    a.part = part;
+    a.nbl = nbl_part;
+    a.nbc = nbc_part;
+    a.err = d_err;
+    a.W = cfg.work;
+    a.J = cfg.jtiles;
+    a.ni = ni;
+    a.eps2 = eps2;
+    const Variant &v = kVariants[cfg.variant];
+    v.fn<<<cfg.grid, v.threads, v.smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const ForceConfig &cfg, const Partial *part,
+                          const int *nbl_part, const int *nbc_part,
+                          const int *jidx, int ni, g6x_out *d_out, int *d_nbl,
+                          int *d_nblen, cudaStream_t s)
+{
+    if (ni <= 0)
+        return cudaSuccess;
+    ReduceArgs a;
+    a.part = part;
+    a.nbl = nbl_part;
+    a.nbc = nbc_part;
+    a.jidx = jidx;
+    a.out = d_out;
+    a.nbl_out = d_nbl;
+    a.nblen_out = d_nblen;
+    a.W = cfg.work;
+    a.J = cfg.jtiles;
+    a.G = cfg.grid;
+    a.ni = ni;
+    a.itile = cfg.itile;
+    a.list = cfg.list;
+    long long threads = (long long)ni * 32;
+    int blocks = (int)((threads + 255) / 256);
+    k_reduce<<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace g6

@@ -1,0 +1,376 @@
+"""Thin ctypes binding of ``libg6gb.so`` (declared in ``include/g6gb.h``).
+
+Argument marshalling only: every function converts numpy arrays (or device
+pointers) to the C types and calls the C entry point of the same name; all
+work of the hot path happens in the CUDA library.  There is no fallback: if
+the library is missing or cannot load, ``lib()`` raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libg6gb.so")
+
+G6_OK = 0
+G6_EINVAL = -22
+G6_ENOTOPEN = -19
+G6_EBUSY = -16
+G6_ENOMEM = -12
+G6_EIO = -5
+G6_ETIMEDOUT = -110
+G6_ENODEV = -6
+G6_EOVERFLOW = 1
+G6_MAXNB = 256
+G6_MAX_CLUSTERS = 16
+G6X_PREC_DS = 0
+G6X_PREC_FP64 = 1
+
+# Record layouts of the device-resident entry points (g6x_jrec, g6x_irec,
+# g6x_out in g6gb.h).
+JREC = np.dtype([("x", "<f8", 3), ("v", "<f8", 3), ("a2", "<f8", 3), ("j6", "<f8", 3),
+                 ("mass", "<f8"), ("tj", "<f8"), ("address", "<i4"), ("index", "<i4")])
+IREC = np.dtype([("x", "<f8", 3), ("v", "<f8", 3), ("h2", "<f8"), ("index", "<i4"),
+                 ("pad", "<i4")])
+OUT = np.dtype([("acc", "<f8", 3), ("jerk", "<f8", 3), ("pot", "<f8"), ("nnb", "<i4"),
+                ("nnr2", "<f4")])
+assert JREC.itemsize == 120 and IREC.itemsize == 64 and OUT.itemsize == 64
+
+# Every symbol include/g6gb.h declares.
+EXPORTS = [
+    "g6_open", "g6_close", "g6_npipes", "g6_set_tunit", "g6_set_xunit", "g6_set_ti",
+    "g6_set_j_particle", "g6calc_firsthalf", "g6calc_lasthalf", "g6calc_lasthalf2",
+    "g6_read_neighbour_list", "g6_get_neighbour_list", "g6x_open_ex",
+    "g6x_set_precision", "g6x_set_ni_max", "g6x_set_stream", "g6x_set_allocator",
+    "g6x_set_j_particles", "g6x_strerror", "g6x_set_j_dev", "g6x_calc_dev",
+    "g6x_sync", "g6x_set_variant", "g6x_get_predicted", "g6x_last_config",
+    "g6x_launch_count", "g6x_set_timing", "g6x_get_timing", "g6h_create", "g6h_run", "g6h_get_state", "g6h_energy",
+    "g6h_stats", "g6h_destroy",
+]
+
+_lib = None
+P = C.c_void_p
+I = C.c_int
+D = C.c_double
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class G6Error(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, strerror(code) if _lib else "", code))
+
+
+def lib():
+    """Load libg6gb.so (raises if it was not built: no CPU fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libg6gb.so is not built; run paper_0902_4463_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        sig = {
+            "g6_open": (I, [I]), "g6_close": (I, [I]), "g6_npipes": (I, []),
+            "g6_set_tunit": (I, [I]), "g6_set_xunit": (I, [I]), "g6_set_ti": (I, [I, D]),
+            "g6_set_j_particle": (I, [I, I, I, D, D, D, P, P, P, P, P]),
+            "g6calc_firsthalf": (None, [I, I, I, P, P, P, P, P, P, D, P]),
+            "g6calc_lasthalf": (I, [I, I, I, P, P, P, D, P, P, P, P]),
+            "g6calc_lasthalf2": (I, [I, I, I, P, P, P, D, P, P, P, P, P]),
+            "g6_read_neighbour_list": (I, [I]),
+            "g6_get_neighbour_list": (I, [I, I, I, P, P]),
+            "g6x_open_ex": (I, [I, I, I]), "g6x_set_precision": (I, [I, I]),
+            "g6x_set_ni_max": (I, [I, I]), "g6x_set_stream": (I, [I, P]),
+            "g6x_set_allocator": (I, [ALLOC_FN, FREE_FN, P]),
+            "g6x_set_j_particles": (I, [I, I, P, P, P, P, P, P, P, P]),
+            "g6x_strerror": (C.c_char_p, [I]),
+            "g6x_set_j_dev": (I, [I, I, P]),
+            "g6x_calc_dev": (I, [I, D, I, I, P, D, I, P]),
+            "g6x_sync": (I, [I]), "g6x_set_variant": (I, [I, I, I]),
+            "g6x_get_predicted": (I, [I, I, P, P, P, P, P]),
+            "g6x_last_config": (I, [I, P, P, P, P, P, P]),
+            "g6x_launch_count": (C.c_longlong, [I]),
+            "g6x_set_timing": (I, [I, I]),
+            "g6x_get_timing": (I, [I, P, P]),
+            "g6h_create": (P, [I, I, P, P, P, D, D, D, D, D, P]),
+            "g6h_run": (I, [P, D]),
+            "g6h_get_state": (I, [P, P, P, P, P, P, P]),
+            "g6h_energy": (I, [P, P, P]),
+            "g6h_stats": (I, [P, P, P, P]),
+            "g6h_destroy": (None, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _d(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a if shape is None else a.reshape(shape)
+
+
+def _i(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(rc, what):
+    if rc < 0:
+        raise G6Error(rc, what)
+    return rc
+
+
+def strerror(code):
+    return lib().g6x_strerror(int(code)).decode()
+
+
+# ------------------------------------------------------------ GRAPE-6 API --
+
+def g6_open(cid):
+    return _check(lib().g6_open(cid), "g6_open")
+
+
+def g6x_open_ex(cid, nj_max, ni_max):
+    return _check(lib().g6x_open_ex(cid, int(nj_max), int(ni_max)), "g6x_open_ex")
+
+
+def g6_close(cid):
+    return _check(lib().g6_close(cid), "g6_close")
+
+
+def g6_npipes():
+    return lib().g6_npipes()
+
+
+def g6_set_tunit(v):
+    return lib().g6_set_tunit(int(v))
+
+
+def g6_set_xunit(v):
+    return lib().g6_set_xunit(int(v))
+
+
+def g6_set_ti(cid, ti):
+    return _check(lib().g6_set_ti(cid, float(ti)), "g6_set_ti")
+
+
+def g6_set_j_particle(cid, address, index, tj, dtj, mass, k18, j6, a2, v, x):
+    args = [_d(q, 3) for q in (k18, j6, a2, v, x)]
+    return _check(lib().g6_set_j_particle(cid, int(address), int(index), float(tj),
+                                          float(dtj), float(mass), *[_p(q) for q in args]),
+                  "g6_set_j_particle")
+
+
+def g6x_set_j_particles(cid, address, index, tj, mass, j6, a2, v, x):
+    address, index = _i(address), _i(index)
+    n = address.shape[0]
+    tj = _d(np.broadcast_to(np.asarray(tj, dtype=np.float64), (n,)))
+    mass = _d(np.broadcast_to(np.asarray(mass, dtype=np.float64), (n,)))
+    j6, a2, v, x = (_d(q, (n, 3)) for q in (j6, a2, v, x))
+    return _check(lib().g6x_set_j_particles(cid, n, _p(address), _p(index), _p(tj), _p(mass),
+                                            _p(j6), _p(a2), _p(v), _p(x)),
+                  "g6x_set_j_particles")
+
+
+def g6calc_firsthalf(cid, nj, ni, index, xi, vi, eps2, h2=None):
+    index = _i(index)
+    xi, vi = _d(xi, (ni, 3)), _d(vi, (ni, 3))
+    h2 = None if h2 is None else _d(np.broadcast_to(np.asarray(h2, dtype=np.float64), (ni,)))
+    # keep the marshalled arrays alive until the call returned (it copies them)
+    lib().g6calc_firsthalf(cid, int(nj), int(ni), _p(index), _p(xi), _p(vi), None, None,
+                           None, float(eps2), _p(h2))
+
+
+def g6calc_lasthalf2(cid, nj, ni, eps2=0.0):
+    """Returns (acc[ni,3], jerk[ni,3], pot[ni], nnbindex[ni])."""
+    acc = np.empty((ni, 3))
+    jerk = np.empty((ni, 3))
+    pot = np.empty(ni)
+    nnb = np.empty(ni, dtype=np.int32)
+    _check(lib().g6calc_lasthalf2(cid, int(nj), int(ni), None, None, None, float(eps2), None,
+                                  _p(acc), _p(jerk), _p(pot), _p(nnb)), "g6calc_lasthalf2")
+    return acc, jerk, pot, nnb
+
+
+def g6calc_lasthalf(cid, nj, ni, eps2=0.0):
+    """Returns (acc[ni,3], jerk[ni,3], pot[ni])."""
+    acc = np.empty((ni, 3))
+    jerk = np.empty((ni, 3))
+    pot = np.empty(ni)
+    _check(lib().g6calc_lasthalf(cid, int(nj), int(ni), None, None, None, float(eps2), None,
+                                 _p(acc), _p(jerk), _p(pot)), "g6calc_lasthalf")
+    return acc, jerk, pot
+
+
+def g6_read_neighbour_list(cid):
+    return _check(lib().g6_read_neighbour_list(cid), "g6_read_neighbour_list")
+
+
+def g6_get_neighbour_list(cid, ipipe, maxlength=G6_MAXNB):
+    """Returns (rc, nblen, list) where list holds min(nblen, maxlength, 256) ids."""
+    nbl = np.empty(max(1, maxlength), dtype=np.int32)
+    nblen = C.c_int(0)
+    rc = _check(lib().g6_get_neighbour_list(cid, int(ipipe), int(maxlength), C.byref(nblen),
+                                            _p(nbl)), "g6_get_neighbour_list")
+    n = min(nblen.value, maxlength, G6_MAXNB)
+    return rc, nblen.value, nbl[:n].copy()
+
+
+# ------------------------------------------------------------- extensions --
+
+def g6x_set_precision(cid, mode):
+    return _check(lib().g6x_set_precision(cid, int(mode)), "g6x_set_precision")
+
+
+def g6x_set_ni_max(cid, ni_max):
+    return _check(lib().g6x_set_ni_max(cid, int(ni_max)), "g6x_set_ni_max")
+
+
+def g6x_set_stream(cid, stream_ptr):
+    return _check(lib().g6x_set_stream(cid, C.c_void_p(int(stream_ptr) if stream_ptr else 0)),
+                  "g6x_set_stream")
+
+
+def g6x_set_variant(cid, variant=-1, grid=0):
+    return _check(lib().g6x_set_variant(cid, int(variant), int(grid)), "g6x_set_variant")
+
+
+def g6x_set_j_dev(cid, n, d_rec_ptr):
+    return _check(lib().g6x_set_j_dev(cid, int(n), C.c_void_p(int(d_rec_ptr))),
+                  "g6x_set_j_dev")
+
+
+def g6x_calc_dev(cid, ti, nj, ni, d_irec_ptr, eps2, nl, d_out_ptr):
+    return _check(lib().g6x_calc_dev(cid, float(ti), int(nj), int(ni),
+                                     C.c_void_p(int(d_irec_ptr)), float(eps2), int(nl),
+                                     C.c_void_p(int(d_out_ptr))), "g6x_calc_dev")
+
+
+def g6x_sync(cid):
+    return _check(lib().g6x_sync(cid), "g6x_sync")
+
+
+def g6x_get_predicted(cid, nj, fp64=False):
+    """DS mode: (hi[nj,4], lo[nj,4], vel[nj,4]) float32; FP64 mode: (x[nj,4], v[nj,4])."""
+    if fp64:
+        x = np.empty((nj, 4))
+        v = np.empty((nj, 4))
+        _check(lib().g6x_get_predicted(cid, int(nj), None, None, None, _p(x), _p(v)),
+               "g6x_get_predicted")
+        return x, v
+    hi = np.empty((nj, 4), dtype=np.float32)
+    lo = np.empty((nj, 4), dtype=np.float32)
+    vel = np.empty((nj, 4), dtype=np.float32)
+    _check(lib().g6x_get_predicted(cid, int(nj), _p(hi), _p(lo), _p(vel), None, None),
+           "g6x_get_predicted")
+    return hi, lo, vel
+
+
+def g6x_last_config(cid):
+    vals = [C.c_int(0) for _ in range(6)]
+    _check(lib().g6x_last_config(cid, *[C.byref(v) for v in vals]), "g6x_last_config")
+    return dict(zip(("variant", "ti", "tj", "ni_per", "grid", "jtiles"),
+                    [v.value for v in vals]))
+
+
+def g6x_launch_count(cid):
+    return lib().g6x_launch_count(cid)
+
+
+def g6x_set_timing(cid, enable=True):
+    return _check(lib().g6x_set_timing(cid, int(bool(enable))), "g6x_set_timing")
+
+
+def g6x_get_timing(cid):
+    """Returns (ms[4], count[4]) for scatter, predictor, force, reduction."""
+    ms = np.zeros(4)
+    cnt = np.zeros(4, dtype=np.int64)
+    _check(lib().g6x_get_timing(cid, _p(ms), _p(cnt)), "g6x_get_timing")
+    return ms, cnt
+
+
+_torch_hooks = None
+
+
+def g6x_use_torch_allocator():
+    """Route every later g6_open's device allocations through PyTorch's
+    caching allocator (torch.cuda.caching_allocator_alloc/delete)."""
+    global _torch_hooks
+    import torch
+
+    def _alloc(nbytes, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes))
+        except Exception:
+            return None
+
+    def _free(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _check(lib().g6x_set_allocator(hooks[0], hooks[1], None), "g6x_set_allocator")
+    _torch_hooks = hooks
+
+
+def g6x_use_cuda_allocator():
+    global _torch_hooks
+    _check(lib().g6x_set_allocator(ALLOC_FN(), FREE_FN(), None), "g6x_set_allocator")
+    _torch_hooks = None
+
+
+# --------------------------------------------------------- Hermite driver --
+
+class G6HSim:
+    """Owner of a g6h_sim handle (the C++ Hermite block-time-step driver)."""
+
+    def __init__(self, cid, m, x, v, eps2, eta, eta_s=0.0, dt_max=2.0 ** -4,
+                 dt_min=2.0 ** -40):
+        m = _d(m).reshape(-1)
+        n = m.shape[0]
+        x, v = _d(x, (n, 3)), _d(v, (n, 3))
+        err = C.c_int(0)
+        h = lib().g6h_create(cid, n, _p(m), _p(x), _p(v), float(eps2), float(eta),
+                             float(eta_s), float(dt_max), float(dt_min), C.byref(err))
+        if not h:
+            raise G6Error(err.value or G6_EINVAL, "g6h_create")
+        self.h = h
+        self.n = n
+
+    def run(self, t_end):
+        return _check(lib().g6h_run(self.h, float(t_end)), "g6h_run")
+
+    def state(self):
+        n = self.n
+        x, v, a, j = (np.empty((n, 3)) for _ in range(4))
+        t, dt = np.empty(n), np.empty(n)
+        _check(lib().g6h_get_state(self.h, _p(x), _p(v), _p(a), _p(j), _p(t), _p(dt)),
+               "g6h_get_state")
+        return dict(x=x, v=v, acc=a, jerk=j, t=t, dt=dt)
+
+    def energy(self):
+        ek, ep = C.c_double(0), C.c_double(0)
+        _check(lib().g6h_energy(self.h, C.byref(ek), C.byref(ep)), "g6h_energy")
+        return ek.value, ep.value
+
+    def stats(self):
+        nb, na = C.c_longlong(0), C.c_longlong(0)
+        hist = np.zeros(64, dtype=np.int64)
+        _check(lib().g6h_stats(self.h, C.byref(nb), C.byref(na), _p(hist)), "g6h_stats")
+        return dict(nblocks=nb.value, nactive=na.value, hist=hist)
+
+    def close(self):
+        if self.h:
+            lib().g6h_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

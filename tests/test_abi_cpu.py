@@ -1,0 +1,92 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every symbol
+include/g6gb.h declares, and fails cleanly (no crash, an error code) where no
+GPU exists.  No compute call runs here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_0902_4463_gb300 import build, g6gb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "g6gb.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return g6gb.lib()
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(g6[a-z0-9_]*)\s*\(", text))
+    names -= {"g6x_alloc_fn", "g6x_free_fn"}
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert len(declared) >= 30
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(g6gb.EXPORTS)
+
+
+def test_record_layouts_match_header():
+    # g6x_jrec 120 B, g6x_irec 64 B, g6x_out 64 B as documented in g6gb.h
+    assert g6gb.JREC.itemsize == 120
+    assert g6gb.IREC.itemsize == 64
+    assert g6gb.OUT.itemsize == 64
+
+
+def test_paper_constants_golden(lib):
+    # tests/golden/paper_constants.txt holds the numbers the paper prints
+    vals = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "paper_constants.txt")):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = line.split()
+            vals[k] = int(v)
+    assert g6gb.g6_npipes() == vals["npipes"]
+    assert g6gb.G6_MAXNB == vals["max_neighbours"]
+    from bench import FLOPS_PER_PAIR, FLOPS_PER_PAIR_DS
+    assert FLOPS_PER_PAIR == vals["flops_per_pair"]
+    assert FLOPS_PER_PAIR_DS == vals["flops_per_pair_ds"]
+    assert vals["flops_per_pair_ds"] - vals["flops_per_pair"] == 3 * (vals["ds_sub_flops"] - 1)
+
+
+def test_strerror_and_argument_errors_without_gpu(lib):
+    assert g6gb.strerror(g6gb.G6_EINVAL) == "invalid argument"
+    assert g6gb.strerror(g6gb.G6_EOVERFLOW) == "neighbour list overflow"
+    assert lib.g6_open(-1) == g6gb.G6_EINVAL
+    assert lib.g6_open(g6gb.G6_MAX_CLUSTERS) == g6gb.G6_EINVAL
+    assert lib.g6_close(3) == g6gb.G6_ENOTOPEN
+    assert lib.g6_set_ti(3, 0.0) == g6gb.G6_ENOTOPEN
+    assert lib.g6x_set_precision(3, 0) == g6gb.G6_ENOTOPEN
+    assert lib.g6_set_tunit(51) == 0 and lib.g6_set_xunit(51) == 0
+
+
+@pytest.mark.skipif(os.path.exists("/dev/nvidia0"), reason="host has a GPU")
+def test_open_without_gpu_reports_enodev(lib):
+    assert lib.g6_open(0) == g6gb.G6_ENODEV
+    assert lib.g6x_open_ex(1, 1024, 256) == g6gb.G6_ENODEV
+
+
+def test_binding_refuses_missing_library(tmp_path, monkeypatch):
+    monkeypatch.setattr(g6gb, "_lib", None)
+    monkeypatch.setattr(g6gb, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        g6gb.lib()
+
+
+def test_product_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_0902_4463_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cpp", ".h", ".cuh")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "oracle.h" not in text and "liboracle" not in text, f

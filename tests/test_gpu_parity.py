@@ -1,0 +1,228 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (stated for the FP32 + double-single path at N = 32768: median
+relative force error <= 1e-6, max <= 1e-5) are applied to acceleration, jerk
+and potential.  Nearest neighbours must be valid (FP64 distance within 1e-5
+relative of the oracle minimum; floating point decides near-ties).  The
+all-FP64 path must agree to 1e-11."""
+import numpy as np
+import pytest
+
+from paper_0902_4463_gb300 import g6gb as g6
+from paper_0902_4463_gb300 import ics
+from tests.gpu_helpers import check_nn, load_j, rel_err_vec, sweep
+
+pytestmark = pytest.mark.gpu
+
+CID = 2
+
+
+@pytest.fixture()
+def ctx():
+    from paper_0902_4463_gb300 import build
+    build.build()
+    g6.g6x_open_ex(CID, 1 << 20 | 4096, 1 << 20)
+    yield CID
+    g6.g6_close(CID)
+
+
+def _tol(prec):
+    return (1e-6, 1e-5) if prec == g6.G6X_PREC_DS else (1e-12, 1e-10)
+
+
+@pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64])
+def test_full_sweep_plummer_1024(ctx, orc, prec):
+    # Plummer N = 1024, eps2 = 1e-4, every particle active at t = 0.
+    n, eps2 = 1024, 1e-4
+    m, x, v = ics.plummer(n, 1)
+    idx = np.arange(n)
+    g6.g6x_set_precision(ctx, prec)
+    load_j(ctx, x, v, m)
+    acc, jerk, pot, nnb = sweep(ctx, n, x, v, idx, eps2, 0.0)
+    oa, oj, op, onn, onr = orc.force(x, v, idx, x, v, m, idx, eps2)
+    med, mx = _tol(prec)
+    ea, ej = rel_err_vec(acc, oa), rel_err_vec(jerk, oj)
+    ep = np.abs(pot - op) / np.abs(op)
+    assert np.median(ea) <= med and ea.max() <= mx
+    assert np.median(ej) <= med and ej.max() <= 10 * mx
+    assert np.median(ep) <= med and ep.max() <= mx
+    assert check_nn(onn, onr, nnb, x, x, idx) > 0.99
+
+
+@pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64])
+def test_predictor_matches_eq1_eq2(ctx, orc, prec):
+    # j-particles last updated at varied block times; predicted to t_blk.
+    n, t_blk = 3001, 0.375
+    st = ics.taylor_state(n, 7, t_blk)
+    g6.g6x_set_precision(ctx, prec)
+    load_j(ctx, st["x0"], st["v0"], st["m"], st["a0"], st["j0"], st["tj"])
+    g6.g6_set_ti(ctx, t_blk)
+    xp, vp = orc.predict(st["x0"], st["v0"], st["a0"], st["j0"], st["tj"], t_blk)
+    h = (t_blk - st["tj"])[:, None]
+    inc = np.abs(st["v0"] * h) + np.abs(st["a0"] * h * h / 2) + np.abs(st["j0"] * h ** 3 / 6)
+    vinc = np.abs(st["v0"]) + np.abs(st["a0"] * h) + np.abs(st["j0"] * h * h / 2)
+    if prec == g6.G6X_PREC_DS:
+        hi, lo, vel = g6.g6x_get_predicted(ctx, n)
+        x_gpu = hi[:, :3].astype(np.float64) + lo[:, :3].astype(np.float64)
+        assert np.all(np.abs(x_gpu - xp) <= 8 * 2.0 ** -24 * inc + 2.0 ** -46 * np.abs(xp))
+        assert np.all(np.abs(vel[:, :3] - vp) <= 8 * 2.0 ** -24 * vinc)
+        # hi is the nearest float of the position (DS split of Sect. 2.2)
+        assert np.all(np.abs(hi[:, :3] - xp) <= 2.0 ** -23 * np.abs(xp) + 8 * 2.0 ** -24 * inc)
+        assert np.array_equal(hi[:, 3], st["m"].astype(np.float32))
+        assert np.array_equal(vel[:, 3].view(np.int32), np.arange(n, dtype=np.int32))
+    else:
+        x64, v64 = g6.g6x_get_predicted(ctx, n, fp64=True)
+        assert np.allclose(x64[:, :3], xp, rtol=0, atol=1e-15 * (1 + np.abs(xp)).max())
+        assert np.allclose(v64[:, :3], vp, rtol=0, atol=1e-14 * (1 + np.abs(vp)).max())
+        assert np.array_equal(x64[:, 3], st["m"])
+
+
+@pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64])
+def test_subset_of_predicted_particles_ragged(ctx, orc, prec):
+    # n and m not multiples of any tile; i-particles are a seeded subset that
+    # sit at their generator positions while the j-particles are predicted.
+    n, m_act, t_blk, eps2 = 3001, 777, 0.25, 1e-5
+    st = ics.taylor_state(n, 11, t_blk)
+    g6.g6x_set_precision(ctx, prec)
+    load_j(ctx, st["x0"], st["v0"], st["m"], st["a0"], st["j0"], st["tj"])
+    act = ics.permutation(n, 11)[:m_act]
+    xi, vi = st["x0"][act], st["v0"][act]
+    acc, jerk, pot, nnb = sweep(ctx, n, xi, vi, act, eps2, t_blk)
+    xp, vp = orc.predict(st["x0"], st["v0"], st["a0"], st["j0"], st["tj"], t_blk)
+    idx = np.arange(n)
+    oa, oj, op, onn, onr = orc.force(xi, vi, act, xp, vp, st["m"], idx, eps2)
+    med, mx = _tol(prec)
+    ea, ej = rel_err_vec(acc, oa), rel_err_vec(jerk, oj)
+    ep = np.abs(pot - op) / np.abs(op)
+    assert np.median(ea) <= med and ea.max() <= mx
+    assert np.median(ej) <= 3 * med and ej.max() <= 30 * mx
+    assert np.median(ep) <= med and ep.max() <= mx
+    check_nn(onn, onr, nnb, xi, xp, idx)
+
+
+@pytest.mark.parametrize("n,m_act", [(1, 1), (7, 7), (33, 5), (255, 255), (257, 256),
+                                     (513, 33), (2049, 17), (300, 1)])
+def test_odd_sizes(ctx, orc, n, m_act):
+    eps2 = 1e-3
+    m, x, v = ics.plummer(n, 100 + n)
+    idx = np.arange(n)
+    load_j(ctx, x, v, m)
+    act = ics.permutation(n, n)[:m_act]
+    acc, jerk, pot, nnb = sweep(ctx, n, x[act], v[act], act, eps2, 0.0)
+    oa, oj, op, onn, onr = orc.force(x[act], v[act], act, x, v, m, idx, eps2)
+    if n == 1:
+        assert np.all(acc == 0) and np.all(jerk == 0) and np.all(pot == 0)
+        assert nnb[0] == -1
+        return
+    ea = rel_err_vec(acc, oa)
+    assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5
+    assert np.allclose(pot, op, rtol=1e-6)
+    check_nn(onn, onr, nnb, x[act], x, idx)
+
+
+def test_i_not_in_j_memory_feels_every_particle(ctx, orc):
+    # An i-particle whose index matches no j-slot is not self-excluded.
+    n, eps2 = 500, 1e-2
+    m, x, v = ics.plummer(n, 5)
+    load_j(ctx, x, v, m)
+    xi = x[:3] + 0.01
+    acc, jerk, pot, nnb = sweep(ctx, n, xi, v[:3], [10 ** 6, 10 ** 6 + 1, 10 ** 6 + 2],
+                                eps2, 0.0)
+    oa, oj, op, onn, onr = orc.force(xi, v[:3], [10 ** 6, 10 ** 6 + 1, 10 ** 6 + 2], x, v, m,
+                                     np.arange(n), eps2)
+    assert np.all(rel_err_vec(acc, oa) < 1e-5)
+    assert np.array_equal(nnb, onn)
+
+
+def test_two_body_without_softening(ctx, orc):
+    x = np.array([[-0.25, 0.0, 0.0], [0.25, 0.0, 0.0]])
+    v = np.array([[0.0, -0.8, 0.0], [0.0, 0.8, 0.0]])
+    m = np.array([0.5, 0.5])
+    load_j(ctx, x, v, m)
+    acc, jerk, pot, nnb = sweep(ctx, 2, x, v, [0, 1], 0.0, 0.0)
+    oa, oj, op, onn, _ = orc.force(x, v, [0, 1], x, v, m, [0, 1], 0.0)
+    assert np.allclose(acc, oa, rtol=1e-6, atol=1e-7)
+    assert np.allclose(jerk, oj, rtol=1e-6, atol=1e-7)
+    assert np.allclose(pot, op, rtol=1e-6)
+    assert list(nnb) == [1, 0]
+
+
+def test_close_binaries_need_double_single(ctx, orc):
+    # Binaries with separations 1e-4..1e-2 inside a Plummer sphere
+    # (Sect. 2.3: DS separations keep the digits FP32 positions would lose).
+    n = 4096
+    m, x, v, pairs = ics.plummer_with_binaries(n, 5)
+    idx = np.arange(n)
+    eps2 = 1e-8
+    load_j(ctx, x, v, m)
+    act = pairs[:64].reshape(-1)
+    acc, jerk, pot, nnb = sweep(ctx, n, x[act], v[act], act, eps2, 0.0)
+    oa, oj, op, onn, onr = orc.force(x[act], v[act], act, x, v, m, idx, eps2)
+    ea = rel_err_vec(acc, oa)
+    assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5
+    # every binary member's nearest neighbour is its companion
+    assert np.array_equal(nnb, onn)
+    assert np.array_equal(nnb, pairs[:64][:, ::-1].reshape(-1))
+
+
+def test_device_resident_path_matches_host_path(ctx):
+    import torch
+    n, eps2, t_blk = 5000, 1e-4, 0.125
+    st = ics.taylor_state(n, 3, t_blk)
+    load_j(ctx, st["x0"], st["v0"], st["m"], st["a0"], st["j0"], st["tj"])
+    act = ics.permutation(n, 3)[:1234]
+    xi, vi = st["x0"][act], st["v0"][act]
+    acc, jerk, pot, nnb = sweep(ctx, n, xi, vi, act, eps2, t_blk)
+    rec = np.zeros(act.size, dtype=g6.IREC)
+    rec["x"], rec["v"], rec["index"] = xi, vi, act
+    d_rec = torch.from_numpy(rec.view(np.uint8)).cuda()
+    d_out = torch.empty(act.size * g6.OUT.itemsize, dtype=torch.uint8, device="cuda")
+    g6.g6x_set_stream(ctx, torch.cuda.current_stream().cuda_stream)
+    g6.g6x_calc_dev(ctx, t_blk, n, act.size, d_rec.data_ptr(), eps2, 0, d_out.data_ptr())
+    g6.g6x_sync(ctx)
+    out = d_out.cpu().numpy().view(g6.OUT)
+    g6.g6x_set_stream(ctx, 0)
+    assert np.array_equal(out["acc"], acc) and np.array_equal(out["jerk"], jerk)
+    assert np.array_equal(out["pot"], pot) and np.array_equal(out["nnb"], nnb)
+
+
+def test_j_updates_between_calls(ctx, orc):
+    # set_j_particle after a calculation replaces slots; repeated writes to
+    # one slot keep the last; the prediction is redone.
+    n, eps2 = 1000, 1e-3
+    m, x, v = ics.plummer(n, 9)
+    idx = np.arange(n)
+    load_j(ctx, x, v, m)
+    sweep(ctx, n, x[:10], v[:10], idx[:10], eps2, 0.0)
+    x2 = x.copy()
+    x2[:50] += 0.05
+    z = np.zeros(3)
+    for k in range(50):
+        g6.g6_set_j_particle(ctx, k, k, 0.0, 0.0, m[k], z, z, z, v[k], x[k] - 1.0)
+        g6.g6_set_j_particle(ctx, k, k, 0.0, 0.0, m[k], z, z, z, v[k], x2[k])
+    acc, jerk, pot, nnb = sweep(ctx, n, x2[:100], v[:100], idx[:100], eps2, 0.0)
+    oa, oj, op, onn, onr = orc.force(x2[:100], v[:100], idx[:100], x2, v, m, idx, eps2)
+    assert np.median(rel_err_vec(acc, oa)) < 1e-6
+    assert np.allclose(pot, op, rtol=1e-6)
+
+
+def test_argument_errors_are_reported(ctx):
+    lib = g6.lib()
+    z = np.zeros(3)
+    zp = z.ctypes.data_as(g6.C.c_void_p)
+    assert lib.g6_set_j_particle(ctx, -1, 0, 0.0, 0.0, 1.0, zp, zp, zp, zp, zp) == g6.G6_EINVAL
+    assert lib.g6_set_j_particle(ctx, 0, -5, 0.0, 0.0, 1.0, zp, zp, zp, zp, zp) == g6.G6_EINVAL
+    assert lib.g6_open(ctx) == g6.G6_EBUSY
+    # lasthalf without firsthalf
+    assert lib.g6calc_lasthalf(ctx, 1, 1, None, None, None, 0.0, None, None, None,
+                               None) == g6.G6_EBUSY
+    # negative softening is latched by firsthalf and returned by lasthalf
+    g6.g6calc_firsthalf(ctx, 10, 1, [0], np.zeros((1, 3)), np.zeros((1, 3)), -1.0)
+    with pytest.raises(g6.G6Error):
+        g6.g6calc_lasthalf(ctx, 10, 1)
+    # the context stays usable
+    m, x, v = ics.plummer(64, 2)
+    load_j(ctx, x, v, m)
+    acc, *_ = sweep(ctx, 64, x, v, np.arange(64), 1e-2, 0.0)
+    assert np.all(np.isfinite(acc))
