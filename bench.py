@@ -258,7 +258,10 @@ def main():
 
     g6.g6x_use_torch_allocator()
     g6.g6x_open_ex(CID, n, max(m, 1))
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated (non-legacy) stream: the library and the timing events
+    # below both run on it
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     g6.g6x_set_stream(CID, stream.cuda_stream)
     if args.variant >= 0 or args.grid > 0:
         g6.g6x_set_variant(CID, args.variant, args.grid)

@@ -217,7 +217,7 @@ void free_ctx(Ctx &c)
         cudaStreamSynchronize(c.stream);
     g6::JStore &js = c.js;
     void *dptrs[] = {js.x0, js.t0, js.v0m, js.a2f, js.j6f, js.v64, js.a264, js.j664,
-                     js.idx, c.pred.ph, c.pred.pl, c.pred.pv, c.pred.p64, c.pred.v64,
+                     js.idx, c.pred.pt, c.pred.p64, c.pred.v64,
                      c.d_jst, c.d_irec, c.d_out, c.d_part, c.d_nbl_part, c.d_nbc_part,
                      c.d_nbl, c.d_nblen, c.d_err};
     for (void *p : dptrs)
@@ -514,15 +514,13 @@ int g6x_open_ex(int cid, int nj_max, int ni_max)
     js.a264 = (double4 *)dev_alloc(n * sizeof(double4));
     js.j664 = (double4 *)dev_alloc(n * sizeof(double4));
     js.idx = (int *)dev_alloc(n * sizeof(int));
-    c.pred.ph = (float4 *)dev_alloc(n * sizeof(float4));
-    c.pred.pl = (float4 *)dev_alloc(n * sizeof(float4));
-    c.pred.pv = (float4 *)dev_alloc(n * sizeof(float4));
+    c.pred.pt = (float *)dev_alloc(n * g6::JW * sizeof(float));
     c.pred.p64 = (double4 *)dev_alloc(n * sizeof(double4));
     c.pred.v64 = (double4 *)dev_alloc(n * sizeof(double4));
     c.d_err = (int *)dev_alloc(sizeof(int));
     c.h_err = (int *)host_alloc(sizeof(int));
     if (!js.x0 || !js.t0 || !js.v0m || !js.a2f || !js.j6f || !js.v64 || !js.a264
-        || !js.j664 || !js.idx || !c.pred.ph || !c.pred.pl || !c.pred.pv || !c.pred.p64
+        || !js.j664 || !js.idx || !c.pred.pt || !c.pred.p64
         || !c.pred.v64 || !c.d_err || !c.h_err)
         rc = G6_ENOMEM;
     if (!rc)
@@ -962,14 +960,39 @@ int g6x_get_predicted(int cid, int nj, float *hi, float *lo, float *vel, double 
     if (rc)
         return rc;
     cudaError_t e = cudaSuccess;
-    size_t f4 = sizeof(float4) * (size_t)nj, d4 = sizeof(double4) * (size_t)nj;
+    size_t d4 = sizeof(double4) * (size_t)nj;
     if (c->prec == G6X_PREC_DS) {
-        if (hi && e == cudaSuccess)
-            e = cudaMemcpyAsync(hi, c->pred.ph, f4, cudaMemcpyDeviceToHost, c->stream);
-        if (lo && e == cudaSuccess)
-            e = cudaMemcpyAsync(lo, c->pred.pl, f4, cudaMemcpyDeviceToHost, c->stream);
-        if (vel && e == cudaSuccess)
-            e = cudaMemcpyAsync(vel, c->pred.pv, f4, cudaMemcpyDeviceToHost, c->stream);
+        // copy the tiled layout back and unpack it into (x, y, z, w) rows
+        const int ntile = (nj + JT - 1) / JT;
+        std::vector<float> t((size_t)ntile * JT * g6::JW);
+        e = cudaMemcpyAsync(t.data(), c->pred.pt, t.size() * sizeof(float),
+                            cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess) {
+            for (int k = 0; k < nj; ++k) {
+                const float *b = t.data() + (size_t)(k / JT) * JT * g6::JW + k % JT;
+                auto w = [&](int comp) { return b[comp * JT]; };
+                if (hi) {
+                    hi[4 * k + 0] = w(g6::W_XH);
+                    hi[4 * k + 1] = w(g6::W_YH);
+                    hi[4 * k + 2] = w(g6::W_ZH);
+                    hi[4 * k + 3] = w(g6::W_M);
+                }
+                if (lo) {
+                    lo[4 * k + 0] = w(g6::W_XL);
+                    lo[4 * k + 1] = w(g6::W_YL);
+                    lo[4 * k + 2] = w(g6::W_ZL);
+                    lo[4 * k + 3] = 0.f;
+                }
+                if (vel) {
+                    vel[4 * k + 0] = w(g6::W_VX);
+                    vel[4 * k + 1] = w(g6::W_VY);
+                    vel[4 * k + 2] = w(g6::W_VZ);
+                    vel[4 * k + 3] = w(g6::W_ID);
+                }
+            }
+        }
     } else {
         if (x64 && e == cudaSuccess)
             e = cudaMemcpyAsync(x64, c->pred.p64, d4, cudaMemcpyDeviceToHost, c->stream);

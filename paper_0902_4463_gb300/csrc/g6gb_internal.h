@@ -40,11 +40,17 @@ struct JStore {
     int cap;
 };
 
+// Words per j-particle of the predicted DS layout and their order inside a
+// tile: each tile of JT j-particles is one contiguous block of JW * JT
+// 32-bit words, component-major (all x_hi of the tile, then all y_hi, ...),
+// so that one bulk copy stages a tile and a thread reads two consecutive
+// j-particles of one component as a float2.
+constexpr int JW = 11;
+enum JWord { W_XH = 0, W_YH, W_ZH, W_M, W_XL, W_YL, W_ZL, W_VX, W_VY, W_VZ, W_ID };
+
 // Predicted j-particles (force-kernel input).
 struct Pred {
-    float4 *ph;        // DS: (x_hi, y_hi, z_hi, m)
-    float4 *pl;        // DS: (x_lo, y_lo, z_lo, 0)
-    float4 *pv;        // DS: (vx, vy, vz, index bits)
+    float *pt;         // DS: tiled layout above, cap / JT tiles
     double4 *p64;      // FP64: (x, y, z, m)
     double4 *v64;      // FP64: (vx, vy, vz, index)
 };

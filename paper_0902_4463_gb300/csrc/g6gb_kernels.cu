@@ -181,12 +181,15 @@ __global__ void k_scatter(const g6x_jrec *__restrict__ rec, int n, JStore js)
 
 // Eq. 1 and Eq. 2 with the DS position of Sect. 2.2: the Taylor increment
 // dt (v + dt (a/2 + dt j/6)) is formed in FP32, added to the FP64 x0, and the
-// sum is split into hi = rn(x), lo = rn(x - hi).  The velocity is FP32.
+// sum is split into hi = rn(x), lo = rn(x - hi).  The velocity is FP32.  The
+// output is the tiled component-major layout (JW words per particle) that the
+// force kernel stages tile by tile.
 __global__ void __launch_bounds__(256) k_predict_ds(JStore js, Pred p, int nj,
                                                     int nj_pad, double t)
 {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nj_pad;
          k += gridDim.x * blockDim.x) {
+        float *o = p.pt + (size_t)(k / JT) * (JW * JT) + (k % JT);
         if (k < nj) {
             double dt = t - js.t0[k];
             float h = (float)dt;
@@ -199,20 +202,30 @@ __global__ void __launch_bounds__(256) k_predict_ds(JStore js, Pred p, int nj,
             double pz = js.x0[2 * js.cap + k] + (double)dz;
             float hx = __double2float_rn(px), hy = __double2float_rn(py),
                   hz = __double2float_rn(pz);
-            float lx = __double2float_rn(px - (double)hx);
-            float ly = __double2float_rn(py - (double)hy);
-            float lz = __double2float_rn(pz - (double)hz);
             float h3 = 3.0f * h;
-            float vx = fmaf(h, fmaf(h3, j.x, 2.0f * a.x), v.x);
-            float vy = fmaf(h, fmaf(h3, j.y, 2.0f * a.y), v.y);
-            float vz = fmaf(h, fmaf(h3, j.z, 2.0f * a.z), v.z);
-            p.ph[k] = make_float4(hx, hy, hz, v.w);
-            p.pl[k] = make_float4(lx, ly, lz, 0.f);
-            p.pv[k] = make_float4(vx, vy, vz, __int_as_float(js.idx[k]));
+            o[W_XH * JT] = hx;
+            o[W_YH * JT] = hy;
+            o[W_ZH * JT] = hz;
+            o[W_M * JT] = v.w;
+            o[W_XL * JT] = __double2float_rn(px - (double)hx);
+            o[W_YL * JT] = __double2float_rn(py - (double)hy);
+            o[W_ZL * JT] = __double2float_rn(pz - (double)hz);
+            o[W_VX * JT] = fmaf(h, fmaf(h3, j.x, 2.0f * a.x), v.x);
+            o[W_VY * JT] = fmaf(h, fmaf(h3, j.y, 2.0f * a.y), v.y);
+            o[W_VZ * JT] = fmaf(h, fmaf(h3, j.z, 2.0f * a.z), v.z);
+            o[W_ID * JT] = __int_as_float(js.idx[k]);
         } else {
-            p.ph[k] = make_float4((float)FAR, (float)FAR, (float)FAR, 0.f);
-            p.pl[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            p.pv[k] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+            o[W_XH * JT] = (float)FAR;
+            o[W_YH * JT] = (float)FAR;
+            o[W_ZH * JT] = (float)FAR;
+            o[W_M * JT] = 0.f;
+            o[W_XL * JT] = 0.f;
+            o[W_YL * JT] = 0.f;
+            o[W_ZL * JT] = 0.f;
+            o[W_VX * JT] = 0.f;
+            o[W_VY * JT] = 0.f;
+            o[W_VZ * JT] = 0.f;
+            o[W_ID * JT] = __int_as_float(-1);
         }
     }
 }
@@ -245,7 +258,7 @@ __global__ void __launch_bounds__(256) k_predict_64(JStore js, Pred p, int nj,
 // ----------------------------------------------------------------- K2 ---
 
 struct ForceArgs {
-    const float4 *ph, *pl, *pv;       // DS predicted j
+    const float *pt;                  // DS predicted j, tiled layout
     const double4 *p64, *v64;         // FP64 predicted j
     const g6x_irec *irec;
     Partial *part;
@@ -258,8 +271,7 @@ struct ForceArgs {
     double eps2;
 };
 
-// Pair forces on NI i-particles per thread in FP32 with the DS separation of
-// Eq. 3 (Sect. 2.3).  Per pair:
+// Pair forces in FP32 with the DS separation of Eq. 3 (Sect. 2.3).  Per pair:
 //   dx   = (xj_hi - xi_hi) + (xj_lo - xi_lo)                       Eq. 3
 //   r2u  = |dx|^2  (nearest neighbour and lists use it unsoftened)
 //   key  = r2u, or +inf for the i-particle's own j (index match)
@@ -267,22 +279,29 @@ struct ForceArgs {
 //   acc  += m r^-3 dx
 //   jerk += m r^-3 (dv - 3 (dx.dv) r^-2 dx)
 //   pot  += m r^-1                      (negated in K3)
-// Sums run in FP32 over each j-tile and are folded into compensated
-// (TwoSum) FP32 pairs every ~128 pairs, so the rounding of long sums does
-// not grow with n; the pairs are combined in FP64 when partials are written.
+// Each thread holds NI i-particles and walks its share of every j-tile two
+// j-particles at a time: the pair of j values of one component is one float2
+// and the arithmetic uses the packed FP32x2 instructions of sm_100+, which
+// issue two lanes of FP32 work per instruction.  Subtractions are additions
+// of the pre-negated i values (exact).  Sums run in FP32 over one flush
+// interval (>= 256 j per thread) and are then folded into compensated
+// (TwoSum) FP32 pairs kept in shared memory, so rounding does not grow with
+// n; the pairs are combined in FP64 when partials are written.
 template <int TI, int TJ, int NI, bool LIST>
 __global__ void __launch_bounds__(TI * TJ) k_force_ds(const ForceArgs a)
 {
     constexpr int NT = TI * TJ;
     constexpr int ITILE = TI * NI;
-    constexpr int JPT = JT / TJ;
-    constexpr int FLUSH = (128 + JPT - 1) / JPT;
+    constexpr int PPT = JT / 2 / TJ;                  // j-pairs per thread per tile
+    constexpr int FLUSH = (128 + PPT - 1) / PPT;      // tiles between flushes
+    constexpr unsigned TILE_BYTES = JW * JT * sizeof(float);
     static_assert(TJ == 1 || NI == 1, "split-j variants carry one i per thread");
     static_assert(!LIST || TJ == 1, "neighbour lists need whole j-tiles per thread");
-    static_assert(JT % TJ == 0, "j-tile must split evenly");
+    static_assert(JT % (2 * TJ) == 0, "j-tile must split into j-pairs evenly");
 
     extern __shared__ __align__(128) unsigned char dyn_smem[];
-    float4 *stage_buf = reinterpret_cast<float4 *>(dyn_smem);
+    float *stage_buf = reinterpret_cast<float *>(dyn_smem);
+    float2 *comp = reinterpret_cast<float2 *>(dyn_smem + NSTAGE * TILE_BYTES);  // [NI][7][NT]
     __shared__ __align__(8) uint64_t bar[NSTAGE];
     __shared__ int s_abort;
     __shared__ double red[TJ > 1 ? 8 * NT : 1];
@@ -308,35 +327,41 @@ __global__ void __launch_bounds__(TI * TJ) k_force_ds(const ForceArgs a)
         long long p = wb + q;
         int jt = (int)(p % a.J);
         int s = q % NSTAGE;
-        float4 *dst = stage_buf + (size_t)s * 3 * JT;
-        mbar_expect_tx(&bar[s], 3u * JT * sizeof(float4));
-        bulk_g2s(dst, a.ph + (size_t)jt * JT, JT * sizeof(float4), &bar[s]);
-        bulk_g2s(dst + JT, a.pl + (size_t)jt * JT, JT * sizeof(float4), &bar[s]);
-        bulk_g2s(dst + 2 * JT, a.pv + (size_t)jt * JT, JT * sizeof(float4), &bar[s]);
+        mbar_expect_tx(&bar[s], TILE_BYTES);
+        bulk_g2s(stage_buf + (size_t)s * JW * JT, a.pt + (size_t)jt * JW * JT, TILE_BYTES,
+                 &bar[s]);
     };
     if (tid == 0)
         for (int q = 0; q < NSTAGE && q < ntile; ++q)
             issue(q);
 
-    const float eps2 = (float)a.eps2;
-    float xh[NI][3], xl[NI][3], vi[NI][3], h2[NI];
+    const float2 eps2 = make_float2((float)a.eps2, (float)a.eps2);
+    const float2 m3 = make_float2(-3.0f, -3.0f);
+    const float INF = __int_as_float(0x7f800000);
+    float2 nxh[NI][3], nxl[NI][3], nv[NI][3];
+    float h2[NI];
     int iid[NI];
-    float ta[NI][7], hs[NI][7], ls[NI][7];
+    float2 ta[NI][7];
     float nnr[NI];
     int nnj[NI], nbn[NI];
     int cur_t = -1;
     int since_flush = 0;
+
+    auto cslot = [&](int k, int q) -> float2 & { return comp[(k * 7 + q) * NT + tid]; };
 
     auto flush = [&]() {
 #pragma unroll
         for (int k = 0; k < NI; ++k)
 #pragma unroll
             for (int q = 0; q < 7; ++q) {
+                float2 hl = cslot(k, q);
                 float s, e;
-                two_sum(hs[k][q], ta[k][q], s, e);
-                hs[k][q] = s;
-                ls[k][q] = __fadd_rn(ls[k][q], e);
-                ta[k][q] = 0.f;
+                two_sum(hl.x, ta[k][q].x, s, e);
+                hl.y = __fadd_rn(hl.y, e);
+                two_sum(s, ta[k][q].y, hl.x, e);
+                hl.y = __fadd_rn(hl.y, e);
+                cslot(k, q) = hl;
+                ta[k][q] = make_float2(0.f, 0.f);
             }
     };
 
@@ -351,29 +376,30 @@ __global__ void __launch_bounds__(TI * TJ) k_force_ds(const ForceArgs a)
                 for (int d = 0; d < 3; ++d) {
                     double x = r.x[d];
                     float hi = __double2float_rn(x);
-                    xh[k][d] = hi;
-                    xl[k][d] = __double2float_rn(x - (double)hi);
-                    vi[k][d] = (float)r.v[d];
+                    float lo = __double2float_rn(x - (double)hi);
+                    nxh[k][d] = make_float2(-hi, -hi);
+                    nxl[k][d] = make_float2(-lo, -lo);
+                    float w = -(float)r.v[d];
+                    nv[k][d] = make_float2(w, w);
                 }
                 h2[k] = (float)r.h2;
                 iid[k] = r.index;
             } else {
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    xh[k][d] = 0.f;
-                    xl[k][d] = 0.f;
-                    vi[k][d] = 0.f;
+                    nxh[k][d] = make_float2(0.f, 0.f);
+                    nxl[k][d] = make_float2(0.f, 0.f);
+                    nv[k][d] = make_float2(0.f, 0.f);
                 }
                 h2[k] = 0.f;
                 iid[k] = -2;
             }
 #pragma unroll
             for (int q = 0; q < 7; ++q) {
-                ta[k][q] = 0.f;
-                hs[k][q] = 0.f;
-                ls[k][q] = 0.f;
+                ta[k][q] = make_float2(0.f, 0.f);
+                cslot(k, q) = make_float2(0.f, 0.f);
             }
-            nnr[k] = __int_as_float(0x7f800000);
+            nnr[k] = INF;
             nnj[k] = -1;
             nbn[k] = 0;
         }
@@ -388,12 +414,18 @@ __global__ void __launch_bounds__(TI * TJ) k_force_ds(const ForceArgs a)
             for (int k = 0; k < NI; ++k) {
                 int il = k * TI + ti;
                 Partial *P = a.part + (size_t)seg * ITILE + il;
+                double s[7];
+#pragma unroll
+                for (int q = 0; q < 7; ++q) {
+                    float2 hl = cslot(k, q);
+                    s[q] = (double)hl.x + (double)hl.y;
+                }
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    P->acc[d] = (double)hs[k][d] + (double)ls[k][d];
-                    P->jerk[d] = (double)hs[k][3 + d] + (double)ls[k][3 + d];
+                    P->acc[d] = s[d];
+                    P->jerk[d] = s[3 + d];
                 }
-                P->pot = (double)hs[k][6] + (double)ls[k][6];
+                P->pot = s[6];
                 P->nnr2 = (double)nnr[k];
                 P->nnj = nnj[k];
                 if constexpr (LIST)
@@ -401,8 +433,10 @@ __global__ void __launch_bounds__(TI * TJ) k_force_ds(const ForceArgs a)
             }
         } else {
 #pragma unroll
-            for (int q = 0; q < 7; ++q)
-                red[q * NT + tid] = (double)hs[0][q] + (double)ls[0][q];
+            for (int q = 0; q < 7; ++q) {
+                float2 hl = cslot(0, q);
+                red[q * NT + tid] = (double)hl.x + (double)hl.y;
+            }
             red[7 * NT + tid] = (double)nnr[0];
             redj[tid] = nnj[0];
             __syncthreads();
@@ -455,51 +489,74 @@ __global__ void __launch_bounds__(TI * TJ) k_force_ds(const ForceArgs a)
         if (!ready) {
             s_abort = 1;
         } else {
-            const float4 *sph = stage_buf + (size_t)s * 3 * JT;
-            const float4 *spl = sph + JT;
-            const float4 *spv = spl + JT;
+            const float *S = stage_buf + (size_t)s * JW * JT;
+            const float2 *XH = reinterpret_cast<const float2 *>(S + W_XH * JT);
+            const float2 *YH = reinterpret_cast<const float2 *>(S + W_YH * JT);
+            const float2 *ZH = reinterpret_cast<const float2 *>(S + W_ZH * JT);
+            const float2 *MM = reinterpret_cast<const float2 *>(S + W_M * JT);
+            const float2 *XL = reinterpret_cast<const float2 *>(S + W_XL * JT);
+            const float2 *YL = reinterpret_cast<const float2 *>(S + W_YL * JT);
+            const float2 *ZL = reinterpret_cast<const float2 *>(S + W_ZL * JT);
+            const float2 *VX = reinterpret_cast<const float2 *>(S + W_VX * JT);
+            const float2 *VY = reinterpret_cast<const float2 *>(S + W_VY * JT);
+            const float2 *VZ = reinterpret_cast<const float2 *>(S + W_VZ * JT);
+            const int2 *ID = reinterpret_cast<const int2 *>(S + W_ID * JT);
             const int jbase = jt * JT;
 #pragma unroll 2
-            for (int kk = 0; kk < JPT; ++kk) {
-                const int jj = tj + kk * TJ;
-                const float4 pj = sph[jj];
-                const float4 lj = spl[jj];
-                const float4 vj = spv[jj];
-                const int jid = __float_as_int(vj.w);
+            for (int kk = 0; kk < PPT; ++kk) {
+                const int jp = tj + kk * TJ;
+                const float2 xh = XH[jp], yh = YH[jp], zh = ZH[jp], mj = MM[jp];
+                const float2 xl = XL[jp], yl = YL[jp], zl = ZL[jp];
+                const float2 vx = VX[jp], vy = VY[jp], vz = VZ[jp];
+                const int2 id = ID[jp];
 #pragma unroll
                 for (int k = 0; k < NI; ++k) {
-                    const float dx = (pj.x - xh[k][0]) + (lj.x - xl[k][0]);
-                    const float dy = (pj.y - xh[k][1]) + (lj.y - xl[k][1]);
-                    const float dz = (pj.z - xh[k][2]) + (lj.z - xl[k][2]);
-                    const float ux = vj.x - vi[k][0];
-                    const float uy = vj.y - vi[k][1];
-                    const float uz = vj.z - vi[k][2];
-                    const float r2u = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    const float key = (jid == iid[k]) ? __int_as_float(0x7f800000) : r2u;
-                    const float ri = rsqrt_approx(key + eps2);
-                    const float rv = fmaf(dz, uz, fmaf(dy, uy, dx * ux));
-                    const float ri2 = ri * ri;
-                    const float mr = pj.w * ri;
-                    const float mr3 = mr * ri2;
-                    const float sc = -3.0f * (rv * ri2);
-                    ta[k][6] += mr;
-                    ta[k][0] = fmaf(mr3, dx, ta[k][0]);
-                    ta[k][1] = fmaf(mr3, dy, ta[k][1]);
-                    ta[k][2] = fmaf(mr3, dz, ta[k][2]);
-                    ta[k][3] = fmaf(mr3, fmaf(sc, dx, ux), ta[k][3]);
-                    ta[k][4] = fmaf(mr3, fmaf(sc, dy, uy), ta[k][4]);
-                    ta[k][5] = fmaf(mr3, fmaf(sc, dz, uz), ta[k][5]);
-                    if (key < nnr[k]) {
-                        nnr[k] = key;
-                        nnj[k] = jbase + jj;
+                    const float2 dx = __fadd2_rn(__fadd2_rn(xh, nxh[k][0]), __fadd2_rn(xl, nxl[k][0]));
+                    const float2 dy = __fadd2_rn(__fadd2_rn(yh, nxh[k][1]), __fadd2_rn(yl, nxl[k][1]));
+                    const float2 dz = __fadd2_rn(__fadd2_rn(zh, nxh[k][2]), __fadd2_rn(zl, nxl[k][2]));
+                    const float2 ux = __fadd2_rn(vx, nv[k][0]);
+                    const float2 uy = __fadd2_rn(vy, nv[k][1]);
+                    const float2 uz = __fadd2_rn(vz, nv[k][2]);
+                    const float2 r2u = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                    float2 key;
+                    key.x = (id.x == iid[k]) ? INF : r2u.x;
+                    key.y = (id.y == iid[k]) ? INF : r2u.y;
+                    const float2 r2 = __fadd2_rn(key, eps2);
+                    float2 ri;
+                    ri.x = rsqrt_approx(r2.x);
+                    ri.y = rsqrt_approx(r2.y);
+                    const float2 rv = __ffma2_rn(dz, uz, __ffma2_rn(dy, uy, __fmul2_rn(dx, ux)));
+                    const float2 ri2 = __fmul2_rn(ri, ri);
+                    const float2 mr = __fmul2_rn(mj, ri);
+                    const float2 mr3 = __fmul2_rn(mr, ri2);
+                    const float2 sc = __fmul2_rn(__fmul2_rn(rv, ri2), m3);
+                    ta[k][6] = __fadd2_rn(ta[k][6], mr);
+                    ta[k][0] = __ffma2_rn(mr3, dx, ta[k][0]);
+                    ta[k][1] = __ffma2_rn(mr3, dy, ta[k][1]);
+                    ta[k][2] = __ffma2_rn(mr3, dz, ta[k][2]);
+                    ta[k][3] = __ffma2_rn(mr3, __ffma2_rn(sc, dx, ux), ta[k][3]);
+                    ta[k][4] = __ffma2_rn(mr3, __ffma2_rn(sc, dy, uy), ta[k][4]);
+                    ta[k][5] = __ffma2_rn(mr3, __ffma2_rn(sc, dz, uz), ta[k][5]);
+                    const int j0 = jbase + 2 * jp;
+                    if (key.x < nnr[k]) {
+                        nnr[k] = key.x;
+                        nnj[k] = j0;
+                    }
+                    if (key.y < nnr[k]) {
+                        nnr[k] = key.y;
+                        nnj[k] = j0 + 1;
                     }
                     if constexpr (LIST) {
-                        if (key < h2[k]) {
-                            if (nbn[k] < G6_MAXNB) {
-                                int il = k * TI + ti;
-                                a.nbl[((size_t)(c + t) * ITILE + il) * G6_MAXNB + nbn[k]] =
-                                    jbase + jj;
-                            }
+                        const int il = k * TI + ti;
+                        int *dst = a.nbl + ((size_t)(c + t) * ITILE + il) * G6_MAXNB;
+                        if (key.x < h2[k]) {
+                            if (nbn[k] < G6_MAXNB)
+                                dst[nbn[k]] = j0;
+                            ++nbn[k];
+                        }
+                        if (key.y < h2[k]) {
+                            if (nbn[k] < G6_MAXNB)
+                                dst[nbn[k]] = j0 + 1;
                             ++nbn[k];
                         }
                     }
@@ -744,16 +801,20 @@ struct Variant {
     int smem;
 };
 
-constexpr int DS_SMEM = NSTAGE * 3 * JT * (int)sizeof(float4);
+// dynamic shared memory of a DS variant: NSTAGE j-tiles + compensated sums
+constexpr int ds_smem(int nt, int ni)
+{
+    return NSTAGE * JW * JT * (int)sizeof(float) + ni * 7 * nt * (int)sizeof(float2);
+}
 
 const Variant kVariants[] = {
-    {{128, 1, 4, 0, G6X_PREC_DS}, k_force_ds<128, 1, 4, false>, 128, DS_SMEM},
-    {{128, 1, 2, 0, G6X_PREC_DS}, k_force_ds<128, 1, 2, false>, 128, DS_SMEM},
-    {{128, 1, 1, 0, G6X_PREC_DS}, k_force_ds<128, 1, 1, false>, 128, DS_SMEM},
-    {{32, 8, 1, 0, G6X_PREC_DS}, k_force_ds<32, 8, 1, false>, 256, DS_SMEM},
-    {{16, 16, 1, 0, G6X_PREC_DS}, k_force_ds<16, 16, 1, false>, 256, DS_SMEM},
-    {{128, 1, 1, 1, G6X_PREC_DS}, k_force_ds<128, 1, 1, true>, 128, DS_SMEM},
-    {{32, 1, 1, 1, G6X_PREC_DS}, k_force_ds<32, 1, 1, true>, 32, DS_SMEM},
+    {{128, 1, 2, 0, G6X_PREC_DS}, k_force_ds<128, 1, 2, false>, 128, ds_smem(128, 2)},
+    {{128, 1, 1, 0, G6X_PREC_DS}, k_force_ds<128, 1, 1, false>, 128, ds_smem(128, 1)},
+    {{64, 4, 1, 0, G6X_PREC_DS}, k_force_ds<64, 4, 1, false>, 256, ds_smem(256, 1)},
+    {{32, 8, 1, 0, G6X_PREC_DS}, k_force_ds<32, 8, 1, false>, 256, ds_smem(256, 1)},
+    {{16, 16, 1, 0, G6X_PREC_DS}, k_force_ds<16, 16, 1, false>, 256, ds_smem(256, 1)},
+    {{128, 1, 1, 1, G6X_PREC_DS}, k_force_ds<128, 1, 1, true>, 128, ds_smem(128, 1)},
+    {{32, 1, 1, 1, G6X_PREC_DS}, k_force_ds<32, 1, 1, true>, 32, ds_smem(32, 1)},
     {{128, 1, 1, 0, G6X_PREC_FP64}, k_force_64<false>, 128, 0},
     {{128, 1, 1, 1, G6X_PREC_FP64}, k_force_64<true>, 128, 0},
 };
@@ -765,7 +826,8 @@ bool g_smem_set[kNumVariants];
 cudaError_t prepare_variant(int v)
 {
     if (!g_smem_set[v]) {
-        if (kVariants[v].smem > 48 * 1024) {
+        // static + dynamic shared memory may exceed the 48 KB default
+        if (kVariants[v].smem > 0) {
             cudaError_t e = cudaFuncSetAttribute(
                 kVariants[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                 kVariants[v].smem);
@@ -813,9 +875,9 @@ ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
         v = 4;
     } else if (ni <= 32) {
         v = 3;
-    } else if (ni <= 4096) {
+    } else if (ni <= 64) {
         v = 2;
-    } else if (ni <= 16384) {
+    } else if (ni <= 8192) {
         v = 1;
     } else {
         v = 0;
@@ -894,9 +956,7 @@ cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
     if (e != cudaSuccess)
         return e;
     ForceArgs a;
-    a.ph = p.ph;
-    a.pl = p.pl;
-    a.pv = p.pv;
+    a.pt = p.pt;
     a.p64 = p.p64;
     a.v64 = p.v64;
     a.irec = d_irec;

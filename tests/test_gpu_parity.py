@@ -161,9 +161,10 @@ def test_close_binaries_need_double_single(ctx, orc):
     oa, oj, op, onn, onr = orc.force(x[act], v[act], act, x, v, m, idx, eps2)
     ea = rel_err_vec(acc, oa)
     assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5
-    # every binary member's nearest neighbour is its companion
+    # nearest neighbours agree with the oracle; almost all are the companion
+    # (a wide pair can have a closer third star)
     assert np.array_equal(nnb, onn)
-    assert np.array_equal(nnb, pairs[:64][:, ::-1].reshape(-1))
+    assert np.mean(nnb == pairs[:64][:, ::-1].reshape(-1)) > 0.9
 
 
 def test_device_resident_path_matches_host_path(ctx):
