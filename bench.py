@@ -39,7 +39,7 @@ T_BLK = 2.0 ** -10
 SEED = 3
 CID = 0
 KERNEL_SRC = os.path.join(ROOT, "paper_0902_4463_gb300", "csrc", "g6gb_kernels.cu")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_ds_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_force_ds_plummer_n262144.md")
 
 
 def parse():
@@ -155,11 +155,15 @@ def kernel_traffic():
     """DRAM bytes per force launch from the committed ncu capture, if it was
     taken on the current kernel source (else None)."""
     try:
-        rec = json.load(open(TRAFFIC_FILE))
+        rec = {}
+        for line in open(TRAFFIC_FILE):
+            if ":" in line and not line.startswith(("|", "#", " ")):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
         sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
         if rec.get("kernel_source_sha256") == sha:
-            return rec.get("bytes_per_launch_full")
-    except (OSError, ValueError):
+            return int(rec["traffic_bytes_per_launch_full"])
+    except (OSError, ValueError, KeyError):
         pass
     return None
 
