@@ -229,6 +229,35 @@ int g6x_calc_dev(int clusterid, double ti, int nj, int ni,
 int g6x_get_predicted(int clusterid, int nj, float *hi, float *lo, float *vel,
                       double *x64, double *v64);
 
+/* ------------------------------------ allocation-free force entry point --
+ * The paper has no counterpart to this call; it exists for callers of this
+ * library that must not allocate device memory when they ask for a force:
+ * for example an integrator whose device memory belongs to another
+ * framework's pool, which forbids cudaMalloc calls outside it, or a
+ * latency-critical host loop that cannot accept the device-wide
+ * synchronisation that cudaMalloc and cudaFree may cause.  g6x_calc_dev can
+ * grow its context's partial-sum buffer when a larger block arrives; this
+ * variant never allocates.
+ *
+ * Same work and arguments as g6x_calc_dev without neighbour lists, except
+ * that the partial sums between the force kernel and the reduction live in
+ * one fixed device array of G6X_NOALLOC_SCRATCH_BYTES (about 10.1 MiB) that
+ * every GPU loading this library holds until the process exits.
+ *   - The context must already be open (g6_open allocates, at set-up).
+ *   - ni > G6X_NOALLOC_NI_MAX, or a launch whose partial sums cannot fit the
+ *     array even on a smaller grid, returns G6_EINVAL before any work.
+ *   - The first call on each device looks up the array's device address;
+ *     make that first call during set-up, before any stream capture.
+ *   - All calls in the process share the array and it keeps the last call's
+ *     contents; each call writes every record it reads, so nothing needs
+ *     clearing.  Calls that overlap on the GPU (other streams or contexts)
+ *     race on the array: issue them one after another.
+ * Returns 0 or a negative G6_E* code. */
+#define G6X_NOALLOC_NI_MAX        16384
+#define G6X_NOALLOC_SCRATCH_BYTES (147456 * 72)
+int g6x_calc_dev_noalloc(int clusterid, double ti, int nj, int ni,
+                         const g6x_irec *d_irec, double eps2, g6x_out *d_out);
+
 /* Wait for the context's stream and report a device-side error recorded by
  * an earlier g6x_calc_dev (G6_ETIMEDOUT) or a CUDA error.  Returns 0 or the
  * code.  Not allowed between firsthalf and lasthalf (G6_EBUSY). */

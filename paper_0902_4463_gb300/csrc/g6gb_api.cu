@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -920,6 +921,102 @@ int g6x_calc_dev(int cid, double ti, int nj, int ni, const g6x_irec *d_irec, dou
     if (!rc && ni > 0)
         rc = run_force(*c, nj, ni, d_irec, eps2, nl != 0, d_out);
     return rc;
+}
+
+// ------------------------------------------------ allocation-free variant
+//
+// g6x_calc_dev_noalloc keeps the partial sums between the force kernel and
+// the reduction in the file-scope device array below instead of in context
+// memory that grows on demand, so the call itself never allocates.  The
+// array is G6X_NOALLOC_SCRATCH_BYTES on every GPU that loads this library,
+// held until the process exits.  In host code its name only stands in for
+// the device object; kernels get its device address from
+// cudaGetSymbolAddress, looked up once per device by the first call there.
+static __device__ __align__(256) unsigned char g6x_noalloc_scratch[G6X_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr size_t kNoallocSlots = G6X_NOALLOC_SCRATCH_BYTES / sizeof(g6::Partial);
+static_assert(G6X_NOALLOC_SCRATCH_BYTES % sizeof(g6::Partial) == 0,
+              "scratch holds a whole number of partial records");
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices];
+
+// Device address of the scratch array on the current device.
+int noalloc_scratch(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return cuda_err(e);
+    if (dev < 0 || dev >= kMaxDevices)
+        return G6_ENODEV;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g6x_noalloc_scratch);
+        if (e != cudaSuccess)
+            return cuda_err(e);
+        if (!p)
+            return G6_EIO;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return 0;
+}
+
+}  // namespace
+
+extern "C" int g6x_calc_dev_noalloc(int cid, double ti, int nj, int ni,
+                                    const g6x_irec *d_irec, double eps2, g6x_out *d_out)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (c->pending || nj < 0 || nj > c->cap || ni < 0 || ni > G6X_NOALLOC_NI_MAX
+        || check_eps2(eps2) || !std::isfinite(ti) || (ni > 0 && (!d_irec || !d_out)))
+        return G6_EINVAL;
+    // Choose the launch before any work, shrinking the grid if the partial
+    // records would not fit the array; reject what still does not fit.
+    const int nj_pad = round_up(nj > 0 ? nj : 1, JT);
+    ForceConfig cfg = g6::choose_config(c->prec, ni, nj_pad, 0, c->sm_count,
+                                        c->force_variant, c->force_grid);
+    if (cfg.list)
+        return G6_EINVAL;
+    if (g6::partial_slots(cfg) > kNoallocSlots) {
+        long long g = (long long)(kNoallocSlots / cfg.itile) - cfg.n_itile;
+        if (g < 1)
+            return G6_EINVAL;
+        cfg = g6::choose_config(c->prec, ni, nj_pad, 0, c->sm_count, cfg.variant, (int)g);
+        if (g6::partial_slots(cfg) > kNoallocSlots)
+            return G6_EINVAL;
+    }
+    void *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc)
+        return rc;
+    c->t_set = ti;
+    rc = flush_jstage(*c);
+    if (!rc)
+        rc = predict_if_stale(*c, nj);
+    if (rc || ni == 0)
+        return rc;
+    // Every record the reduction reads is written by the force kernel of
+    // this same call, so nothing left by an earlier call needs clearing.
+    g6::Partial *part = static_cast<g6::Partial *>(scratch);
+    cudaError_t e = g6::launch_force(cfg, c->pred, d_irec, ni, eps2, part, nullptr, nullptr,
+                                     c->d_err, c->stream);
+    if (e == cudaSuccess)
+        e = g6::launch_reduce(cfg, part, nullptr, nullptr, c->js.idx, ni, d_out, nullptr,
+                              nullptr, c->stream);
+    if (e != cudaSuccess)
+        return cuda_err(e);
+    c->launches += 2;
+    c->last_cfg = cfg;
+    c->lists_ready = false;
+    return 0;
 }
 
 int g6x_sync(int cid)

@@ -26,6 +26,8 @@ G6_MAXNB = 256
 G6_MAX_CLUSTERS = 16
 G6X_PREC_DS = 0
 G6X_PREC_FP64 = 1
+G6X_NOALLOC_NI_MAX = 16384
+G6X_NOALLOC_SCRATCH_BYTES = 147456 * 72
 
 # Record layouts of the device-resident entry points (g6x_jrec, g6x_irec,
 # g6x_out in g6gb.h).
@@ -44,7 +46,7 @@ EXPORTS = [
     "g6_read_neighbour_list", "g6_get_neighbour_list", "g6x_open_ex",
     "g6x_set_precision", "g6x_set_ni_max", "g6x_set_stream", "g6x_set_allocator",
     "g6x_set_j_particles", "g6x_strerror", "g6x_set_j_dev", "g6x_calc_dev",
-    "g6x_sync", "g6x_set_variant", "g6x_get_predicted", "g6x_last_config",
+    "g6x_calc_dev_noalloc", "g6x_sync", "g6x_set_variant", "g6x_get_predicted", "g6x_last_config",
     "g6x_launch_count", "g6x_set_timing", "g6x_get_timing", "g6h_create", "g6h_run", "g6h_get_state", "g6h_energy",
     "g6h_stats", "g6h_destroy",
 ]
@@ -86,6 +88,7 @@ def lib():
             "g6x_strerror": (C.c_char_p, [I]),
             "g6x_set_j_dev": (I, [I, I, P]),
             "g6x_calc_dev": (I, [I, D, I, I, P, D, I, P]),
+            "g6x_calc_dev_noalloc": (I, [I, D, I, I, P, D, P]),
             "g6x_sync": (I, [I]), "g6x_set_variant": (I, [I, I, I]),
             "g6x_get_predicted": (I, [I, I, P, P, P, P, P]),
             "g6x_last_config": (I, [I, P, P, P, P, P, P]),
@@ -250,6 +253,15 @@ def g6x_calc_dev(cid, ti, nj, ni, d_irec_ptr, eps2, nl, d_out_ptr):
     return _check(lib().g6x_calc_dev(cid, float(ti), int(nj), int(ni),
                                      C.c_void_p(int(d_irec_ptr)), float(eps2), int(nl),
                                      C.c_void_p(int(d_out_ptr))), "g6x_calc_dev")
+
+
+def g6x_calc_dev_noalloc(cid, ti, nj, ni, d_irec_ptr, eps2, d_out_ptr):
+    """Allocation-free form of g6x_calc_dev (partial sums in a fixed static
+    device array; ni <= G6X_NOALLOC_NI_MAX; no neighbour lists)."""
+    return _check(lib().g6x_calc_dev_noalloc(cid, float(ti), int(nj), int(ni),
+                                             C.c_void_p(int(d_irec_ptr)), float(eps2),
+                                             C.c_void_p(int(d_out_ptr))),
+                  "g6x_calc_dev_noalloc")
 
 
 def g6x_sync(cid):
