@@ -1,0 +1,186 @@
+"""GPU parity at the benchmark's sizes and through the Hermite driver.
+
+* Plummer N = 32768 (eps2 = 1e-5): every i-particle against all j, DS and FP64,
+  compared element by element with the oracle.
+* Plummer N = 2^20 (eps2 = 1e-6), m = N, in the launch configuration the
+  benchmark times: 256 sampled i-particles checked against the oracle.
+* Neighbour lists (Sect. 4) on a Plummer sphere with binaries, h2 = 1e-4.
+* The C++ Hermite block-time-step driver (Sect. 2) on a Kepler orbit against
+  the closed-form solution, and on Plummer N = 1024 to t = 0.25 with eta = 0.01
+  against the oracle's integrator: energy drift within 2x the oracle's.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_0902_4463_gb300 import g6gb as g6
+from paper_0902_4463_gb300 import ics
+from tests.gpu_helpers import check_nn, load_j, rel_err_vec, sweep
+
+pytestmark = pytest.mark.gpu
+
+CID = 3
+
+
+@pytest.fixture()
+def open_ctx():
+    from paper_0902_4463_gb300 import build
+    build.build()
+    opened = []
+
+    def _open(nj, ni):
+        g6.g6x_open_ex(CID, nj, ni)
+        opened.append(CID)
+        return CID
+
+    yield _open
+    for c in opened:
+        g6.g6_close(c)
+
+
+@pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64])
+def test_plummer_32768_full_sweep(open_ctx, orc, prec):
+    n, eps2 = 32768, 1e-5
+    m, x, v = ics.plummer(n, 2)
+    idx = np.arange(n)
+    cid = open_ctx(n, n)
+    g6.g6x_set_precision(cid, prec)
+    load_j(cid, x, v, m)
+    acc, jerk, pot, nnb = sweep(cid, n, x, v, idx, eps2, 0.0)
+    oa, oj, op, onn, onr = orc.force(x, v, idx, x, v, m, idx, eps2)
+    med, mx = (1e-6, 1e-5) if prec == g6.G6X_PREC_DS else (1e-12, 1e-10)
+    ea, ej = rel_err_vec(acc, oa), rel_err_vec(jerk, oj)
+    ep = np.abs(pot - op) / np.abs(op)
+    assert np.median(ea) <= med and ea.max() <= mx, (np.median(ea), ea.max())
+    assert np.median(ej) <= med and ej.max() <= 10 * mx, (np.median(ej), ej.max())
+    assert np.median(ep) <= med and ep.max() <= mx
+    assert check_nn(onn, onr, nnb, x, x, idx) > 0.999
+
+
+def test_full_size_sampled_in_bench_configuration(open_ctx, orc):
+    # N = 2^20, every particle active, j predicted from t_j = 0 to 2^-10
+    n, eps2, t_blk = 1 << 20, 1e-6, 2.0 ** -10
+    st = ics.taylor_state(n, 3, t_blk, dt_levels=None)
+    cid = open_ctx(n, n)
+    load_j(cid, st["x0"], st["v0"], st["m"], st["a0"], st["j0"], st["tj"])
+    idx = np.arange(n)
+    acc, jerk, pot, nnb = sweep(cid, n, st["x0"], st["v0"], idx, eps2, t_blk)
+    cfg = g6.g6x_last_config(cid)
+    assert cfg["variant"] == 0 and cfg["grid"] % 152 == 0
+    sample = ics.permutation(n, 99)[:256]
+    xp, vp = orc.predict(st["x0"], st["v0"], st["a0"], st["j0"], st["tj"], t_blk)
+    oa, oj, op, onn, onr = orc.force(st["x0"][sample], st["v0"][sample], sample, xp, vp,
+                                     st["m"], idx, eps2)
+    ea, ej = rel_err_vec(acc[sample], oa), rel_err_vec(jerk[sample], oj)
+    ep = np.abs(pot[sample] - op) / np.abs(op)
+    assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5, (np.median(ea), ea.max())
+    assert np.median(ej) <= 1e-6 and ej.max() <= 1e-4
+    assert np.median(ep) <= 1e-6 and ep.max() <= 1e-5
+    check_nn(onn, onr, nnb[sample], st["x0"][sample], xp, idx)
+    # properties that hold at any size: finite, attractive on average
+    assert np.all(np.isfinite(acc)) and np.all(np.isfinite(jerk)) and np.all(pot < 0)
+
+
+def _list_ok(gpu_ids, orc_pos, idx_j, xi, xj, h2, tol=1e-6):
+    """Lists agree as sets, except members within tol of the radius."""
+    g = set(int(k) for k in gpu_ids)
+    o = set(int(idx_j[p]) for p in orc_pos)
+    for k in g ^ o:
+        r2 = float(np.sum((xj[k] - xi) ** 2))
+        assert abs(r2 - h2) <= tol * h2, (k, r2, h2)
+
+
+@pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64])
+def test_neighbour_lists_plummer_with_binaries(open_ctx, orc, prec):
+    n, eps2 = 8192, 1e-8
+    m, x, v, pairs = ics.plummer_with_binaries(n, 5)
+    idx = np.arange(n)
+    cid = open_ctx(n, n)
+    g6.g6x_set_precision(cid, prec)
+    load_j(cid, x, v, m)
+    act = np.sort(ics.permutation(n, 5)[:600])
+    h2 = np.full(act.size, 1e-4)
+    h2[::7] = 0.05 ** 2                       # some long lists
+    h2[::11] = 0.3 ** 2                       # some that overflow 256
+    acc, jerk, pot, nnb = sweep(cid, n, x[act], v[act], act, eps2, 0.0, h2=h2)
+    rc = g6.g6_read_neighbour_list(cid)
+    nblen, nbl, nov = orc.neighbours(x[act], act, x, idx, h2, maxnb=g6.G6_MAXNB)
+    assert rc == (g6.G6_EOVERFLOW if nov else 0) and nov > 0
+    for q in range(act.size):
+        rc_q, ln, ids = g6.g6_get_neighbour_list(cid, q, g6.G6_MAXNB)
+        if nblen[q] <= g6.G6_MAXNB:
+            assert abs(ln - nblen[q]) <= 2
+            _list_ok(ids, nbl[q, :nblen[q]], idx, x[act[q]], x, h2[q])
+            assert list(ids) == sorted(ids)            # ascending j-slot
+        else:
+            assert ln > g6.G6_MAXNB and rc_q == g6.G6_EOVERFLOW
+            assert len(ids) == g6.G6_MAXNB and list(ids) == sorted(ids)
+    # forces are unchanged by list building
+    oa, *_ = orc.force(x[act], v[act], act, x, v, m, idx, eps2)
+    ea = rel_err_vec(acc, oa)
+    lim = (1e-6, 1e-5) if prec == g6.G6X_PREC_DS else (1e-12, 1e-10)
+    assert np.median(ea) <= lim[0] and ea.max() <= lim[1]
+
+
+def test_lists_with_all_radii_zero_are_empty(open_ctx):
+    n = 1000
+    m, x, v = ics.plummer(n, 8)
+    cid = open_ctx(n, n)
+    load_j(cid, x, v, m)
+    sweep(cid, n, x[:50], v[:50], np.arange(50), 1e-4, 0.0, h2=np.zeros(50))
+    assert g6.g6_read_neighbour_list(cid) == 0
+    for q in range(50):
+        rc, ln, ids = g6.g6_get_neighbour_list(cid, q)
+        assert rc == 0 and ln == 0 and ids.size == 0
+
+
+def _kepler_relative(t, a=1.0, e=0.5, mtot=1.0):
+    nmean = math.sqrt(mtot / a ** 3)
+    M = nmean * t
+    E = M
+    for _ in range(100):
+        E -= (E - e * math.sin(E) - M) / (1.0 - e * math.cos(E))
+    return np.array([a * (math.cos(E) - e), a * math.sqrt(1 - e * e) * math.sin(E), 0.0])
+
+
+@pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64])
+def test_hermite_driver_kepler_orbit(open_ctx, prec):
+    rp, vpk = 0.5, math.sqrt(3.0)
+    m = np.array([0.5, 0.5])
+    x = np.array([[-rp / 2, 0, 0], [rp / 2, 0, 0]])
+    v = np.array([[0, -vpk / 2, 0], [0, vpk / 2, 0]])
+    cid = open_ctx(256, 256)
+    g6.g6x_set_precision(cid, prec)
+    sim = g6.G6HSim(cid, m, x, v, 0.0, 0.005)
+    sim.run(2.0)
+    st = sim.state()
+    assert np.all(st["t"] == 2.0)
+    err = np.linalg.norm((st["x"][1] - st["x"][0]) - _kepler_relative(2.0))
+    assert err < 2e-4
+    ek, ep = sim.energy()
+    assert abs((ek + ep) / -0.125 - 1) < 1e-6
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64])
+def test_hermite_driver_plummer_1024_energy_drift(open_ctx, orc, prec):
+    n, eps2, eta, t_end = 1024, 1e-4, 0.01, 0.25
+    m, x, v = ics.plummer(n, 1)
+    E0 = orc.energy(m, x, v, eps2)
+    ref = orc.hermite_run(m, x, v, eps2, eta, t_end)
+    assert ref["err"] == 0
+    dE_orc = abs(orc.energy(m, ref["x"], ref["v"], eps2) / E0 - 1)
+    cid = open_ctx(n, n)
+    g6.g6x_set_precision(cid, prec)
+    sim = g6.G6HSim(cid, m, x, v, eps2, eta)
+    sim.run(t_end)
+    st = sim.state()
+    assert np.all(st["t"] == t_end)
+    dE_gpu = abs(orc.energy(m, st["x"], st["v"], eps2) / E0 - 1)
+    ek, ep = sim.energy()                        # the library's own energy sweep
+    assert abs((ek + ep) / E0 - 1 - (orc.energy(m, st["x"], st["v"], eps2) / E0 - 1)) < 1e-7
+    stats = sim.stats()
+    assert stats["nblocks"] > 10 and stats["hist"].sum() == stats["nblocks"]
+    assert dE_gpu <= 2 * max(dE_orc, 1e-12), (dE_gpu, dE_orc)
+    sim.close()
