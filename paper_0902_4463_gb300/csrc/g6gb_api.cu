@@ -218,7 +218,7 @@ void free_ctx(Ctx &c)
         cudaStreamSynchronize(c.stream);
     g6::JStore &js = c.js;
     void *dptrs[] = {js.x0, js.t0, js.v0m, js.a2f, js.j6f, js.v64, js.a264, js.j664,
-                     js.idx, c.pred.pt, c.pred.p64, c.pred.v64,
+                     js.idx, c.pred.pt, c.pred.trange, c.pred.p64, c.pred.v64,
                      c.d_jst, c.d_irec, c.d_out, c.d_part, c.d_nbl_part, c.d_nbc_part,
                      c.d_nbl, c.d_nblen, c.d_err};
     for (void *p : dptrs)
@@ -516,12 +516,13 @@ int g6x_open_ex(int cid, int nj_max, int ni_max)
     js.j664 = (double4 *)dev_alloc(n * sizeof(double4));
     js.idx = (int *)dev_alloc(n * sizeof(int));
     c.pred.pt = (float *)dev_alloc(n * g6::JW * sizeof(float));
+    c.pred.trange = (int2 *)dev_alloc((n / JT) * sizeof(int2));
     c.pred.p64 = (double4 *)dev_alloc(n * sizeof(double4));
     c.pred.v64 = (double4 *)dev_alloc(n * sizeof(double4));
     c.d_err = (int *)dev_alloc(sizeof(int));
     c.h_err = (int *)host_alloc(sizeof(int));
     if (!js.x0 || !js.t0 || !js.v0m || !js.a2f || !js.j6f || !js.v64 || !js.a264
-        || !js.j664 || !js.idx || !c.pred.pt || !c.pred.p64
+        || !js.j664 || !js.idx || !c.pred.pt || !c.pred.trange || !c.pred.p64
         || !c.pred.v64 || !c.d_err || !c.h_err)
         rc = G6_ENOMEM;
     if (!rc)

@@ -51,6 +51,10 @@ enum JWord { W_XH = 0, W_YH, W_ZH, W_M, W_XL, W_YL, W_ZL, W_VX, W_VY, W_VZ, W_ID
 // Predicted j-particles (force-kernel input).
 struct Pred {
     float *pt;         // DS: tiled layout above, cap / JT tiles
+    int2 *trange;      // DS: per tile, smallest and largest particle index
+                       //     (empty tile: INT_MAX, -1); lets the force kernel
+                       //     skip the per-pair self test on tiles that hold
+                       //     none of its i-particles
     double4 *p64;      // FP64: (x, y, z, m)
     double4 *v64;      // FP64: (vx, vy, vz, index)
 };

@@ -28,6 +28,7 @@
 
 #include <climits>
 #include <cmath>
+#include <type_traits>
 
 namespace g6 {
 
@@ -184,12 +185,39 @@ __global__ void k_scatter(const g6x_jrec *__restrict__ rec, int n, JStore js)
 // sum is split into hi = rn(x), lo = rn(x - hi).  The velocity is FP32.  The
 // output is the tiled component-major layout (JW words per particle) that the
 // force kernel stages tile by tile.
-__global__ void __launch_bounds__(256) k_predict_ds(JStore js, Pred p, int nj,
-                                                    int nj_pad, double t)
+// One CTA of JT threads per tile (grid-stride over tiles); the CTA also
+// records the tile's range of particle indices.
+__global__ void __launch_bounds__(JT) k_predict_ds(JStore js, Pred p, int nj,
+                                                   int nj_pad, double t)
 {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nj_pad;
-         k += gridDim.x * blockDim.x) {
-        float *o = p.pt + (size_t)(k / JT) * (JW * JT) + (k % JT);
+    __shared__ int s_lo[JT / 32], s_hi[JT / 32];
+    const int ntiles = nj_pad / JT;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int k = tile * JT + threadIdx.x;
+        float *o = p.pt + (size_t)tile * (JW * JT) + threadIdx.x;
+        int lo_id = INT_MAX, hi_id = -1;
+        if (k < nj && js.idx[k] >= 0) {
+            lo_id = js.idx[k];
+            hi_id = lo_id;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            lo_id = min(lo_id, __shfl_xor_sync(0xffffffffu, lo_id, off));
+            hi_id = max(hi_id, __shfl_xor_sync(0xffffffffu, hi_id, off));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            s_lo[threadIdx.x >> 5] = lo_id;
+            s_hi[threadIdx.x >> 5] = hi_id;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < JT / 32; ++w) {
+                lo_id = min(lo_id, s_lo[w]);
+                hi_id = max(hi_id, s_hi[w]);
+            }
+            p.trange[tile] = make_int2(lo_id, hi_id);
+        }
+        __syncthreads();
         if (k < nj) {
             double dt = t - js.t0[k];
             float h = (float)dt;
@@ -259,6 +287,7 @@ __global__ void __launch_bounds__(256) k_predict_64(JStore js, Pred p, int nj,
 
 struct ForceArgs {
     const float *pt;                  // DS predicted j, tiled layout
+    const int2 *trange;               // DS per-tile index range
     const double4 *p64, *v64;         // FP64 predicted j
     const g6x_irec *irec;
     Partial *part;
@@ -283,17 +312,26 @@ struct ForceArgs {
 // j-particles at a time: the pair of j values of one component is one float2
 // and the arithmetic uses the packed FP32x2 instructions of sm_100+, which
 // issue two lanes of FP32 work per instruction.  Subtractions are additions
-// of the pre-negated i values (exact).  Sums run in FP32 over one flush
-// interval (>= 256 j per thread) and are then folded into compensated
-// (TwoSum) FP32 pairs kept in shared memory, so rounding does not grow with
-// n; the pairs are combined in FP64 when partials are written.
-template <int TI, int TJ, int NI, bool LIST>
-__global__ void __launch_bounds__(TI * TJ) k_force_ds(const ForceArgs a)
+// of the pre-negated i values (exact).
+//
+// The per-pair self test is needed only on j-tiles whose index range holds
+// one of the warp's i-particles; other tiles take the same loop without it.
+// The nearest neighbour is tracked lazily: a running minimum of the key per
+// tile and the tile that lowered it; when a segment ends, that one tile is
+// scanned again with the same arithmetic to find the first j that attains
+// the minimum (ties to the lower j-slot).
+//
+// Sums run in FP32 over one flush interval (>= 512 j per thread) and are
+// then folded into compensated (TwoSum) FP32 pairs kept in shared memory, so
+// rounding does not grow with n; the pairs are combined in FP64 when
+// partials are written.
+template <int TI, int TJ, int NI, bool LIST, int MINB = 1, int UNR = 2>
+__global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
 {
     constexpr int NT = TI * TJ;
     constexpr int ITILE = TI * NI;
     constexpr int PPT = JT / 2 / TJ;                  // j-pairs per thread per tile
-    constexpr int FLUSH = (128 + PPT - 1) / PPT;      // tiles between flushes
+    constexpr int FLUSH = (256 + PPT - 1) / PPT;      // tiles between flushes (>= 512 j)
     constexpr unsigned TILE_BYTES = JW * JT * sizeof(float);
     static_assert(TJ == 1 || NI == 1, "split-j variants carry one i per thread");
     static_assert(!LIST || TJ == 1, "neighbour lists need whole j-tiles per thread");
@@ -342,8 +380,8 @@ __global__ void __launch_bounds__(TI * TJ) k_force_ds(const ForceArgs a)
     float h2[NI];
     int iid[NI];
     float2 ta[NI][7];
-    float nnr[NI];
-    int nnj[NI], nbn[NI];
+    float tmin[NI], nnr[NI];
+    int nnt[NI], nbn[NI];
     int cur_t = -1;
     int since_flush = 0;
 
@@ -399,11 +437,39 @@ __global__ void __launch_bounds__(TI * TJ) k_force_ds(const ForceArgs a)
                 ta[k][q] = make_float2(0.f, 0.f);
                 cslot(k, q) = make_float2(0.f, 0.f);
             }
+            tmin[k] = INF;
             nnr[k] = INF;
-            nnj[k] = -1;
+            nnt[k] = -1;
             nbn[k] = 0;
         }
         since_flush = 0;
+    };
+
+    // First j of the thread's share of tile nnt[k] whose key equals nnr[k],
+    // recomputed with the loop's arithmetic (packed lanes round like the
+    // scalar operations used here).
+    auto nn_rescan = [&](int k) -> int {
+        if (!(nnr[k] < INF) || nnt[k] < 0)
+            return -1;
+        const float *T = a.pt + (size_t)nnt[k] * JW * JT;
+        for (int kk = 0; kk < PPT; ++kk) {
+            const int jp = tj + kk * TJ;
+            for (int h = 0; h < 2; ++h) {
+                const int jj = 2 * jp + h;
+                const float dx = __fadd_rn(__fadd_rn(T[W_XH * JT + jj], nxh[k][0].x),
+                                           __fadd_rn(T[W_XL * JT + jj], nxl[k][0].x));
+                const float dy = __fadd_rn(__fadd_rn(T[W_YH * JT + jj], nxh[k][1].x),
+                                           __fadd_rn(T[W_YL * JT + jj], nxl[k][1].x));
+                const float dz = __fadd_rn(__fadd_rn(T[W_ZH * JT + jj], nxh[k][2].x),
+                                           __fadd_rn(T[W_ZL * JT + jj], nxl[k][2].x));
+                const float r2u = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                const int id = __float_as_int(T[W_ID * JT + jj]);
+                const float key = (id == iid[k]) ? INF : r2u;
+                if (key == nnr[k])
+                    return nnt[k] * JT + jj;
+            }
+        }
+        return -1;
     };
 
     auto finalize = [&](int t) {
@@ -427,7 +493,7 @@ __global__ void __launch_bounds__(TI * TJ) k_force_ds(const ForceArgs a)
                 }
                 P->pot = s[6];
                 P->nnr2 = (double)nnr[k];
-                P->nnj = nnj[k];
+                P->nnj = nn_rescan(k);
                 if constexpr (LIST)
                     a.nbc[(size_t)seg * ITILE + il] = nbn[k];
             }
@@ -438,7 +504,7 @@ __global__ void __launch_bounds__(TI * TJ) k_force_ds(const ForceArgs a)
                 red[q * NT + tid] = (double)hl.x + (double)hl.y;
             }
             red[7 * NT + tid] = (double)nnr[0];
-            redj[tid] = nnj[0];
+            redj[tid] = nn_rescan(0);
             __syncthreads();
             if (tid < TI) {
                 double s[7];
@@ -473,6 +539,80 @@ __global__ void __launch_bounds__(TI * TJ) k_force_ds(const ForceArgs a)
         }
     };
 
+    // All pairs of the thread's share of one staged tile.  SELF: apply the
+    // per-pair self test (tiles that may hold one of the i-particles).
+    auto tile_pass = [&](const float *S, int t, int jt, auto self_tag) {
+        constexpr bool SELF = decltype(self_tag)::value;
+        const float2 *XH = reinterpret_cast<const float2 *>(S + W_XH * JT);
+        const float2 *YH = reinterpret_cast<const float2 *>(S + W_YH * JT);
+        const float2 *ZH = reinterpret_cast<const float2 *>(S + W_ZH * JT);
+        const float2 *MM = reinterpret_cast<const float2 *>(S + W_M * JT);
+        const float2 *XL = reinterpret_cast<const float2 *>(S + W_XL * JT);
+        const float2 *YL = reinterpret_cast<const float2 *>(S + W_YL * JT);
+        const float2 *ZL = reinterpret_cast<const float2 *>(S + W_ZL * JT);
+        const float2 *VX = reinterpret_cast<const float2 *>(S + W_VX * JT);
+        const float2 *VY = reinterpret_cast<const float2 *>(S + W_VY * JT);
+        const float2 *VZ = reinterpret_cast<const float2 *>(S + W_VZ * JT);
+        const int2 *ID = reinterpret_cast<const int2 *>(S + W_ID * JT);
+        const int jbase = jt * JT;
+#pragma unroll UNR
+        for (int kk = 0; kk < PPT; ++kk) {
+            const int jp = tj + kk * TJ;
+            const float2 xh = XH[jp], yh = YH[jp], zh = ZH[jp], mj = MM[jp];
+            const float2 xl = XL[jp], yl = YL[jp], zl = ZL[jp];
+            const float2 vx = VX[jp], vy = VY[jp], vz = VZ[jp];
+            int2 id = make_int2(0, 0);
+            if constexpr (SELF)
+                id = ID[jp];
+#pragma unroll
+            for (int k = 0; k < NI; ++k) {
+                const float2 dx = __fadd2_rn(__fadd2_rn(xh, nxh[k][0]), __fadd2_rn(xl, nxl[k][0]));
+                const float2 dy = __fadd2_rn(__fadd2_rn(yh, nxh[k][1]), __fadd2_rn(yl, nxl[k][1]));
+                const float2 dz = __fadd2_rn(__fadd2_rn(zh, nxh[k][2]), __fadd2_rn(zl, nxl[k][2]));
+                const float2 ux = __fadd2_rn(vx, nv[k][0]);
+                const float2 uy = __fadd2_rn(vy, nv[k][1]);
+                const float2 uz = __fadd2_rn(vz, nv[k][2]);
+                float2 key = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                if constexpr (SELF) {
+                    key.x = (id.x == iid[k]) ? INF : key.x;
+                    key.y = (id.y == iid[k]) ? INF : key.y;
+                }
+                const float2 r2 = __fadd2_rn(key, eps2);
+                float2 ri;
+                ri.x = rsqrt_approx(r2.x);
+                ri.y = rsqrt_approx(r2.y);
+                const float2 rv = __ffma2_rn(dz, uz, __ffma2_rn(dy, uy, __fmul2_rn(dx, ux)));
+                const float2 ri2 = __fmul2_rn(ri, ri);
+                const float2 mr = __fmul2_rn(mj, ri);
+                const float2 mr3 = __fmul2_rn(mr, ri2);
+                const float2 sc = __fmul2_rn(__fmul2_rn(rv, ri2), m3);
+                ta[k][6] = __fadd2_rn(ta[k][6], mr);
+                ta[k][0] = __ffma2_rn(mr3, dx, ta[k][0]);
+                ta[k][1] = __ffma2_rn(mr3, dy, ta[k][1]);
+                ta[k][2] = __ffma2_rn(mr3, dz, ta[k][2]);
+                ta[k][3] = __ffma2_rn(mr3, __ffma2_rn(sc, dx, ux), ta[k][3]);
+                ta[k][4] = __ffma2_rn(mr3, __ffma2_rn(sc, dy, uy), ta[k][4]);
+                ta[k][5] = __ffma2_rn(mr3, __ffma2_rn(sc, dz, uz), ta[k][5]);
+                tmin[k] = fminf(tmin[k], fminf(key.x, key.y));
+                if constexpr (LIST) {
+                    const int il = k * TI + ti;
+                    const int j0 = jbase + 2 * jp;
+                    int *dst = a.nbl + ((size_t)(c + t) * ITILE + il) * G6_MAXNB;
+                    if (key.x < h2[k]) {
+                        if (nbn[k] < G6_MAXNB)
+                            dst[nbn[k]] = j0;
+                        ++nbn[k];
+                    }
+                    if (key.y < h2[k]) {
+                        if (nbn[k] < G6_MAXNB)
+                            dst[nbn[k]] = j0 + 1;
+                        ++nbn[k];
+                    }
+                }
+            }
+        }
+    };
+
     for (int q = 0; q < ntile; ++q) {
         const long long p = wb + q;
         const int t = (int)(p / a.J);
@@ -483,6 +623,16 @@ __global__ void __launch_bounds__(TI * TJ) k_force_ds(const ForceArgs a)
             load_i(t);
             cur_t = t;
         }
+        // Does this tile hold the j-particle of one of the warp's i-particles?
+        bool self_tile = LIST;
+        if constexpr (!LIST) {
+            const int2 rg = a.trange[jt];
+            bool mine = false;
+#pragma unroll
+            for (int k = 0; k < NI; ++k)
+                mine |= (iid[k] >= rg.x && iid[k] <= rg.y);
+            self_tile = __any_sync(0xffffffffu, mine);
+        }
         const int s = q % NSTAGE;
         const uint32_t par = (uint32_t)((q / NSTAGE) & 1);
         const bool ready = mbar_wait_bounded(&bar[s], par);
@@ -490,77 +640,17 @@ __global__ void __launch_bounds__(TI * TJ) k_force_ds(const ForceArgs a)
             s_abort = 1;
         } else {
             const float *S = stage_buf + (size_t)s * JW * JT;
-            const float2 *XH = reinterpret_cast<const float2 *>(S + W_XH * JT);
-            const float2 *YH = reinterpret_cast<const float2 *>(S + W_YH * JT);
-            const float2 *ZH = reinterpret_cast<const float2 *>(S + W_ZH * JT);
-            const float2 *MM = reinterpret_cast<const float2 *>(S + W_M * JT);
-            const float2 *XL = reinterpret_cast<const float2 *>(S + W_XL * JT);
-            const float2 *YL = reinterpret_cast<const float2 *>(S + W_YL * JT);
-            const float2 *ZL = reinterpret_cast<const float2 *>(S + W_ZL * JT);
-            const float2 *VX = reinterpret_cast<const float2 *>(S + W_VX * JT);
-            const float2 *VY = reinterpret_cast<const float2 *>(S + W_VY * JT);
-            const float2 *VZ = reinterpret_cast<const float2 *>(S + W_VZ * JT);
-            const int2 *ID = reinterpret_cast<const int2 *>(S + W_ID * JT);
-            const int jbase = jt * JT;
-#pragma unroll 2
-            for (int kk = 0; kk < PPT; ++kk) {
-                const int jp = tj + kk * TJ;
-                const float2 xh = XH[jp], yh = YH[jp], zh = ZH[jp], mj = MM[jp];
-                const float2 xl = XL[jp], yl = YL[jp], zl = ZL[jp];
-                const float2 vx = VX[jp], vy = VY[jp], vz = VZ[jp];
-                const int2 id = ID[jp];
+            if (self_tile)
+                tile_pass(S, t, jt, std::true_type{});
+            else
+                tile_pass(S, t, jt, std::false_type{});
 #pragma unroll
-                for (int k = 0; k < NI; ++k) {
-                    const float2 dx = __fadd2_rn(__fadd2_rn(xh, nxh[k][0]), __fadd2_rn(xl, nxl[k][0]));
-                    const float2 dy = __fadd2_rn(__fadd2_rn(yh, nxh[k][1]), __fadd2_rn(yl, nxl[k][1]));
-                    const float2 dz = __fadd2_rn(__fadd2_rn(zh, nxh[k][2]), __fadd2_rn(zl, nxl[k][2]));
-                    const float2 ux = __fadd2_rn(vx, nv[k][0]);
-                    const float2 uy = __fadd2_rn(vy, nv[k][1]);
-                    const float2 uz = __fadd2_rn(vz, nv[k][2]);
-                    const float2 r2u = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-                    float2 key;
-                    key.x = (id.x == iid[k]) ? INF : r2u.x;
-                    key.y = (id.y == iid[k]) ? INF : r2u.y;
-                    const float2 r2 = __fadd2_rn(key, eps2);
-                    float2 ri;
-                    ri.x = rsqrt_approx(r2.x);
-                    ri.y = rsqrt_approx(r2.y);
-                    const float2 rv = __ffma2_rn(dz, uz, __ffma2_rn(dy, uy, __fmul2_rn(dx, ux)));
-                    const float2 ri2 = __fmul2_rn(ri, ri);
-                    const float2 mr = __fmul2_rn(mj, ri);
-                    const float2 mr3 = __fmul2_rn(mr, ri2);
-                    const float2 sc = __fmul2_rn(__fmul2_rn(rv, ri2), m3);
-                    ta[k][6] = __fadd2_rn(ta[k][6], mr);
-                    ta[k][0] = __ffma2_rn(mr3, dx, ta[k][0]);
-                    ta[k][1] = __ffma2_rn(mr3, dy, ta[k][1]);
-                    ta[k][2] = __ffma2_rn(mr3, dz, ta[k][2]);
-                    ta[k][3] = __ffma2_rn(mr3, __ffma2_rn(sc, dx, ux), ta[k][3]);
-                    ta[k][4] = __ffma2_rn(mr3, __ffma2_rn(sc, dy, uy), ta[k][4]);
-                    ta[k][5] = __ffma2_rn(mr3, __ffma2_rn(sc, dz, uz), ta[k][5]);
-                    const int j0 = jbase + 2 * jp;
-                    if (key.x < nnr[k]) {
-                        nnr[k] = key.x;
-                        nnj[k] = j0;
-                    }
-                    if (key.y < nnr[k]) {
-                        nnr[k] = key.y;
-                        nnj[k] = j0 + 1;
-                    }
-                    if constexpr (LIST) {
-                        const int il = k * TI + ti;
-                        int *dst = a.nbl + ((size_t)(c + t) * ITILE + il) * G6_MAXNB;
-                        if (key.x < h2[k]) {
-                            if (nbn[k] < G6_MAXNB)
-                                dst[nbn[k]] = j0;
-                            ++nbn[k];
-                        }
-                        if (key.y < h2[k]) {
-                            if (nbn[k] < G6_MAXNB)
-                                dst[nbn[k]] = j0 + 1;
-                            ++nbn[k];
-                        }
-                    }
+            for (int k = 0; k < NI; ++k) {
+                if (tmin[k] < nnr[k]) {
+                    nnr[k] = tmin[k];
+                    nnt[k] = jt;
                 }
+                tmin[k] = INF;
             }
             if (++since_flush >= FLUSH) {
                 flush();
@@ -808,7 +898,7 @@ constexpr int ds_smem(int nt, int ni)
 }
 
 const Variant kVariants[] = {
-    {{128, 1, 2, 0, G6X_PREC_DS}, k_force_ds<128, 1, 2, false>, 128, ds_smem(128, 2)},
+    {{128, 1, 2, 0, G6X_PREC_DS}, k_force_ds<128, 1, 2, false, 3, 2>, 128, ds_smem(128, 2)},
     {{128, 1, 1, 0, G6X_PREC_DS}, k_force_ds<128, 1, 1, false>, 128, ds_smem(128, 1)},
     {{64, 4, 1, 0, G6X_PREC_DS}, k_force_ds<64, 4, 1, false>, 256, ds_smem(256, 1)},
     {{32, 8, 1, 0, G6X_PREC_DS}, k_force_ds<32, 8, 1, false>, 256, ds_smem(256, 1)},
@@ -817,6 +907,11 @@ const Variant kVariants[] = {
     {{32, 1, 1, 1, G6X_PREC_DS}, k_force_ds<32, 1, 1, true>, 32, ds_smem(32, 1)},
     {{128, 1, 1, 0, G6X_PREC_FP64}, k_force_64<false>, 128, 0},
     {{128, 1, 1, 1, G6X_PREC_FP64}, k_force_64<true>, 128, 0},
+    // alternative shapes, for tuning
+    {{128, 1, 2, 0, G6X_PREC_DS}, k_force_ds<128, 1, 2, false, 4, 2>, 128, ds_smem(128, 2)},
+    {{128, 1, 2, 0, G6X_PREC_DS}, k_force_ds<128, 1, 2, false, 3, 4>, 128, ds_smem(128, 2)},
+    {{128, 1, 3, 0, G6X_PREC_DS}, k_force_ds<128, 1, 3, false, 2, 2>, 128, ds_smem(128, 3)},
+    {{96, 1, 2, 0, G6X_PREC_DS}, k_force_ds<96, 1, 2, false, 4, 2>, 96, ds_smem(96, 2)},
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
@@ -941,7 +1036,7 @@ cudaError_t launch_predict(int prec, JStore js, Pred p, int nj, int nj_pad,
     if (prec == G6X_PREC_FP64)
         k_predict_64<<<blocks, 256, 0, s>>>(js, p, nj, nj_pad, t);
     else
-        k_predict_ds<<<blocks, 256, 0, s>>>(js, p, nj, nj_pad, t);
+        k_predict_ds<<<blocks, JT, 0, s>>>(js, p, nj, nj_pad, t);
     return cudaGetLastError();
 }
 
@@ -957,6 +1052,7 @@ cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
         return e;
     ForceArgs a;
     a.pt = p.pt;
+    a.trange = p.trange;
     a.p64 = p.p64;
     a.v64 = p.v64;
     a.irec = d_irec;
