@@ -400,11 +400,22 @@ def main():
                                       g6._p(jerk), g6._p(pot), g6._p(nnb))
             if rc < 0:
                 raise g6.G6Error(rc, "g6calc_lasthalf2")
+            # host corrector and next time steps of the block (row a6)
+            rc = lib.g6h_correct_block(m, T_BLK, g6._p(tj), g6._p(dt_cur), 0.01, 2.0 ** -4,
+                                       2.0 ** -40, g6._p(xc), g6._p(vc), g6._p(a0), g6._p(j0),
+                                       g6._p(acc), g6._p(jerk), g6._p(dt_new))
+            if rc < 0:
+                raise g6.G6Error(rc, "g6h_correct_block")
 
         acc = np.empty((m, 3))
         jerk = np.empty((m, 3))
         pot = np.empty(m)
         nnb = np.empty(m, dtype=np.int32)
+        a0 = np.ascontiguousarray(st["a0"][act])
+        j0 = np.ascontiguousarray(st["j0"][act])
+        dt_cur = np.full(m, T_BLK)
+        dt_new = np.empty(m)
+        xc, vc = xi.copy(), vi.copy()
         k2 = max(1, min(args.steps, 3))
         api_step()
         torch.cuda.synchronize()
@@ -423,7 +434,8 @@ def main():
                "h2d_bytes_per_step": int(m * (g6.JREC.itemsize + g6.IREC.itemsize)),
                "d2h_bytes_per_step": int(m * g6.OUT.itemsize + 4),
                "ms_per_step": t_e2e * 1e3,
-               "api": "g6x_set_j_particles + g6_set_ti + g6calc_firsthalf + g6calc_lasthalf2"}
+               "api": "g6x_set_j_particles + g6_set_ti + g6calc_firsthalf + g6calc_lasthalf2"
+                      " + g6h_correct_block (host corrector and time steps)"}
 
     cpu = None
     accuracy = None

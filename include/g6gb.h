@@ -308,6 +308,19 @@ g6h_sim *g6h_create(int clusterid, int n, const double *m, const double *x,
  * dt_max).  Returns 0 or a negative error. */
 int g6h_run(g6h_sim *s, double t_end);
 
+/* The driver's corrector and time-step choice for n particles that reach
+ * the block time t_blk together (Sect. 2; Makino & Aarseth 1992 corrector,
+ * Aarseth 1985 criterion with a'' taken at the end of the step, power-of-two
+ * quantisation that may double only at commensurate times).  Per particle:
+ * t0, dt = time and step of its last correction; xp, vp [n][3] = predicted
+ * state at t_blk, overwritten with the corrected x1, v1; (a0, j0) force at
+ * t0 and (a1, j1) at t_blk [n][3]; dt_new = next step, -1 where it would fall
+ * below dt_min.  Returns the number of such particles, or G6_EINVAL. */
+int g6h_correct_block(int n, double t_blk, const double *t0, const double *dt,
+                      double eta, double dt_max, double dt_min, double *xp,
+                      double *vp, const double *a0, const double *j0,
+                      const double *a1, const double *j1, double *dt_new);
+
 /* Copy the current state out (any pointer may be NULL): x, v, acc, jerk
  * [n][3]; t, dt [n]. */
 int g6h_get_state(const g6h_sim *s, double *x, double *v, double *acc,

@@ -95,6 +95,31 @@ double quantise(double dt, double req, double t, double dt_max)
 
 extern "C" {
 
+int g6h_correct_block(int n, double t_blk, const double *t0, const double *dt, double eta,
+                      double dt_max, double dt_min, double *xp, double *vp, const double *a0,
+                      const double *j0, const double *a1, const double *j1, double *dt_new)
+{
+    if (n < 0 || (n > 0 && (!t0 || !dt || !xp || !vp || !a0 || !j0 || !a1 || !j1 || !dt_new)))
+        return G6_EINVAL;
+    int small = 0;
+    for (int k = 0; k < n; ++k) {
+        const double h = t_blk - t0[k];
+        double d2[3], d3[3], d2e[3];
+        correct(h, &a0[3 * k], &j0[3 * k], &a1[3 * k], &j1[3 * k], &xp[3 * k], &vp[3 * k], d2,
+                d3);
+        for (int d = 0; d < 3; ++d)
+            d2e[d] = d2[d] + h * d3[d];
+        const double req = aarseth(&a1[3 * k], &j1[3 * k], d2e, d3, eta);
+        double nd = quantise(dt[k], req, t_blk, dt_max);
+        if (!(nd >= dt_min)) {
+            nd = -1.0;
+            ++small;
+        }
+        dt_new[k] = nd;
+    }
+    return small;
+}
+
 g6h_sim *g6h_create(int cid, int n, const double *m, const double *x, const double *v,
                     double eps2, double eta, double eta_s, double dt_max, double dt_min,
                     int *err)

@@ -47,7 +47,7 @@ EXPORTS = [
     "g6x_set_precision", "g6x_set_ni_max", "g6x_set_stream", "g6x_set_allocator",
     "g6x_set_j_particles", "g6x_strerror", "g6x_set_j_dev", "g6x_calc_dev",
     "g6x_calc_dev_noalloc", "g6x_sync", "g6x_set_variant", "g6x_get_predicted", "g6x_last_config",
-    "g6x_launch_count", "g6x_set_timing", "g6x_get_timing", "g6h_create", "g6h_run", "g6h_get_state", "g6h_energy",
+    "g6x_launch_count", "g6x_set_timing", "g6x_get_timing", "g6h_correct_block", "g6h_create", "g6h_run", "g6h_get_state", "g6h_energy",
     "g6h_stats", "g6h_destroy",
 ]
 
@@ -95,6 +95,7 @@ def lib():
             "g6x_launch_count": (C.c_longlong, [I]),
             "g6x_set_timing": (I, [I, I]),
             "g6x_get_timing": (I, [I, P, P]),
+            "g6h_correct_block": (I, [I, D, P, P, D, D, D, P, P, P, P, P, P, P]),
             "g6h_create": (P, [I, I, P, P, P, D, D, D, D, D, P]),
             "g6h_run": (I, [P, D]),
             "g6h_get_state": (I, [P, P, P, P, P, P, P]),
@@ -337,6 +338,23 @@ def g6x_use_cuda_allocator():
 
 
 # --------------------------------------------------------- Hermite driver --
+
+def g6h_correct_block(t_blk, t0, dt, eta, dt_max, dt_min, xp, vp, a0, j0, a1, j1):
+    """Host Hermite corrector + next step for a block (C++).  Returns
+    (x1, v1, dt_new, n_too_small); xp and vp are not modified."""
+    xp = _d(xp).reshape(-1, 3).copy()
+    vp = _d(vp).reshape(-1, 3).copy()
+    n = xp.shape[0]
+    t0 = _d(np.broadcast_to(np.asarray(t0, dtype=np.float64), (n,)))
+    dt = _d(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
+    a0, j0, a1, j1 = (_d(q, (n, 3)) for q in (a0, j0, a1, j1))
+    dt_new = np.empty(n)
+    rc = _check(lib().g6h_correct_block(n, float(t_blk), _p(t0), _p(dt), float(eta),
+                                        float(dt_max), float(dt_min), _p(xp), _p(vp), _p(a0),
+                                        _p(j0), _p(a1), _p(j1), _p(dt_new)),
+                "g6h_correct_block")
+    return xp, vp, dt_new, rc
+
 
 class G6HSim:
     """Owner of a g6h_sim handle (the C++ Hermite block-time-step driver)."""
