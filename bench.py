@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune", default="", help="run the autotuner first and write its table here")
+    ap.add_argument("--tune-file", default="", help="load an autotuner table before timing")
     ap.add_argument("--variant", type=int, default=-1)
     ap.add_argument("--grid", type=int, default=0)
     return ap.parse_args()
@@ -269,6 +271,8 @@ def main():
     g6.g6x_set_stream(CID, stream.cuda_stream)
     if args.variant >= 0 or args.grid > 0:
         g6.g6x_set_variant(CID, args.variant, args.grid)
+    if args.tune_file:
+        g6.g6x_load_tuning(args.tune_file)
 
     def to_dev(a):
         return torch.from_numpy(a.view(np.uint8).copy()).to(dev)
@@ -278,6 +282,11 @@ def main():
     d_irec = to_dev(irec)
     d_out = torch.empty(m * g6.OUT.itemsize, dtype=torch.uint8, device=dev)
     g6.g6x_set_j_dev(CID, n, d_jall.data_ptr())
+    tuned = None
+    if args.tune:
+        t0 = time.perf_counter()
+        tuned = {"sizes": g6.g6x_autotune(CID, n, m, args.tune), "file": args.tune,
+                 "seconds": round(time.perf_counter() - t0, 1)}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
@@ -497,6 +506,8 @@ def main():
         }
         if sweep is not None:
             line["sweep"] = sweep
+        if tuned is not None:
+            line["autotune"] = tuned
         print(json.dumps(line))
     g6.g6_close(CID)
     if ws > 1:

@@ -276,6 +276,23 @@ int g6x_set_timing(int clusterid, int enable);
  * Synchronises the stream.  Either pointer may be NULL. */
 int g6x_get_timing(int clusterid, double ms[4], long long count[4]);
 
+/* Autotuner: for each power-of-two block size m = 16 .. m_max (sizes above
+ * 2^17 reuse the 2^17 result), time every force-kernel variant of the
+ * current precision whose i-tile suits m, on grids of one and two times the
+ * resident CTAs, against the nj j-particles in j-memory (i-particles taken
+ * from the first m slots), and keep the fastest in a process-wide table that
+ * later calculations without a pinned variant use.  Writes the table to
+ * `path` when not NULL.  Synchronous; allocates two scratch buffers.
+ * Returns the number of sizes tuned or a negative error. */
+int g6x_autotune(int clusterid, int nj, int m_max, const char *path);
+
+/* Load a table written by g6x_autotune (g6_open loads the file named by
+ * env G6GB_TUNE_FILE once).  Returns entries read or G6_EINVAL. */
+int g6x_load_tuning(const char *path);
+
+/* Forget every tuned entry (back to the built-in choice).  Returns 0. */
+int g6x_clear_tuning(void);
+
 /* Launch statistics of the last calculation: kernel variant id, threads
  * along i and j, i-particles per thread, grid size and j-tiles.  Any pointer
  * may be NULL. */

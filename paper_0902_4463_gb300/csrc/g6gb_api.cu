@@ -10,7 +10,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <mutex>
+#include <sstream>
+#include <string>
 #include <utility>
 #include <vector>
 
@@ -554,6 +557,12 @@ int g6x_open_ex(int cid, int nj_max, int ni_max)
 
 int g6_open(int cid)
 {
+    static bool tuning_loaded = false;
+    const char *tf = std::getenv("G6GB_TUNE_FILE");
+    if (!tuning_loaded && tf && *tf) {
+        tuning_loaded = true;
+        g6x_load_tuning(tf);
+    }
     return g6x_open_ex(cid, env_int("G6GB_NJ", G6_NJ_DEFAULT), g6_npipes());
 }
 
@@ -1017,6 +1026,170 @@ extern "C" int g6x_calc_dev_noalloc(int cid, double ti, int nj, int ni,
     c->launches += 2;
     c->last_cfg = cfg;
     c->lists_ready = false;
+    return 0;
+}
+
+// ------------------------------------------------------------ autotuner
+//
+// For each power-of-two block size the tuner times every force-kernel
+// variant of the current precision whose i-tile suits the block, on grids of
+// one and two times the resident CTAs, with i-particles taken from the first
+// m j-slots, and keeps the fastest in the process-wide table that
+// choose_config consults.  Sizes above 2^17 reuse the 2^17 choice.
+
+namespace {
+
+int write_tuning(const char *path)
+{
+    std::ofstream f(path);
+    if (!f)
+        return G6_EINVAL;
+    f << "# g6gb force-kernel tuning table: precision log2(m) variant grid_multiplier\n";
+    int n = 0;
+    for (int prec = 0; prec < 2; ++prec)
+        for (int b = 0; b < g6::TUNE_BUCKETS; ++b) {
+            int v, g;
+            if (g6::tune_exact(prec, b, &v, &g)) {
+                f << prec << " " << b << " " << v << " " << g << "\n";
+                ++n;
+            }
+        }
+    return f ? n : G6_EIO;
+}
+
+}  // namespace
+
+extern "C" int g6x_autotune(int cid, int nj, int m_max, const char *path)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (c->pending || nj < 1 || nj > c->cap || m_max < 16)
+        return G6_EINVAL;
+    if (m_max > nj)
+        m_max = nj;
+    int rc = flush_jstage(*c);
+    if (!rc)
+        rc = predict_if_stale(*c, nj);
+    if (rc)
+        return rc;
+    const int nj_pad = round_up(nj, JT);
+    const int m_cap = m_max < (1 << 17) ? m_max : (1 << 17);
+    g6x_irec *d_i = (g6x_irec *)dev_alloc(sizeof(g6x_irec) * m_cap);
+    g6x_out *d_o = (g6x_out *)dev_alloc(sizeof(g6x_out) * m_cap);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!d_i || !d_o || cudaEventCreate(&e0) != cudaSuccess
+        || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        dev_free(d_i);
+        dev_free(d_o);
+        if (e0)
+            cudaEventDestroy(e0);
+        return G6_ENOMEM;
+    }
+    cudaError_t e = g6::launch_irec_from_store(c->js, d_i, m_cap, c->stream);
+    c->launches += 1;
+    int tuned = 0;
+    bool lost_work = false;
+    for (int m = 16; e == cudaSuccess && m <= m_cap; m *= 2) {
+        float best = 1e30f;
+        int bv = -1, bg = 1;
+        for (int v = 0; v < g6::variant_count() && e == cudaSuccess; ++v) {
+            const g6::VariantInfo vi = g6::variant_info(v);
+            if (vi.prec != c->prec || vi.list || vi.ti * vi.nper > 16 * m)
+                continue;
+            int occ = g6::variant_occupancy(v);
+            if (occ < 1)
+                continue;
+            int last_grid = -1;
+            for (int gm = 1; gm <= 2 && e == cudaSuccess; ++gm) {
+                ForceConfig cfg = g6::choose_config(c->prec, m, nj_pad, 0, c->sm_count, v,
+                                                    c->sm_count * occ * gm);
+                if (cfg.grid == last_grid)
+                    continue;
+                last_grid = cfg.grid;
+                if (grow_dev(c->d_part, c->part_cap, g6::partial_slots(cfg))) {
+                    lost_work = true;
+                    continue;
+                }
+                float t_best = 1e30f;
+                for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+                    e = cudaEventRecord(e0, c->stream);
+                    if (e == cudaSuccess)
+                        e = g6::launch_force(cfg, c->pred, d_i, m, 1e-6, c->d_part, nullptr,
+                                             nullptr, c->d_err, c->stream);
+                    if (e == cudaSuccess)
+                        e = g6::launch_reduce(cfg, c->d_part, nullptr, nullptr, c->js.idx, m,
+                                              d_o, nullptr, nullptr, c->stream);
+                    if (e == cudaSuccess)
+                        e = cudaEventRecord(e1, c->stream);
+                    if (e == cudaSuccess)
+                        e = cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    if (e == cudaSuccess)
+                        e = cudaEventElapsedTime(&ms, e0, e1);
+                    c->launches += 2;
+                    if (r > 0 && ms < t_best)
+                        t_best = ms;
+                }
+                if (t_best < best) {
+                    best = t_best;
+                    bv = v;
+                    bg = gm;
+                }
+            }
+        }
+        if (bv >= 0) {
+            g6::tune_set(c->prec, g6::tune_bucket(m), bv, bg);
+            ++tuned;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dev_free(d_i);
+    dev_free(d_o);
+    if (e != cudaSuccess)
+        return cuda_err(e);
+    if (lost_work && tuned == 0)
+        return G6_ENOMEM;
+    if (path) {
+        int w = write_tuning(path);
+        if (w < 0)
+            return w;
+    }
+    return tuned;
+}
+
+extern "C" int g6x_load_tuning(const char *path)
+{
+    if (!path)
+        return G6_EINVAL;
+    std::ifstream f(path);
+    if (!f)
+        return G6_EINVAL;
+    std::string line;
+    int n = 0;
+    while (std::getline(f, line)) {
+        if (line.empty() || line[0] == '#')
+            continue;
+        std::istringstream is(line);
+        int prec, b, v, g;
+        if (!(is >> prec >> b >> v >> g))
+            return G6_EINVAL;
+        if (prec < 0 || prec > 1 || b < 0 || b >= g6::TUNE_BUCKETS || v < 0
+            || v >= g6::variant_count() || g < 1 || g > 8
+            || g6::variant_info(v).prec != prec || g6::variant_info(v).list)
+            return G6_EINVAL;
+        g6::tune_set(prec, b, v, g);
+        ++n;
+    }
+    return n;
+}
+
+extern "C" int g6x_clear_tuning(void)
+{
+    g6::tune_clear();
     return 0;
 }
 

@@ -91,6 +91,16 @@ ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
 // Number of Partial slots a launch with this configuration writes.
 size_t partial_slots(const ForceConfig &cfg);
 
+// Autotuning table (see g6x_autotune): per precision and power-of-two
+// bucket of ni, the force variant and grid multiplier to use.
+constexpr int TUNE_BUCKETS = 32;
+int tune_bucket(int ni);
+void tune_set(int prec, int bucket, int variant, int gmul);
+bool tune_get(int prec, int bucket, int *variant, int *gmul);
+bool tune_exact(int prec, int bucket, int *variant, int *gmul);
+void tune_clear();
+
+cudaError_t launch_irec_from_store(JStore js, g6x_irec *out, int m, cudaStream_t s);
 cudaError_t launch_scatter(const g6x_jrec *d_rec, int n, JStore js,
                            cudaStream_t s);
 cudaError_t launch_init_store(JStore js, cudaStream_t s);

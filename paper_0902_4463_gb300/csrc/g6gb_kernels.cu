@@ -178,6 +178,26 @@ __global__ void k_scatter(const g6x_jrec *__restrict__ rec, int n, JStore js)
     js.idx[a] = r.index;
 }
 
+// Tuning input: i-records built from the first m j-slots of j-memory.
+__global__ void k_irec_from_store(JStore js, g6x_irec *out, int m)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m || k >= js.cap)
+        return;
+    g6x_irec r;
+    r.x[0] = js.x0[k];
+    r.x[1] = js.x0[js.cap + k];
+    r.x[2] = js.x0[2 * js.cap + k];
+    double4 v = js.v64[k];
+    r.v[0] = v.x;
+    r.v[1] = v.y;
+    r.v[2] = v.z;
+    r.h2 = 0.0;
+    r.index = js.idx[k];
+    r.pad = 0;
+    out[k] = r;
+}
+
 // ----------------------------------------------------------------- K1 ---
 
 // Eq. 1 and Eq. 2 with the DS position of Sect. 2.2: the Taylor increment
@@ -956,10 +976,87 @@ int variant_occupancy(int v)
     return g_occ[v];
 }
 
+// ------------------------------------------------------------- tuning ---
+//
+// Best (variant, grid multiplier) per precision and power-of-two block size,
+// filled by the autotuner (g6x_autotune) or loaded from its file.  Grid =
+// multiplier x SMs x resident CTAs per SM.  Buckets above the largest tuned
+// one reuse that one.
+
+namespace {
+struct TuneEntry {
+    int variant = -1;
+    int gmul = 1;
+};
+TuneEntry g_tune[2][TUNE_BUCKETS];
+}  // namespace
+
+int tune_bucket(int ni)
+{
+    int b = 0;
+    while (b < TUNE_BUCKETS - 1 && (2 << b) <= ni)
+        ++b;
+    return b;
+}
+
+void tune_set(int prec, int bucket, int variant, int gmul)
+{
+    if (prec < 0 || prec > 1 || bucket < 0 || bucket >= TUNE_BUCKETS)
+        return;
+    g_tune[prec][bucket].variant = variant;
+    g_tune[prec][bucket].gmul = gmul < 1 ? 1 : gmul;
+}
+
+bool tune_get(int prec, int bucket, int *variant, int *gmul)
+{
+    if (prec < 0 || prec > 1 || bucket < 0 || bucket >= TUNE_BUCKETS)
+        return false;
+    int b = -1;
+    if (g_tune[prec][bucket].variant >= 0) {
+        b = bucket;
+    } else {
+        int top = -1;
+        for (int q = 0; q < TUNE_BUCKETS; ++q)
+            if (g_tune[prec][q].variant >= 0)
+                top = q;
+        if (top >= 0 && bucket > top)
+            b = top;
+    }
+    if (b < 0)
+        return false;
+    *variant = g_tune[prec][b].variant;
+    *gmul = g_tune[prec][b].gmul;
+    return true;
+}
+
+bool tune_exact(int prec, int bucket, int *variant, int *gmul)
+{
+    if (prec < 0 || prec > 1 || bucket < 0 || bucket >= TUNE_BUCKETS
+        || g_tune[prec][bucket].variant < 0)
+        return false;
+    *variant = g_tune[prec][bucket].variant;
+    *gmul = g_tune[prec][bucket].gmul;
+    return true;
+}
+
+void tune_clear()
+{
+    for (auto &row : g_tune)
+        for (auto &e : row)
+            e = TuneEntry();
+}
+
 ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
                           int force_variant, int force_grid)
 {
     int v;
+    int gmul = 1, tv = -1;
+    if (force_variant < 0 && !list && tune_get(prec, tune_bucket(ni), &tv, &gmul)
+        && tv >= 0 && tv < kNumVariants && kVariants[tv].info.prec == prec
+        && !kVariants[tv].info.list)
+        force_variant = tv;
+    else
+        gmul = 1;
     if (force_variant >= 0 && force_variant < kNumVariants) {
         v = force_variant;
     } else if (prec == G6X_PREC_FP64) {
@@ -993,7 +1090,7 @@ ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
     int occ = variant_occupancy(v);
     if (occ < 1)
         occ = 1;
-    long long g = force_grid > 0 ? force_grid : (long long)sm_count * occ;
+    long long g = force_grid > 0 ? force_grid : (long long)sm_count * occ * gmul;
     if (g > c.work)
         g = c.work;
     if (g < 1)
@@ -1013,6 +1110,14 @@ cudaError_t launch_init_store(JStore js, cudaStream_t s)
     if (blocks > 65535)
         blocks = 65535;
     k_init_store<<<blocks, 256, 0, s>>>(js);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_irec_from_store(JStore js, g6x_irec *out, int m, cudaStream_t s)
+{
+    if (m <= 0)
+        return cudaSuccess;
+    k_irec_from_store<<<(m + 255) / 256, 256, 0, s>>>(js, out, m);
     return cudaGetLastError();
 }
 

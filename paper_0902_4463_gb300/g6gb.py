@@ -46,7 +46,8 @@ EXPORTS = [
     "g6_read_neighbour_list", "g6_get_neighbour_list", "g6x_open_ex",
     "g6x_set_precision", "g6x_set_ni_max", "g6x_set_stream", "g6x_set_allocator",
     "g6x_set_j_particles", "g6x_strerror", "g6x_set_j_dev", "g6x_calc_dev",
-    "g6x_calc_dev_noalloc", "g6x_sync", "g6x_set_variant", "g6x_get_predicted", "g6x_last_config",
+    "g6x_calc_dev_noalloc", "g6x_sync", "g6x_set_variant",
+    "g6x_autotune", "g6x_load_tuning", "g6x_clear_tuning", "g6x_get_predicted", "g6x_last_config",
     "g6x_launch_count", "g6x_set_timing", "g6x_get_timing", "g6h_correct_block", "g6h_create", "g6h_run", "g6h_get_state", "g6h_energy",
     "g6h_stats", "g6h_destroy",
 ]
@@ -89,7 +90,10 @@ def lib():
             "g6x_set_j_dev": (I, [I, I, P]),
             "g6x_calc_dev": (I, [I, D, I, I, P, D, I, P]),
             "g6x_calc_dev_noalloc": (I, [I, D, I, I, P, D, P]),
-            "g6x_sync": (I, [I]), "g6x_set_variant": (I, [I, I, I]),
+            "g6x_sync": (I, [I]),
+            "g6x_autotune": (I, [I, I, I, C.c_char_p]),
+            "g6x_load_tuning": (I, [C.c_char_p]),
+            "g6x_clear_tuning": (I, []), "g6x_set_variant": (I, [I, I, I]),
             "g6x_get_predicted": (I, [I, I, P, P, P, P, P]),
             "g6x_last_config": (I, [I, P, P, P, P, P, P]),
             "g6x_launch_count": (C.c_longlong, [I]),
@@ -263,6 +267,20 @@ def g6x_calc_dev_noalloc(cid, ti, nj, ni, d_irec_ptr, eps2, d_out_ptr):
                                              C.c_void_p(int(d_irec_ptr)), float(eps2),
                                              C.c_void_p(int(d_out_ptr))),
                   "g6x_calc_dev_noalloc")
+
+
+def g6x_autotune(cid, nj, m_max, path=None):
+    return _check(lib().g6x_autotune(cid, int(nj), int(m_max),
+                                     None if path is None else str(path).encode()),
+                  "g6x_autotune")
+
+
+def g6x_load_tuning(path):
+    return _check(lib().g6x_load_tuning(str(path).encode()), "g6x_load_tuning")
+
+
+def g6x_clear_tuning():
+    return lib().g6x_clear_tuning()
 
 
 def g6x_sync(cid):

@@ -90,3 +90,17 @@ def test_product_does_not_import_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "oracle.h" not in text and "liboracle" not in text, f
+
+
+def test_tuning_table_file_round_trip(lib, tmp_path):
+    p = tmp_path / "tune.txt"
+    p.write_text("# table\n0 4 4 1\n0 5 3 2\n0 17 0 1\n1 10 7 1\n")
+    assert g6gb.g6x_load_tuning(p) == 4
+    bad = tmp_path / "bad.txt"
+    bad.write_text("0 4 99 1\n")                  # unknown variant
+    with pytest.raises(g6gb.G6Error):
+        g6gb.g6x_load_tuning(bad)
+    bad.write_text("1 4 0 1\n")                   # DS variant under FP64
+    with pytest.raises(g6gb.G6Error):
+        g6gb.g6x_load_tuning(bad)
+    assert g6gb.g6x_clear_tuning() == 0

@@ -184,3 +184,25 @@ def test_hermite_driver_plummer_1024_energy_drift(open_ctx, orc, prec):
     assert stats["nblocks"] > 10 and stats["hist"].sum() == stats["nblocks"]
     assert dE_gpu <= 2 * max(dE_orc, 1e-12), (dE_gpu, dE_orc)
     sim.close()
+
+
+def test_autotuner_table_is_used_and_results_stay_correct(open_ctx, orc, tmp_path):
+    n, eps2 = 8192, 1e-4
+    m, x, v = ics.plummer(n, 31)
+    idx = np.arange(n)
+    cid = open_ctx(n, n)
+    load_j(cid, x, v, m)
+    path = tmp_path / "tune.txt"
+    try:
+        tuned = g6.g6x_autotune(cid, n, 512, path)
+        assert tuned == 6                                 # m = 16 .. 512
+        assert g6.g6x_load_tuning(path) == tuned
+        for m_act in (16, 100, 512, 3000):
+            act = ics.permutation(n, m_act)[:m_act]
+            acc, jerk, pot, nnb = sweep(cid, n, x[act], v[act], act, eps2, 0.0)
+            oa, oj, op, onn, onr = orc.force(x[act], v[act], act, x, v, m, idx, eps2)
+            ea = rel_err_vec(acc, oa)
+            assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5
+            check_nn(onn, onr, nnb, x[act], x, idx)
+    finally:
+        g6.g6x_clear_tuning()
