@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tune", default="", help="run the autotuner first and write its table here")
     ap.add_argument("--tune-file", default="", help="load an autotuner table before timing")
+    ap.add_argument("--prec", default="ds", choices=["ds", "ds_x64"],
+                    help="DS predictor: the paper's DS + SP add (ds) or an FP64 add (ds_x64)")
     ap.add_argument("--variant", type=int, default=-1)
     ap.add_argument("--grid", type=int, default=0)
     return ap.parse_args()
@@ -273,6 +275,8 @@ def main():
         g6.g6x_set_variant(CID, args.variant, args.grid)
     if args.tune_file:
         g6.g6x_load_tuning(args.tune_file)
+    DS_MODE = g6.G6X_PREC_DS_X64 if args.prec == "ds_x64" else g6.G6X_PREC_DS
+    g6.g6x_set_precision(CID, DS_MODE)
 
     def to_dev(a):
         return torch.from_numpy(a.view(np.uint8).copy()).to(dev)
@@ -359,7 +363,7 @@ def main():
     g6.g6x_set_precision(CID, g6.G6X_PREC_FP64)
     ms64, ph64, c64, _ = timed(m64, d_j64, d_i64, d_o64, 2, 1)
     out64 = d_o64.cpu().numpy().view(g6.OUT)
-    g6.g6x_set_precision(CID, g6.G6X_PREC_DS)
+    g6.g6x_set_precision(CID, DS_MODE)
     msds, phds, cds, _ = timed(m64, d_j64, d_i64, d_o64, 3, 2)
     rate64 = m64 * n / (ph64[2] / max(1, c64[2]) * 1e-3)
     rateds = m64 * n / (phds[2] / max(1, cds[2]) * 1e-3)
@@ -380,7 +384,10 @@ def main():
                           "interactions_per_s": mm * n / (mss * 1e-3),
                           "force_interactions_per_s": mm * n / (fms * 1e-3),
                           "force_frac_fp32_peak": FLOPS_PER_PAIR * mm * n / (fms * 1e-3) / 1e12 / peak,
-                          "predict_ms": phs[1] / max(1, cs[1]), "variant": c["variant"],
+                          "predict_ms": phs[1] / max(1, cs[1]),
+                          "scatter_ms": phs[0] / max(1, cs[0]),
+                          "force_ms": fms, "reduce_ms": phs[3] / max(1, cs[3]),
+                          "variant": c["variant"],
                           "grid": c["grid"]})
             mm *= 2
 
@@ -478,7 +485,7 @@ def main():
             "gflops_60": value * FLOPS_PER_PAIR / 1e9,
             "gflops_66": value * FLOPS_PER_PAIR_DS / 1e9,
             "config": {"workload": "plummer_N%d_full_block_sweep" % n, "n": n, "m": m,
-                       "eps2": EPS2, "t_blk": T_BLK, "seed": SEED,
+                       "eps2": EPS2, "t_blk": T_BLK, "seed": SEED, "predictor": args.prec,
                        "l2": "256 MiB buffer written between timed steps",
                        "parallelism": "replicas" if ws > 1 else "single_gpu",
                        "kernel": cfg},

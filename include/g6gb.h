@@ -11,8 +11,9 @@
  *
  * Precision (Sect. 2.2, 2.3): bulk pair arithmetic in FP32; positions are
  * double-single (hi + lo floats) and separations use the simplified DS
- * difference of Eq. 3; predicted positions are formed in FP64 and split into
- * DS; partial sums are carried as compensated FP32 pairs and reduced in FP64.
+ * difference of Eq. 3; predicted positions come from the DS + SP addition of
+ * Sect. 2.2 (or, with G6X_PREC_DS_X64, from an FP64 addition split into DS);
+ * partial sums are carried as compensated FP32 pairs and reduced in FP64.
  * g6x_set_precision(cid, G6X_PREC_FP64) selects an all-FP64 path instead.
  *
  * Units: G = 1.  pot is the negative physical potential, -sum m_j/sqrt(r^2+eps2).
@@ -150,8 +151,11 @@ int g6_get_neighbour_list(int clusterid, int ipipe, int maxlength, int *nblen,
 
 /* ------------------------------------------------------------ extensions */
 
-#define G6X_PREC_DS   0   /* FP32 + double-single (default, Sect. 2.2-2.3) */
-#define G6X_PREC_FP64 1   /* all-FP64 prediction and force                 */
+#define G6X_PREC_DS     0 /* FP32 force with DS separations (Eq. 3) and the
+                             DS + SP predictor of Sect. 2.2 (default)       */
+#define G6X_PREC_FP64   1 /* all-FP64 prediction and force                 */
+#define G6X_PREC_DS_X64 2 /* as G6X_PREC_DS, but predicted positions are
+                             formed in FP64 and then split into DS           */
 
 /* As g6_open with an explicit j capacity and i-per-call limit. */
 int g6x_open_ex(int clusterid, int nj_max, int ni_max);

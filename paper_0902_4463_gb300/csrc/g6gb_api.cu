@@ -83,7 +83,8 @@ struct Ctx {
     int dev = 0, sm_count = 0;
     cudaStream_t own = nullptr;
     cudaStream_t stream = nullptr;
-    int cap = 0, ni_max = 0, prec = G6X_PREC_DS;
+    int cap = 0, ni_max = 0, prec = G6X_PREC_DS;   // force arithmetic
+    int pmode = G6X_PREC_DS;                           // G6X_PREC_* as selected
     g6::JStore js{};
     g6::Pred pred{};
     // j-memory updates staged on the host, uploaded by the next calculation
@@ -106,9 +107,9 @@ struct Ctx {
     int *d_err = nullptr, *h_err = nullptr;
     // prediction bookkeeping per precision mode
     double t_set = 0.0;
-    double t_pred[2] = {NAN, NAN};
-    int nj_pred[2] = {-1, -1};
-    long long ver = 0, ver_pred[2] = {-1, -1};
+    double t_pred[3] = {NAN, NAN, NAN};
+    int nj_pred[3] = {-1, -1, -1};
+    long long ver = 0, ver_pred[3] = {-1, -1, -1};
     // calculation in flight
     bool pending = false;
     int latched = 0;
@@ -220,7 +221,7 @@ void free_ctx(Ctx &c)
     if (c.stream)
         cudaStreamSynchronize(c.stream);
     g6::JStore &js = c.js;
-    void *dptrs[] = {js.x0, js.t0, js.v0m, js.a2f, js.j6f, js.v64, js.a264, js.j664,
+    void *dptrs[] = {js.x0, js.xds, js.xds2, js.t0, js.v0m, js.a2f, js.j6f, js.v64, js.a264, js.j664,
                      js.idx, c.pred.pt, c.pred.trange, c.pred.p64, c.pred.v64,
                      c.d_jst, c.d_irec, c.d_out, c.d_part, c.d_nbl_part, c.d_nbc_part,
                      c.d_nbl, c.d_nblen, c.d_err};
@@ -347,7 +348,9 @@ int flush_jstage(Ctx &c)
 // that prediction (Sect. 2.1: the O(n) predictor runs once per block time).
 int predict_if_stale(Ctx &c, int nj)
 {
-    int m = c.prec;
+    // kind of prediction: the two DS predictors share one output buffer
+    const int m = c.pmode == G6X_PREC_FP64 ? g6::PRED_FP64
+                  : c.pmode == G6X_PREC_DS_X64 ? g6::PRED_DS_X64 : g6::PRED_DS;
     if (c.t_pred[m] == c.t_set && c.nj_pred[m] == nj && c.ver_pred[m] == c.ver)
         return 0;
     int nj_pad = round_up(nj > 0 ? nj : 1, JT);
@@ -362,6 +365,10 @@ int predict_if_stale(Ctx &c, int nj)
     c.t_pred[m] = c.t_set;
     c.nj_pred[m] = nj;
     c.ver_pred[m] = c.ver;
+    if (m != g6::PRED_FP64) {
+        const int other = m == g6::PRED_DS ? g6::PRED_DS_X64 : g6::PRED_DS;
+        c.ver_pred[other] = -1;
+    }
     return 0;
 }
 
@@ -510,6 +517,8 @@ int g6x_open_ex(int cid, int nj_max, int ni_max)
     g6::JStore &js = c.js;
     js.cap = c.cap;
     js.x0 = (double *)dev_alloc(3 * n * sizeof(double));
+    js.xds = (float4 *)dev_alloc(n * sizeof(float4));
+    js.xds2 = (float2 *)dev_alloc(n * sizeof(float2));
     js.t0 = (double *)dev_alloc(n * sizeof(double));
     js.v0m = (float4 *)dev_alloc(n * sizeof(float4));
     js.a2f = (float4 *)dev_alloc(n * sizeof(float4));
@@ -524,7 +533,7 @@ int g6x_open_ex(int cid, int nj_max, int ni_max)
     c.pred.v64 = (double4 *)dev_alloc(n * sizeof(double4));
     c.d_err = (int *)dev_alloc(sizeof(int));
     c.h_err = (int *)host_alloc(sizeof(int));
-    if (!js.x0 || !js.t0 || !js.v0m || !js.a2f || !js.j6f || !js.v64 || !js.a264
+    if (!js.x0 || !js.xds || !js.xds2 || !js.t0 || !js.v0m || !js.a2f || !js.j6f || !js.v64 || !js.a264
         || !js.j664 || !js.idx || !c.pred.pt || !c.pred.trange || !c.pred.p64
         || !c.pred.v64 || !c.d_err || !c.h_err)
         rc = G6_ENOMEM;
@@ -582,9 +591,10 @@ int g6x_set_precision(int cid, int mode)
     Ctx *c = get(cid, &err);
     if (!c)
         return err;
-    if (mode != G6X_PREC_DS && mode != G6X_PREC_FP64)
+    if (mode != G6X_PREC_DS && mode != G6X_PREC_FP64 && mode != G6X_PREC_DS_X64)
         return G6_EINVAL;
-    c->prec = mode;
+    c->pmode = mode;
+    c->prec = mode == G6X_PREC_FP64 ? G6X_PREC_FP64 : G6X_PREC_DS;
     return 0;
 }
 

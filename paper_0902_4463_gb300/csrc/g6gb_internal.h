@@ -29,6 +29,8 @@ struct Partial {
 // j-memory (the j-store), structure of arrays, capacity `cap` (multiple of JT).
 struct JStore {
     double *x0;        // 3 planes of cap doubles: x, y, z at t0
+    float4 *xds;       // the same position as double-single: (x_hi, y_hi, z_hi, x_lo)
+    float2 *xds2;      //                                     (y_lo, z_lo)
     double *t0;        // time of the stored state
     float4 *v0m;       // (vx, vy, vz, m)              FP32 copy
     float4 *a2f;       // (ax/2, ay/2, az/2, 0)         FP32 copy
@@ -104,7 +106,11 @@ cudaError_t launch_irec_from_store(JStore js, g6x_irec *out, int m, cudaStream_t
 cudaError_t launch_scatter(const g6x_jrec *d_rec, int n, JStore js,
                            cudaStream_t s);
 cudaError_t launch_init_store(JStore js, cudaStream_t s);
-cudaError_t launch_predict(int prec, JStore js, Pred p, int nj, int nj_pad,
+// How K1 predicts: the paper's double-single predictor (FP32 Taylor terms
+// and a DS + SP addition, Sect. 2.2), the same with the addition done in FP64,
+// or everything in FP64 for the FP64 force kernel.
+enum PredKind { PRED_DS = 0, PRED_FP64 = 1, PRED_DS_X64 = 2 };
+cudaError_t launch_predict(int kind, JStore js, Pred p, int nj, int nj_pad,
                            double t, int sm_count, cudaStream_t s);
 cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
                          const g6x_irec *d_irec, int ni, double eps2,

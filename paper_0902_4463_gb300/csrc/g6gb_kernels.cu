@@ -142,6 +142,8 @@ __global__ void k_init_store(JStore js)
         js.x0[k] = FAR;
         js.x0[js.cap + k] = FAR;
         js.x0[2 * js.cap + k] = FAR;
+        js.xds[k] = make_float4((float)FAR, (float)FAR, (float)FAR, 0.f);
+        js.xds2[k] = make_float2(0.f, 0.f);
         js.t0[k] = 0.0;
         js.v0m[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         js.a2f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -168,6 +170,11 @@ __global__ void k_scatter(const g6x_jrec *__restrict__ rec, int n, JStore js)
     js.x0[a] = r.x[0];
     js.x0[js.cap + a] = r.x[1];
     js.x0[2 * js.cap + a] = r.x[2];
+    float hx = __double2float_rn(r.x[0]), hy = __double2float_rn(r.x[1]),
+          hz = __double2float_rn(r.x[2]);
+    js.xds[a] = make_float4(hx, hy, hz, __double2float_rn(r.x[0] - (double)hx));
+    js.xds2[a] = make_float2(__double2float_rn(r.x[1] - (double)hy),
+                             __double2float_rn(r.x[2] - (double)hz));
     js.t0[a] = r.tj;
     js.v0m[a] = make_float4((float)r.v[0], (float)r.v[1], (float)r.v[2], (float)r.mass);
     js.a2f[a] = make_float4((float)r.a2[0], (float)r.a2[1], (float)r.a2[2], 0.f);
@@ -200,44 +207,111 @@ __global__ void k_irec_from_store(JStore js, g6x_irec *out, int m)
 
 // ----------------------------------------------------------------- K1 ---
 
-// Eq. 1 and Eq. 2 with the DS position of Sect. 2.2: the Taylor increment
-// dt (v + dt (a/2 + dt j/6)) is formed in FP32, added to the FP64 x0, and the
-// sum is split into hi = rn(x), lo = rn(x - hi).  The velocity is FP32.  The
-// output is the tiled component-major layout (JW words per particle) that the
-// force kernel stages tile by tile.
-// One CTA of JT threads per tile (grid-stride over tiles); the CTA also
-// records the tile's range of particle indices.
-__global__ void __launch_bounds__(JT) k_predict_ds(JStore js, Pred p, int nj,
-                                                   int nj_pad, double t)
+// DS + SP addition of Sect. 2.2: (hi, lo) + d with the FP32 operations of a
+// TwoSum of hi and d, the low part added in, and a final renormalisation
+// (Fast2Sum) -- ten FP32 operations.
+__device__ __forceinline__ void ds_add_f(float hi, float lo, float d, float &rh, float &rl)
+{
+    float s, e;
+    two_sum(hi, d, s, e);
+    e = __fadd_rn(e, lo);
+    rh = __fadd_rn(s, e);
+    rl = __fsub_rn(e, __fsub_rn(rh, s));
+}
+
+// Records one tile's range of particle indices (empty slots excluded);
+// called by all JT threads of the CTA with their own slot's index.
+__device__ __forceinline__ void tile_index_range(int *s_lo, int *s_hi, int id, bool valid,
+                                                 int2 *out)
+{
+    int lo_id = valid ? id : INT_MAX, hi_id = valid ? id : -1;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        lo_id = min(lo_id, __shfl_xor_sync(0xffffffffu, lo_id, off));
+        hi_id = max(hi_id, __shfl_xor_sync(0xffffffffu, hi_id, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_lo[threadIdx.x >> 5] = lo_id;
+        s_hi[threadIdx.x >> 5] = hi_id;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < JT / 32; ++w) {
+            lo_id = min(lo_id, s_lo[w]);
+            hi_id = max(hi_id, s_hi[w]);
+        }
+        *out = make_int2(lo_id, hi_id);
+    }
+    __syncthreads();
+}
+
+// Eq. 1 and Eq. 2 as the paper evaluates them (Sect. 2.2): the Taylor
+// increment dt (v + dt (a/2 + dt j/6)) in FP32, added to the double-single
+// x0 by the DS + SP addition; the velocity in FP32.  Only dt = t - t0 is
+// formed in FP64 (block times are exact there).  One CTA of JT threads per
+// tile; the output is the tiled component-major layout (JW words per
+// particle) that the force kernel stages tile by tile, plus the tile's index
+// range.
+__global__ void __launch_bounds__(JT) k_predict_ds(JStore js, Pred p, int nj, int nj_pad,
+                                                   double t)
 {
     __shared__ int s_lo[JT / 32], s_hi[JT / 32];
     const int ntiles = nj_pad / JT;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int k = tile * JT + threadIdx.x;
         float *o = p.pt + (size_t)tile * (JW * JT) + threadIdx.x;
-        int lo_id = INT_MAX, hi_id = -1;
-        if (k < nj && js.idx[k] >= 0) {
-            lo_id = js.idx[k];
-            hi_id = lo_id;
+        const int id = k < nj ? js.idx[k] : -1;
+        tile_index_range(s_lo, s_hi, id, k < nj && id >= 0, &p.trange[tile]);
+        if (k < nj) {
+            const float h = (float)(t - js.t0[k]);
+            const float4 v = js.v0m[k], a = js.a2f[k], j = js.j6f[k];
+            const float4 xa = js.xds[k];
+            const float2 xb = js.xds2[k];
+            float hx, lx, hy, ly, hz, lz;
+            ds_add_f(xa.x, xa.w, h * fmaf(h, fmaf(h, j.x, a.x), v.x), hx, lx);
+            ds_add_f(xa.y, xb.x, h * fmaf(h, fmaf(h, j.y, a.y), v.y), hy, ly);
+            ds_add_f(xa.z, xb.y, h * fmaf(h, fmaf(h, j.z, a.z), v.z), hz, lz);
+            const float h3 = 3.0f * h;
+            o[W_XH * JT] = hx;
+            o[W_YH * JT] = hy;
+            o[W_ZH * JT] = hz;
+            o[W_M * JT] = v.w;
+            o[W_XL * JT] = lx;
+            o[W_YL * JT] = ly;
+            o[W_ZL * JT] = lz;
+            o[W_VX * JT] = fmaf(h, fmaf(h3, j.x, 2.0f * a.x), v.x);
+            o[W_VY * JT] = fmaf(h, fmaf(h3, j.y, 2.0f * a.y), v.y);
+            o[W_VZ * JT] = fmaf(h, fmaf(h3, j.z, 2.0f * a.z), v.z);
+            o[W_ID * JT] = __int_as_float(id);
+        } else {
+            o[W_XH * JT] = (float)FAR;
+            o[W_YH * JT] = (float)FAR;
+            o[W_ZH * JT] = (float)FAR;
+            o[W_M * JT] = 0.f;
+            o[W_XL * JT] = 0.f;
+            o[W_YL * JT] = 0.f;
+            o[W_ZL * JT] = 0.f;
+            o[W_VX * JT] = 0.f;
+            o[W_VY * JT] = 0.f;
+            o[W_VZ * JT] = 0.f;
+            o[W_ID * JT] = __int_as_float(-1);
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            lo_id = min(lo_id, __shfl_xor_sync(0xffffffffu, lo_id, off));
-            hi_id = max(hi_id, __shfl_xor_sync(0xffffffffu, hi_id, off));
-        }
-        if ((threadIdx.x & 31) == 0) {
-            s_lo[threadIdx.x >> 5] = lo_id;
-            s_hi[threadIdx.x >> 5] = hi_id;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < JT / 32; ++w) {
-                lo_id = min(lo_id, s_lo[w]);
-                hi_id = max(hi_id, s_hi[w]);
-            }
-            p.trange[tile] = make_int2(lo_id, hi_id);
-        }
-        __syncthreads();
+    }
+}
+
+// Eq. 1 and Eq. 2 with the DS position formed through FP64: the Taylor
+// increment in FP32, added to the FP64 x0, and the sum split into
+// hi = rn(x), lo = rn(x - hi).  The velocity is FP32.  Same output layout.
+__global__ void __launch_bounds__(JT) k_predict_ds_x64(JStore js, Pred p, int nj,
+                                                       int nj_pad, double t)
+{
+    __shared__ int s_lo[JT / 32], s_hi[JT / 32];
+    const int ntiles = nj_pad / JT;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int k = tile * JT + threadIdx.x;
+        float *o = p.pt + (size_t)tile * (JW * JT) + threadIdx.x;
+        const int id = k < nj ? js.idx[k] : -1;
+        tile_index_range(s_lo, s_hi, id, k < nj && id >= 0, &p.trange[tile]);
         if (k < nj) {
             double dt = t - js.t0[k];
             float h = (float)dt;
@@ -353,7 +427,6 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     constexpr int PPT = JT / 2 / TJ;                  // j-pairs per thread per tile
     constexpr int FLUSH = (256 + PPT - 1) / PPT;      // tiles between flushes (>= 512 j)
     constexpr unsigned TILE_BYTES = JW * JT * sizeof(float);
-    static_assert(TJ == 1 || NI == 1, "split-j variants carry one i per thread");
     static_assert(!LIST || TJ == 1, "neighbour lists need whole j-tiles per thread");
     static_assert(JT % (2 * TJ) == 0, "j-tile must split into j-pairs evenly");
 
@@ -362,8 +435,8 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     float2 *comp = reinterpret_cast<float2 *>(dyn_smem + NSTAGE * TILE_BYTES);  // [NI][7][NT]
     __shared__ __align__(8) uint64_t bar[NSTAGE];
     __shared__ int s_abort;
-    __shared__ double red[TJ > 1 ? 8 * NT : 1];
-    __shared__ int redj[TJ > 1 ? NT : 1];
+    __shared__ float s_nnr[TJ > 1 ? NI * NT : 1];
+    __shared__ int s_nnj[TJ > 1 ? NI * NT : 1];
 
     const int tid = threadIdx.x;
     const int ti = tid % TI, tj = tid / TI;
@@ -518,40 +591,45 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                     a.nbc[(size_t)seg * ITILE + il] = nbn[k];
             }
         } else {
+            // The TJ j-groups of an i-particle combine in place: every
+            // thread's compensated sums are in comp[], its nearest neighbour
+            // goes to s_nnr / s_nnj, and one thread per i-particle adds the
+            // groups in FP64 (ties of the neighbour to the lower j-slot).
 #pragma unroll
-            for (int q = 0; q < 7; ++q) {
-                float2 hl = cslot(0, q);
-                red[q * NT + tid] = (double)hl.x + (double)hl.y;
+            for (int k = 0; k < NI; ++k) {
+                s_nnr[k * NT + tid] = nnr[k];
+                s_nnj[k * NT + tid] = nn_rescan(k);
             }
-            red[7 * NT + tid] = (double)nnr[0];
-            redj[tid] = nn_rescan(0);
             __syncthreads();
-            if (tid < TI) {
-                double s[7];
+            for (int il = tid; il < ITILE; il += NT) {
+                const int k = il / TI, ii = il % TI;
+                double sum[7];
 #pragma unroll
                 for (int q = 0; q < 7; ++q)
-                    s[q] = 0.0;
-                double br = red[7 * NT + tid];
-                int bj = redj[tid];
+                    sum[q] = 0.0;
+                double br = INF;
+                int bj = -1;
                 for (int g = 0; g < TJ; ++g) {
-                    int o = g * TI + tid;
+                    const int o = g * TI + ii;
 #pragma unroll
-                    for (int q = 0; q < 7; ++q)
-                        s[q] += red[q * NT + o];
-                    double r = red[7 * NT + o];
-                    int jj = redj[o];
-                    if (r < br || (r == br && jj >= 0 && (bj < 0 || jj < bj))) {
+                    for (int q = 0; q < 7; ++q) {
+                        const float2 hl = comp[(k * 7 + q) * NT + o];
+                        sum[q] += (double)hl.x + (double)hl.y;
+                    }
+                    const double r = s_nnr[k * NT + o];
+                    const int jj = s_nnj[k * NT + o];
+                    if (jj >= 0 && (r < br || (r == br && (bj < 0 || jj < bj)))) {
                         br = r;
                         bj = jj;
                     }
                 }
-                Partial *P = a.part + (size_t)seg * ITILE + tid;
+                Partial *P = a.part + (size_t)seg * ITILE + il;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    P->acc[d] = s[d];
-                    P->jerk[d] = s[3 + d];
+                    P->acc[d] = sum[d];
+                    P->jerk[d] = sum[3 + d];
                 }
-                P->pot = s[6];
+                P->pot = sum[6];
                 P->nnr2 = br;
                 P->nnj = bj;
             }
@@ -898,6 +976,84 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a)
         a.nblen_out[i] = (int)min(total, (long long)INT_MAX);
 }
 
+// K3 for blocks whose i-tiles were split over many CTAs (small m): one CTA
+// of 256 threads per i-particle, the partials strided over all its threads,
+// combined by warp shuffles and then across the 8 warps.  No lists.
+__global__ void __launch_bounds__(256) k_reduce_wide(const ReduceArgs a)
+{
+    const long long i = blockIdx.x;
+    if (i >= a.ni)
+        return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int t = (int)(i / a.itile), il = (int)(i % a.itile);
+    const long long p0 = (long long)t * a.J, p1 = p0 + a.J;
+    const long long clo = work_owner(p0, a.W, a.G), chi = work_owner(p1 - 1, a.W, a.G);
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
+    double br = __longlong_as_double(0x7ff0000000000000ll);
+    int bj = -1;
+    for (long long cc = clo + tid; cc <= chi; cc += 256) {
+        long long b = max(work_begin(cc, a.W, a.G), p0);
+        long long e = min(work_begin(cc + 1, a.W, a.G), p1);
+        if (e <= b)
+            continue;
+        const Partial &P = a.part[(size_t)(cc + t) * a.itile + il];
+        for (int d = 0; d < 3; ++d) {
+            s[d] += P.acc[d];
+            s[3 + d] += P.jerk[d];
+        }
+        s[6] += P.pot;
+        if (P.nnj >= 0 && (P.nnr2 < br || (P.nnr2 == br && (bj < 0 || P.nnj < bj)))) {
+            br = P.nnr2;
+            bj = P.nnj;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q)
+            s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+        double r = __shfl_xor_sync(0xffffffffu, br, off);
+        int jj = __shfl_xor_sync(0xffffffffu, bj, off);
+        if (jj >= 0 && (bj < 0 || r < br || (r == br && jj < bj))) {
+            br = r;
+            bj = jj;
+        }
+    }
+    __shared__ double ws[8][8];
+    __shared__ int wj[8];
+    if (lane == 0) {
+        for (int q = 0; q < 7; ++q)
+            ws[warp][q] = s[q];
+        ws[warp][7] = br;
+        wj[warp] = bj;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+        br = __longlong_as_double(0x7ff0000000000000ll);
+        bj = -1;
+        for (int w = 0; w < 8; ++w) {
+            for (int q = 0; q < 7; ++q)
+                acc[q] += ws[w][q];
+            const double r = ws[w][7];
+            const int jj = wj[w];
+            if (jj >= 0 && (bj < 0 || r < br || (r == br && jj < bj))) {
+                br = r;
+                bj = jj;
+            }
+        }
+        g6x_out o;
+        for (int d = 0; d < 3; ++d) {
+            o.acc[d] = acc[d];
+            o.jerk[d] = acc[3 + d];
+        }
+        o.pot = -acc[6];
+        o.nnb = bj >= 0 ? a.jidx[bj] : -1;
+        o.nnr2 = bj >= 0 ? (float)br : __int_as_float(0x7f800000);
+        a.out[i] = o;
+    }
+}
+
 // ------------------------------------------------------------ variants ---
 
 namespace {
@@ -932,6 +1088,11 @@ const Variant kVariants[] = {
     {{128, 1, 2, 0, G6X_PREC_DS}, k_force_ds<128, 1, 2, false, 3, 4>, 128, ds_smem(128, 2)},
     {{128, 1, 3, 0, G6X_PREC_DS}, k_force_ds<128, 1, 3, false, 2, 2>, 128, ds_smem(128, 3)},
     {{96, 1, 2, 0, G6X_PREC_DS}, k_force_ds<96, 1, 2, false, 4, 2>, 96, ds_smem(96, 2)},
+    // split-j shapes with two i-particles per thread, for small blocks
+    {{8, 32, 2, 0, G6X_PREC_DS}, k_force_ds<8, 32, 2, false, 2, 2>, 256, ds_smem(256, 2)},
+    {{16, 16, 2, 0, G6X_PREC_DS}, k_force_ds<16, 16, 2, false, 2, 2>, 256, ds_smem(256, 2)},
+    {{32, 8, 2, 0, G6X_PREC_DS}, k_force_ds<32, 8, 2, false, 2, 2>, 256, ds_smem(256, 2)},
+    {{64, 4, 2, 0, G6X_PREC_DS}, k_force_ds<64, 4, 2, false, 2, 2>, 256, ds_smem(256, 2)},
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
@@ -1129,7 +1290,7 @@ cudaError_t launch_scatter(const g6x_jrec *d_rec, int n, JStore js, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_predict(int prec, JStore js, Pred p, int nj, int nj_pad,
+cudaError_t launch_predict(int kind, JStore js, Pred p, int nj, int nj_pad,
                            double t, int sm_count, cudaStream_t s)
 {
     int blocks = (nj_pad + 255) / 256;
@@ -1138,8 +1299,10 @@ cudaError_t launch_predict(int prec, JStore js, Pred p, int nj, int nj_pad,
         blocks = cap;
     if (blocks < 1)
         blocks = 1;
-    if (prec == G6X_PREC_FP64)
+    if (kind == PRED_FP64)
         k_predict_64<<<blocks, 256, 0, s>>>(js, p, nj, nj_pad, t);
+    else if (kind == PRED_DS_X64)
+        k_predict_ds_x64<<<blocks, JT, 0, s>>>(js, p, nj, nj_pad, t);
     else
         k_predict_ds<<<blocks, JT, 0, s>>>(js, p, nj, nj_pad, t);
     return cudaGetLastError();
@@ -1195,9 +1358,16 @@ cudaError_t launch_reduce(const ForceConfig &cfg, const Partial *part,
     a.ni = ni;
     a.itile = cfg.itile;
     a.list = cfg.list;
-    long long threads = (long long)ni * 32;
-    int blocks = (int)((threads + 255) / 256);
-    k_reduce<<<blocks, 256, 0, s>>>(a);
+    // many partials per i-particle (small blocks spread over many CTAs):
+    // one CTA per i-particle; otherwise one warp per i-particle
+    const long long per_i = (long long)cfg.grid / cfg.n_itile + 1;
+    if (!cfg.list && per_i >= 64) {
+        k_reduce_wide<<<ni, 256, 0, s>>>(a);
+    } else {
+        long long threads = (long long)ni * 32;
+        int blocks = (int)((threads + 255) / 256);
+        k_reduce<<<blocks, 256, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

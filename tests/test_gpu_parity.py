@@ -28,7 +28,7 @@ def ctx():
 
 
 def _tol(prec):
-    return (1e-6, 1e-5) if prec == g6.G6X_PREC_DS else (1e-12, 1e-10)
+    return (1e-12, 1e-10) if prec == g6.G6X_PREC_FP64 else (1e-6, 1e-5)
 
 
 @pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64])
@@ -50,7 +50,7 @@ def test_full_sweep_plummer_1024(ctx, orc, prec):
     assert check_nn(onn, onr, nnb, x, x, idx) > 0.99
 
 
-@pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64])
+@pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64, g6.G6X_PREC_DS_X64])
 def test_predictor_matches_eq1_eq2(ctx, orc, prec):
     # j-particles last updated at varied block times; predicted to t_blk.
     n, t_blk = 3001, 0.375
@@ -62,7 +62,7 @@ def test_predictor_matches_eq1_eq2(ctx, orc, prec):
     h = (t_blk - st["tj"])[:, None]
     inc = np.abs(st["v0"] * h) + np.abs(st["a0"] * h * h / 2) + np.abs(st["j0"] * h ** 3 / 6)
     vinc = np.abs(st["v0"]) + np.abs(st["a0"] * h) + np.abs(st["j0"] * h * h / 2)
-    if prec == g6.G6X_PREC_DS:
+    if prec != g6.G6X_PREC_FP64:
         hi, lo, vel = g6.g6x_get_predicted(ctx, n)
         x_gpu = hi[:, :3].astype(np.float64) + lo[:, :3].astype(np.float64)
         assert np.all(np.abs(x_gpu - xp) <= 8 * 2.0 ** -24 * inc + 2.0 ** -46 * np.abs(xp))
@@ -78,7 +78,7 @@ def test_predictor_matches_eq1_eq2(ctx, orc, prec):
         assert np.array_equal(x64[:, 3], st["m"])
 
 
-@pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64])
+@pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64, g6.G6X_PREC_DS_X64])
 def test_subset_of_predicted_particles_ragged(ctx, orc, prec):
     # n and m not multiples of any tile; i-particles are a seeded subset that
     # sit at their generator positions while the j-particles are predicted.
