@@ -356,6 +356,12 @@ int g6h_energy(g6h_sim *s, double *e_kin, double *e_pot);
 int g6h_stats(const g6h_sim *s, long long *nblocks, long long *nactive,
               long long *hist);
 
+/* Wall-clock seconds g6h_run spent choosing blocks (scheduler, host
+ * prediction), in the force calls (firsthalf + lasthalf) and in correcting
+ * and sending back the corrected particles.  Any pointer may be NULL. */
+int g6h_profile(const g6h_sim *s, double *sec_sched, double *sec_force,
+                double *sec_correct);
+
 void g6h_destroy(g6h_sim *s);
 
 #ifdef __cplusplus

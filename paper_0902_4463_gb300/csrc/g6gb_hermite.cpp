@@ -6,6 +6,7 @@
 // Scheme: Makino & Aarseth (1992) predictor-corrector, as named in Sect. 2;
 // time steps from the Aarseth (1985) criterion cited in Sect. 3.1-3.2,
 // quantised to powers of two (block time steps).
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -24,9 +25,18 @@ struct g6h_sim {
     std::vector<int> act, aidx;
     std::vector<double> xp, vp, a1, j1, pot;
     double t_now = 0;
+    // wall-clock seconds spent in the scheduler, the force calls and the
+    // host correction (including sending corrected particles)
+    double sec_sched = 0, sec_force = 0, sec_correct = 0;
 };
 
 namespace {
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
 
 double norm3(const double *p) { return std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]); }
 
@@ -204,6 +214,7 @@ int g6h_run(g6h_sim *s, double t_end)
         return G6_EINVAL;
     const int n = s->n;
     for (;;) {
+        double w0 = now_s();
         // block scheduler: earliest next time and the particles due then
         double tb = INFINITY;
         for (int k = 0; k < n; ++k)
@@ -228,12 +239,14 @@ int g6h_run(g6h_sim *s, double t_end)
             }
             s->aidx[q] = k;
         }
+        double w1 = now_s();
         int rc = g6_set_ti(s->cid, tb);
         if (!rc)
             rc = force(*s, na, s->xp.data(), s->vp.data(), s->aidx.data(), s->a1.data(),
                        s->j1.data(), s->pot.data());
         if (rc)
             return rc;
+        double w2 = now_s();
         for (int q = 0; q < na; ++q) {
             const int k = s->act[q];
             const double h = tb - s->t[k];
@@ -256,6 +269,10 @@ int g6h_run(g6h_sim *s, double t_end)
             if (rc)
                 return rc;
         }
+        double w3 = now_s();
+        s->sec_sched += w1 - w0;
+        s->sec_force += w2 - w1;
+        s->sec_correct += w3 - w2;
         s->nblocks += 1;
         s->nactive += na;
         int b = 0;
@@ -326,6 +343,19 @@ int g6h_stats(const g6h_sim *s, long long *nblocks, long long *nactive, long lon
         *nactive = s->nactive;
     if (hist)
         std::memcpy(hist, s->hist, sizeof(s->hist));
+    return 0;
+}
+
+int g6h_profile(const g6h_sim *s, double *sec_sched, double *sec_force, double *sec_correct)
+{
+    if (!s)
+        return G6_EINVAL;
+    if (sec_sched)
+        *sec_sched = s->sec_sched;
+    if (sec_force)
+        *sec_force = s->sec_force;
+    if (sec_correct)
+        *sec_correct = s->sec_correct;
     return 0;
 }
 

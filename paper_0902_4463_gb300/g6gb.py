@@ -50,7 +50,7 @@ EXPORTS = [
     "g6x_calc_dev_noalloc", "g6x_sync", "g6x_set_variant",
     "g6x_autotune", "g6x_load_tuning", "g6x_clear_tuning", "g6x_get_predicted", "g6x_last_config",
     "g6x_launch_count", "g6x_set_timing", "g6x_get_timing", "g6h_correct_block", "g6h_create", "g6h_run", "g6h_get_state", "g6h_energy",
-    "g6h_stats", "g6h_destroy",
+    "g6h_stats", "g6h_profile", "g6h_destroy",
 ]
 
 _lib = None
@@ -106,6 +106,7 @@ def lib():
             "g6h_get_state": (I, [P, P, P, P, P, P, P]),
             "g6h_energy": (I, [P, P, P]),
             "g6h_stats": (I, [P, P, P, P]),
+            "g6h_profile": (I, [P, P, P, P]),
             "g6h_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
@@ -412,6 +413,12 @@ class G6HSim:
         hist = np.zeros(64, dtype=np.int64)
         _check(lib().g6h_stats(self.h, C.byref(nb), C.byref(na), _p(hist)), "g6h_stats")
         return dict(nblocks=nb.value, nactive=na.value, hist=hist)
+
+    def profile(self):
+        """Seconds in (scheduler, force calls, correction) during run()."""
+        a, b, c = C.c_double(0), C.c_double(0), C.c_double(0)
+        _check(lib().g6h_profile(self.h, C.byref(a), C.byref(b), C.byref(c)), "g6h_profile")
+        return dict(sched_s=a.value, force_s=b.value, correct_s=c.value)
 
     def close(self):
         if self.h:

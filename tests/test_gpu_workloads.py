@@ -206,3 +206,26 @@ def test_autotuner_table_is_used_and_results_stay_correct(open_ctx, orc, tmp_pat
             check_nn(onn, onr, nnb, x[act], x, idx)
     finally:
         g6.g6x_clear_tuning()
+
+
+def _oracle_drift(name):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_drift.txt")
+    for line in open(path):
+        if line.startswith(name + " "):
+            f = line.split()
+            return float(f[6]), int(f[7]), int(f[8])
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name,t_end", [("plummer_n32768_t0.25", 0.25), ("plummer_n32768_t1", 1.0)])
+def test_hermite_driver_plummer_32768_drift_vs_stored_oracle(name, t_end):
+    # Plummer N = 32768, eps2 = 1e-5, eta = 0.01: the DS path's energy drift is
+    # within 2x the FP64 oracle's drift, written by tests/golden/make_oracle_drift.py
+    from paper_0902_4463_gb300 import hermite_run
+    d_orc, nb_orc, na_orc = _oracle_drift(name)
+    r = hermite_run.run(32768, 2, 1e-5, 0.01, t_end, "ds", cid=4)
+    assert r["synchronised"]
+    assert abs(r["dE_over_E"]) <= 2 * max(abs(d_orc), 1e-12), (r["dE_over_E"], d_orc)
+    # the block structure follows the oracle's closely
+    assert abs(r["nactive"] / na_orc - 1) < 0.02
