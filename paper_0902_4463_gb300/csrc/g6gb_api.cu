@@ -61,6 +61,25 @@ void *host_alloc(size_t bytes)
     return p;
 }
 
+// Pinned host memory that kernels read and write directly (zero-copy): the
+// GRAPE path's staging, i-records, results and error word live here, so a
+// calculation needs no separate host<->device copies.  *dev receives the
+// device-side address.
+void *host_alloc_mapped(size_t bytes, void **dev)
+{
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, bytes ? bytes : 16, cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaHostGetDevicePointer(dev, p, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(p);
+        return nullptr;
+    }
+    return p;
+}
+
 void host_free(void *p)
 {
     if (p)
@@ -93,13 +112,24 @@ struct Ctx {
     std::vector<int> slot_of;
     cudaEvent_t ev_jst = nullptr;
     bool jst_inflight = false;
+    // the staged records sorted by tile for the fused update + predict launch
+    g6x_jrec *h_jsort = nullptr, *d_jsort = nullptr;
+    int jsort_cap = 0;
+    int *h_toff = nullptr, *d_toff = nullptr;
+    int toff_cap = 0;
+    std::vector<int> tcur;
+    cudaEvent_t ev_jsort = nullptr;
+    bool jsort_inflight = false;
     // i-data and results of the GRAPE path
     g6x_irec *h_irec = nullptr, *d_irec = nullptr;
     g6x_out *h_out = nullptr, *d_out = nullptr;
     int io_cap = 0;
-    // partial results
+    // partial results and the per-i-tile counters of the fused reduction
     Partial *d_part = nullptr;
     size_t part_cap = 0;
+    unsigned *d_tcnt = nullptr;
+    size_t tcnt_cap = 0;
+    bool tcnt_dirty = false;          // a launch may have stopped mid-count
     int *d_nbl_part = nullptr, *d_nbc_part = nullptr;
     size_t nbp_cap = 0;
     int *d_nbl = nullptr, *d_nblen = nullptr, *h_nbl = nullptr, *h_nblen = nullptr;
@@ -221,13 +251,15 @@ void free_ctx(Ctx &c)
     if (c.stream)
         cudaStreamSynchronize(c.stream);
     g6::JStore &js = c.js;
-    void *dptrs[] = {js.x0, js.xds, js.xds2, js.t0, js.v0m, js.a2f, js.j6f, js.v64, js.a264, js.j664,
-                     js.idx, c.pred.pt, c.pred.trange, c.pred.p64, c.pred.v64,
-                     c.d_jst, c.d_irec, c.d_out, c.d_part, c.d_nbl_part, c.d_nbc_part,
-                     c.d_nbl, c.d_nblen, c.d_err};
+    // d_jst, d_irec, d_out and d_err are device aliases of mapped host
+    // buffers, freed with them below
+    void *dptrs[] = {js.x0, js.xds, js.xds2, js.t0, js.v0m, js.a2f, js.j6f, js.v64, js.a264,
+                     js.j664, js.idx, c.pred.pt, c.pred.trange, c.pred.p64, c.pred.v64,
+                     c.d_part, c.d_tcnt, c.d_nbl_part, c.d_nbc_part, c.d_nbl, c.d_nblen};
     for (void *p : dptrs)
         dev_free(p);
-    void *hptrs[] = {c.h_jst, c.h_irec, c.h_out, c.h_nbl, c.h_nblen, c.h_err};
+    void *hptrs[] = {c.h_jst, c.h_jsort, c.h_toff, c.h_irec, c.h_out, c.h_nbl, c.h_nblen,
+                     c.h_err};
     for (void *p : hptrs)
         host_free(p);
     for (int p = 0; p < 4; ++p)
@@ -239,6 +271,8 @@ void free_ctx(Ctx &c)
         cudaEventDestroy(e);
     if (c.ev_jst)
         cudaEventDestroy(c.ev_jst);
+    if (c.ev_jsort)
+        cudaEventDestroy(c.ev_jsort);
     if (c.ev_done)
         cudaEventDestroy(c.ev_done);
     if (c.own)
@@ -267,25 +301,20 @@ int ensure_io(Ctx &c, int n)
     if (n <= c.io_cap && c.h_irec)
         return 0;
     int cap = n < 16 ? 16 : n;
-    g6x_irec *hi = (g6x_irec *)host_alloc(sizeof(g6x_irec) * cap);
-    g6x_out *ho = (g6x_out *)host_alloc(sizeof(g6x_out) * cap);
-    g6x_irec *di = (g6x_irec *)dev_alloc(sizeof(g6x_irec) * cap);
-    g6x_out *dout = (g6x_out *)dev_alloc(sizeof(g6x_out) * cap);
-    if (!hi || !ho || !di || !dout) {
+    void *di = nullptr, *dout = nullptr;
+    g6x_irec *hi = (g6x_irec *)host_alloc_mapped(sizeof(g6x_irec) * cap, &di);
+    g6x_out *ho = (g6x_out *)host_alloc_mapped(sizeof(g6x_out) * cap, &dout);
+    if (!hi || !ho) {
         host_free(hi);
         host_free(ho);
-        dev_free(di);
-        dev_free(dout);
         return G6_ENOMEM;
     }
     host_free(c.h_irec);
     host_free(c.h_out);
-    dev_free(c.d_irec);
-    dev_free(c.d_out);
     c.h_irec = hi;
     c.h_out = ho;
-    c.d_irec = di;
-    c.d_out = dout;
+    c.d_irec = (g6x_irec *)di;
+    c.d_out = (g6x_out *)dout;
     c.io_cap = cap;
     return 0;
 }
@@ -299,13 +328,10 @@ int ensure_jstage(Ctx &c, int need)
         cap *= 2;
     if (cap > c.cap)
         cap = c.cap;
-    g6x_jrec *h = (g6x_jrec *)host_alloc(sizeof(g6x_jrec) * cap);
-    g6x_jrec *d = (g6x_jrec *)dev_alloc(sizeof(g6x_jrec) * cap);
-    if (!h || !d) {
-        host_free(h);
-        dev_free(d);
+    void *d = nullptr;
+    g6x_jrec *h = (g6x_jrec *)host_alloc_mapped(sizeof(g6x_jrec) * cap, &d);
+    if (!h)
         return G6_ENOMEM;
-    }
     if (c.jst_inflight) {
         cudaEventSynchronize(c.ev_jst);
         c.jst_inflight = false;
@@ -313,9 +339,8 @@ int ensure_jstage(Ctx &c, int need)
     if (c.n_jst)
         std::memcpy(h, c.h_jst, sizeof(g6x_jrec) * c.n_jst);
     host_free(c.h_jst);
-    dev_free(c.d_jst);
     c.h_jst = h;
-    c.d_jst = d;
+    c.d_jst = (g6x_jrec *)d;
     c.jst_cap = cap;
     return 0;
 }
@@ -325,11 +350,10 @@ int flush_jstage(Ctx &c)
 {
     if (c.n_jst == 0)
         return 0;
-    cudaError_t e = cudaMemcpyAsync(c.d_jst, c.h_jst, sizeof(g6x_jrec) * c.n_jst,
-                                    cudaMemcpyHostToDevice, c.stream);
-    if (e == cudaSuccess) {
+    cudaError_t e;
+    {
         PhaseTimer pt(c, PH_SCATTER);
-        e = g6::launch_scatter(c.d_jst, c.n_jst, c.js, c.stream);
+        e = g6::launch_scatter(c.d_jst, c.n_jst, c.js, c.stream);   // reads the mapped staging
     }
     if (e == cudaSuccess)
         e = cudaEventRecord(c.ev_jst, c.stream);
@@ -369,6 +393,95 @@ int predict_if_stale(Ctx &c, int nj)
         const int other = m == g6::PRED_DS ? g6::PRED_DS_X64 : g6::PRED_DS;
         c.ver_pred[other] = -1;
     }
+    return 0;
+}
+
+// The GRAPE path's j-store update and prediction in one launch: the staged
+// records are counting-sorted by tile on the host into mapped memory, and
+// each predictor CTA stores its tile's records before predicting the tile.
+int update_and_predict(Ctx &c, int nj)
+{
+    if (c.n_jst == 0)
+        return predict_if_stale(c, nj);
+    const int nj_pad = round_up(nj > 0 ? nj : 1, JT);
+    int max_tile = 0;
+    for (int k = 0; k < c.n_jst; ++k) {
+        const int tl = c.h_jst[k].address / JT;
+        if (tl > max_tile)
+            max_tile = tl;
+    }
+    const int ntiles_all = nj_pad / JT > max_tile + 1 ? nj_pad / JT : max_tile + 1;
+    if (c.jsort_inflight) {                 // the previous sorted batch is still read
+        if (cudaEventQuery(c.ev_jsort) != cudaSuccess)
+            cudaEventSynchronize(c.ev_jsort);
+        cudaGetLastError();
+        c.jsort_inflight = false;
+    }
+    if (c.n_jst > c.jsort_cap) {
+        int cap = c.jsort_cap ? c.jsort_cap : 1024;
+        while (cap < c.n_jst)
+            cap *= 2;
+        void *d = nullptr;
+        g6x_jrec *h = (g6x_jrec *)host_alloc_mapped(sizeof(g6x_jrec) * cap, &d);
+        if (!h)
+            return G6_ENOMEM;
+        host_free(c.h_jsort);
+        c.h_jsort = h;
+        c.d_jsort = (g6x_jrec *)d;
+        c.jsort_cap = cap;
+    }
+    if (ntiles_all + 1 > c.toff_cap) {
+        int cap = ntiles_all + 1 + 64;
+        void *d = nullptr;
+        int *h = (int *)host_alloc_mapped(sizeof(int) * cap, &d);
+        if (!h)
+            return G6_ENOMEM;
+        host_free(c.h_toff);
+        c.h_toff = h;
+        c.d_toff = (int *)d;
+        c.toff_cap = cap;
+    }
+    try {
+        c.tcur.assign(ntiles_all + 1, 0);
+    } catch (...) {
+        return G6_ENOMEM;
+    }
+    for (int k = 0; k < c.n_jst; ++k)
+        ++c.tcur[c.h_jst[k].address / JT + 1];
+    for (int tl = 0; tl < ntiles_all; ++tl)
+        c.tcur[tl + 1] += c.tcur[tl];
+    std::memcpy(c.h_toff, c.tcur.data(), sizeof(int) * (ntiles_all + 1));
+    for (int k = 0; k < c.n_jst; ++k)
+        c.h_jsort[c.tcur[c.h_jst[k].address / JT]++] = c.h_jst[k];
+    const int kind = c.pmode == G6X_PREC_FP64 ? g6::PRED_FP64
+                     : c.pmode == G6X_PREC_DS_X64 ? g6::PRED_DS_X64 : g6::PRED_DS;
+    cudaError_t e;
+    {
+        PhaseTimer pt(c, PH_PREDICT);
+        e = g6::launch_update_predict(kind, c.js, c.pred, nj, nj_pad, c.t_set, c.d_jsort, c.d_toff,
+                                      ntiles_all, c.sm_count, c.stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaEventRecord(c.ev_jsort, c.stream);
+    if (e != cudaSuccess)
+        return cuda_err(e);
+    c.launches += 1;
+    c.jsort_inflight = true;
+    for (int k = 0; k < c.n_jst; ++k)
+        c.slot_of[c.h_jst[k].address] = -1;
+    c.n_jst = 0;
+    c.ver += 1;
+    c.t_pred[kind] = c.t_set;
+    c.nj_pred[kind] = nj;
+    c.ver_pred[kind] = c.ver;
+    if (kind != g6::PRED_FP64) {
+        const int other = kind == g6::PRED_DS ? g6::PRED_DS_X64 : g6::PRED_DS;
+        c.ver_pred[other] = -1;
+    }
+    if (kind != g6::PRED_FP64)
+        c.ver_pred[g6::PRED_FP64] = -1;
+    else
+        c.ver_pred[g6::PRED_DS] = c.ver_pred[g6::PRED_DS_X64] = -1;
     return 0;
 }
 
@@ -432,19 +545,47 @@ int run_force(Ctx &c, int nj, int ni, const g6x_irec *d_irec, double eps2, bool 
             return rc;
     }
     cudaError_t e;
-    {
+    const long long seg_per_tile = (long long)cfg.grid / cfg.n_itile + 1;
+    if (!cfg.list && cfg.prec == G6X_PREC_DS && seg_per_tile <= 4) {
+        // one launch: the last CTA of each i-tile reduces it (K3 fused into
+        // K2) when every tile has only a few partials (large blocks); with
+        // many partials per tile that serial tail costs more than the
+        // separate K3, which spreads the sums over many CTAs
+        if ((size_t)cfg.n_itile > c.tcnt_cap) {
+            size_t n = (size_t)cfg.n_itile + cfg.n_itile / 4 + 64;
+            unsigned *q = (unsigned *)dev_alloc(n * sizeof(*q));
+            if (!q)
+                return G6_ENOMEM;
+            dev_free(c.d_tcnt);
+            c.d_tcnt = q;
+            c.tcnt_cap = n;
+            c.tcnt_dirty = true;
+        }
+        if (c.tcnt_dirty) {
+            if (cudaMemsetAsync(c.d_tcnt, 0, c.tcnt_cap * sizeof(unsigned), c.stream)
+                != cudaSuccess)
+                return cuda_err(cudaGetLastError());
+            c.tcnt_dirty = false;
+        }
         PhaseTimer pt(c, PH_FORCE);
-        e = g6::launch_force(cfg, c.pred, d_irec, ni, eps2, c.d_part, c.d_nbl_part,
-                             c.d_nbc_part, c.d_err, c.stream);
-    }
-    if (e == cudaSuccess) {
-        PhaseTimer pt(c, PH_REDUCE);
-        e = g6::launch_reduce(cfg, c.d_part, c.d_nbl_part, c.d_nbc_part, c.js.idx, ni, d_out,
-                              c.d_nbl, c.d_nblen, c.stream);
+        e = g6::launch_force_fused(cfg, c.pred, d_irec, ni, eps2, c.d_part, c.d_err, d_out,
+                                   c.js.idx, c.d_tcnt, c.stream);
+        c.launches += 1;
+    } else {
+        {
+            PhaseTimer pt(c, PH_FORCE);
+            e = g6::launch_force(cfg, c.pred, d_irec, ni, eps2, c.d_part, c.d_nbl_part,
+                                 c.d_nbc_part, c.d_err, c.stream);
+        }
+        if (e == cudaSuccess) {
+            PhaseTimer pt(c, PH_REDUCE);
+            e = g6::launch_reduce(cfg, c.d_part, c.d_nbl_part, c.d_nbc_part, c.js.idx, ni,
+                                  d_out, c.d_nbl, c.d_nblen, c.stream);
+        }
+        c.launches += 2;
     }
     if (e != cudaSuccess)
         return cuda_err(e);
-    c.launches += 2;
     c.last_cfg = cfg;
     c.lists_ready = cfg.list != 0;
     c.lists_host = false;
@@ -505,6 +646,7 @@ int g6x_open_ex(int cid, int nj_max, int ni_max)
     int rc = 0;
     if (cudaStreamCreateWithFlags(&c.own, cudaStreamNonBlocking) != cudaSuccess
         || cudaEventCreateWithFlags(&c.ev_jst, cudaEventDisableTiming) != cudaSuccess
+        || cudaEventCreateWithFlags(&c.ev_jsort, cudaEventDisableTiming) != cudaSuccess
         || cudaEventCreateWithFlags(&c.ev_done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         free_ctx(c);
@@ -523,16 +665,19 @@ int g6x_open_ex(int cid, int nj_max, int ni_max)
     js.v0m = (float4 *)dev_alloc(n * sizeof(float4));
     js.a2f = (float4 *)dev_alloc(n * sizeof(float4));
     js.j6f = (float4 *)dev_alloc(n * sizeof(float4));
-    js.v64 = (double4 *)dev_alloc(n * sizeof(double4));
-    js.a264 = (double4 *)dev_alloc(n * sizeof(double4));
-    js.j664 = (double4 *)dev_alloc(n * sizeof(double4));
+    js.v64 = (double4_32a *)dev_alloc(n * sizeof(double4_32a));
+    js.a264 = (double4_32a *)dev_alloc(n * sizeof(double4_32a));
+    js.j664 = (double4_32a *)dev_alloc(n * sizeof(double4_32a));
     js.idx = (int *)dev_alloc(n * sizeof(int));
     c.pred.pt = (float *)dev_alloc(n * g6::JW * sizeof(float));
     c.pred.trange = (int2 *)dev_alloc((n / JT) * sizeof(int2));
-    c.pred.p64 = (double4 *)dev_alloc(n * sizeof(double4));
-    c.pred.v64 = (double4 *)dev_alloc(n * sizeof(double4));
-    c.d_err = (int *)dev_alloc(sizeof(int));
-    c.h_err = (int *)host_alloc(sizeof(int));
+    c.pred.p64 = (double4_32a *)dev_alloc(n * sizeof(double4_32a));
+    c.pred.v64 = (double4_32a *)dev_alloc(n * sizeof(double4_32a));
+    {
+        void *de = nullptr;
+        c.h_err = (int *)host_alloc_mapped(sizeof(int), &de);
+        c.d_err = (int *)de;
+    }
     if (!js.x0 || !js.xds || !js.xds2 || !js.t0 || !js.v0m || !js.a2f || !js.j6f || !js.v64 || !js.a264
         || !js.j664 || !js.idx || !c.pred.pt || !c.pred.trange || !c.pred.p64
         || !c.pred.v64 || !c.d_err || !c.h_err)
@@ -549,9 +694,8 @@ int g6x_open_ex(int cid, int nj_max, int ni_max)
         }
     }
     if (!rc) {
-        cudaError_t e = cudaMemsetAsync(c.d_err, 0, sizeof(int), c.stream);
-        if (e == cudaSuccess)
-            e = g6::launch_init_store(js, c.stream);
+        *c.h_err = 0;
+        cudaError_t e = g6::launch_init_store(js, c.stream);
         if (e == cudaSuccess)
             e = cudaStreamSynchronize(c.stream);
         rc = cuda_err(e);
@@ -660,8 +804,10 @@ int g6_set_j_particle(int cid, int address, int index, double tj, double dtj,
         return err;
     if (address < 0 || address >= c->cap || index < 0 || !j6 || !a2 || !v || !x)
         return G6_EINVAL;
-    if (c->jst_inflight) {             // staging buffer still being uploaded
-        cudaEventSynchronize(c->ev_jst);
+    if (c->jst_inflight) {             // staging may still be read by the GPU
+        if (cudaEventQuery(c->ev_jst) != cudaSuccess)
+            cudaEventSynchronize(c->ev_jst);
+        cudaGetLastError();
         c->jst_inflight = false;
     }
     int slot = c->slot_of[address];
@@ -730,15 +876,11 @@ void g6calc_firsthalf(int cid, int nj, int ni, const int index[],
             list = true;
     }
     if (!rc)
-        rc = flush_jstage(*c);
-    if (!rc)
-        rc = predict_if_stale(*c, nj);
+        rc = update_and_predict(*c, nj);
     if (!rc && ni > 0) {
-        cudaError_t e = cudaMemcpyAsync(c->d_irec, c->h_irec, sizeof(g6x_irec) * ni,
-                                        cudaMemcpyHostToDevice, c->stream);
-        rc = cuda_err(e);
-        if (!rc)
-            rc = run_force(*c, nj, ni, c->d_irec, eps2, list, c->d_out);
+        // the kernels read the i-records from, and write results to, the
+        // mapped host buffers: no separate copies
+        rc = run_force(*c, nj, ni, c->d_irec, eps2, list, c->d_out);
         if (!rc && h2 && !list) {
             // every radius is <= 0: no list can have entries; skip the list
             // kernel and publish empty lists
@@ -750,19 +892,9 @@ void g6calc_firsthalf(int cid, int nj, int ni, const int index[],
                 c->list_ni = ni;
             }
         }
-        if (!rc) {
-            e = cudaMemcpyAsync(c->h_out, c->d_out, sizeof(g6x_out) * ni,
-                                cudaMemcpyDeviceToHost, c->stream);
-            rc = cuda_err(e);
-        }
     }
-    if (!rc) {
-        cudaError_t e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int),
-                                        cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess)
-            e = cudaEventRecord(c->ev_done, c->stream);
-        rc = cuda_err(e);
-    }
+    if (!rc)
+        rc = cuda_err(cudaEventRecord(c->ev_done, c->stream));
     c->latched = rc;
     c->pending = true;
 }
@@ -784,10 +916,10 @@ static int lasthalf_common(int cid, int nj, int ni, double acc[][3], double jerk
     cudaError_t e = cudaEventSynchronize(c->ev_done);
     if (e != cudaSuccess)
         return cuda_err(e);
-    if (*c->h_err) {
+    if (*(volatile int *)c->h_err) {
         int code = *c->h_err;
-        *c->h_err = 0;
-        cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+        *(volatile int *)c->h_err = 0;
+        c->tcnt_dirty = true;
         return code < 0 ? code : G6_EIO;
     }
     for (int k = 0; k < ni; ++k) {
@@ -935,9 +1067,7 @@ int g6x_calc_dev(int cid, double ti, int nj, int ni, const g6x_irec *d_irec, dou
         || !std::isfinite(ti) || (ni > 0 && (!d_irec || !d_out)))
         return G6_EINVAL;
     c->t_set = ti;
-    int rc = flush_jstage(*c);
-    if (!rc)
-        rc = predict_if_stale(*c, nj);
+    int rc = update_and_predict(*c, nj);
     if (!rc && ni > 0)
         rc = run_force(*c, nj, ni, d_irec, eps2, nl != 0, d_out);
     return rc;
@@ -1211,16 +1341,13 @@ int g6x_sync(int cid)
         return err;
     if (c->pending)
         return G6_EBUSY;
-    cudaError_t e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost,
-                                    c->stream);
-    if (e == cudaSuccess)
-        e = cudaStreamSynchronize(c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess)
         return cuda_err(e);
-    if (*c->h_err) {
+    if (*(volatile int *)c->h_err) {
         int code = *c->h_err;
-        *c->h_err = 0;
-        cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+        *(volatile int *)c->h_err = 0;
+        c->tcnt_dirty = true;
         return code < 0 ? code : G6_EIO;
     }
     return 0;
@@ -1241,7 +1368,7 @@ int g6x_get_predicted(int cid, int nj, float *hi, float *lo, float *vel, double 
     if (rc)
         return rc;
     cudaError_t e = cudaSuccess;
-    size_t d4 = sizeof(double4) * (size_t)nj;
+    size_t d4 = sizeof(double4_32a) * (size_t)nj;
     if (c->prec == G6X_PREC_DS) {
         // copy the tiled layout back and unpack it into (x, y, z, w) rows
         const int ntile = (nj + JT - 1) / JT;

@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -28,6 +29,9 @@ struct g6h_sim {
     // wall-clock seconds spent in the scheduler, the force calls and the
     // host correction (including sending corrected particles)
     double sec_sched = 0, sec_force = 0, sec_correct = 0;
+    // block scheduler: particles keyed by their next time t + dt (block
+    // times are dyadic, so equal times compare exactly)
+    std::map<double, std::vector<int>> due;
 };
 
 namespace {
@@ -70,22 +74,33 @@ int force(g6h_sim &s, int ni, const double *xi, const double *vi, const int *ii,
 void correct(double h, const double *a0, const double *j0, const double *a1,
              const double *j1, double *xp, double *vp, double *d2, double *d3)
 {
-    const double h2 = h * h, h3 = h2 * h;
+    const double ih = 1.0 / h, ih2 = ih * ih, ih3 = ih2 * ih;
+    const double h2 = h * h, h3 = h2 * h, h4 = h2 * h2;
     for (int d = 0; d < 3; ++d) {
         const double da = a0[d] - a1[d];
-        d2[d] = (-6.0 * da - h * (4.0 * j0[d] + 2.0 * j1[d])) / h2;
-        d3[d] = (12.0 * da + 6.0 * h * (j0[d] + j1[d])) / h3;
-        xp[d] += h2 * h2 * (d2[d] / 24.0 + h * d3[d] / 120.0);
-        vp[d] += h3 * (d2[d] / 6.0 + h * d3[d] / 24.0);
+        d2[d] = (-6.0 * da - h * (4.0 * j0[d] + 2.0 * j1[d])) * ih2;
+        d3[d] = (12.0 * da + 6.0 * h * (j0[d] + j1[d])) * ih3;
+        xp[d] += h4 * (d2[d] * (1.0 / 24.0) + h * d3[d] * (1.0 / 120.0));
+        vp[d] += h3 * (d2[d] * (1.0 / 6.0) + h * d3[d] * (1.0 / 24.0));
     }
 }
 
-// Aarseth (1985): sqrt(eta (|a||a''| + |j|^2) / (|j||a'''| + |a''|^2)).
+double dot3(const double *p, const double *q) { return p[0] * q[0] + p[1] * q[1] + p[2] * q[2]; }
+
+// Aarseth (1985): sqrt(eta (|a||a''| + |j|^2) / (|j||a'''| + |a''|^2)),
+// with |a||a''| = sqrt(|a|^2 |a''|^2) to save square roots.
 double aarseth(const double *a, const double *j, const double *d2, const double *d3,
                double eta)
 {
-    const double na = norm3(a), nj = norm3(j), n2 = norm3(d2), n3 = norm3(d3);
-    return std::sqrt(eta * (na * n2 + nj * nj) / (nj * n3 + n2 * n2));
+    const double a_2 = dot3(a, a), j_2 = dot3(j, j), d2_2 = dot3(d2, d2), d3_2 = dot3(d3, d3);
+    return std::sqrt(eta * (std::sqrt(a_2 * d2_2) + j_2) / (std::sqrt(j_2 * d3_2) + d2_2));
+}
+
+// Is t an integer multiple of the power of two p?  t * (1/p) is exact.
+bool multiple_of(double t, double p)
+{
+    const double q = t * (1.0 / p);
+    return q == std::floor(q);
 }
 
 // Power-of-two step: halve until it fits the request; double at most once
@@ -95,7 +110,7 @@ double quantise(double dt, double req, double t, double dt_max)
     if (req < dt) {
         while (dt > req)
             dt *= 0.5;
-    } else if (req >= 2.0 * dt && 2.0 * dt <= dt_max && std::fmod(t, 2.0 * dt) == 0.0) {
+    } else if (req >= 2.0 * dt && 2.0 * dt <= dt_max && multiple_of(t, 2.0 * dt)) {
         dt *= 2.0;
     }
     return dt;
@@ -199,6 +214,14 @@ g6h_sim *g6h_create(int cid, int n, const double *m, const double *x, const doub
     }
     for (int k = 0; !rc && k < n; ++k)
         rc = send_j(*s, k);
+    if (!rc) {
+        try {
+            for (int k = 0; k < n; ++k)
+                s->due[s->t[k] + s->dt[k]].push_back(k);
+        } catch (...) {
+            rc = G6_ENOMEM;
+        }
+    }
     if (rc) {
         delete s;
         if (err)
@@ -212,21 +235,20 @@ int g6h_run(g6h_sim *s, double t_end)
 {
     if (!s || !(t_end >= 0) || std::fmod(t_end, s->dt_max) != 0.0)
         return G6_EINVAL;
-    const int n = s->n;
     for (;;) {
         double w0 = now_s();
-        // block scheduler: earliest next time and the particles due then
-        double tb = INFINITY;
-        for (int k = 0; k < n; ++k)
-            if (s->t[k] + s->dt[k] < tb)
-                tb = s->t[k] + s->dt[k];
+        // block scheduler: the earliest next time and the particles due then
+        if (s->due.empty())
+            break;
+        auto first = s->due.begin();
+        const double tb = first->first;
         if (tb > t_end)
             break;
-        s->act.clear();
-        for (int k = 0; k < n; ++k)
-            if (s->t[k] + s->dt[k] == tb)
-                s->act.push_back(k);
+        s->act.swap(first->second);
+        s->due.erase(first);
         const int na = (int)s->act.size();
+        std::vector<int> *last_bucket = nullptr;
+        double last_time = 0.0;
         // host prediction of the active i-particles (Eq. 1, Eq. 2)
         for (int q = 0; q < na; ++q) {
             const int k = s->act[q];
@@ -268,7 +290,15 @@ int g6h_run(g6h_sim *s, double t_end)
             rc = send_j(*s, k);
             if (rc)
                 return rc;
+            // most of a block moves to one or two new times: reuse the bucket
+            const double tn = tb + nd;
+            if (!last_bucket || tn != last_time) {
+                last_bucket = &s->due[tn];
+                last_time = tn;
+            }
+            last_bucket->push_back(k);
         }
+        s->act.clear();
         double w3 = now_s();
         s->sec_sched += w1 - w0;
         s->sec_force += w2 - w1;

@@ -17,14 +17,28 @@ namespace g6 {
 constexpr int JT = 256;
 
 // One partial result of a (work segment, i-particle) pair: sums over the
-// j-range the segment covers, in FP64 (Sect. 2.3: partial forces of the P
-// blocks are reduced on the GPU before the copy back).  72 bytes.
-struct Partial {
-    double acc[3], jerk[3], pot;  // pot accumulates +m/r; negated in K3
-    double nnr2;                  // smallest unsoftened |r|^2 seen
+// j-range the segment covers (Sect. 2.3: partial forces of the P blocks are
+// reduced on the GPU before the copy back).
+//
+// DS path: each sum as a compensated FP32 pair (hi, lo), about 48 bits; the
+// reductions stay in compensated FP32 and convert to FP64 once per result,
+// because GB300's FP64 pipe is about 1/64 of its FP32 rate.  64 bytes.
+struct PartialDS {
+    float2 acc[3], jerk[3], pot;  // pot accumulates +m/r; negated at the end
+    float nnr2;                   // smallest unsoftened |r|^2 seen
     int nnj;                      // its j-slot, -1 if none
+};
+// All-FP64 path: plain FP64 sums.  72 bytes.
+struct Partial64 {
+    double acc[3], jerk[3], pot;
+    double nnr2;
+    int nnj;
     int pad;
 };
+// Bytes of one partial slot whichever path writes it.
+constexpr size_t PARTIAL_BYTES = sizeof(Partial64) > sizeof(PartialDS) ? sizeof(Partial64)
+                                                                         : sizeof(PartialDS);
+using Partial = Partial64;   // slot-sized unit of partial buffers
 
 // j-memory (the j-store), structure of arrays, capacity `cap` (multiple of JT).
 struct JStore {
@@ -35,9 +49,9 @@ struct JStore {
     float4 *v0m;       // (vx, vy, vz, m)              FP32 copy
     float4 *a2f;       // (ax/2, ay/2, az/2, 0)         FP32 copy
     float4 *j6f;       // (jx/6, jy/6, jz/6, 0)         FP32 copy
-    double4 *v64;      // (vx, vy, vz, m)              FP64 copy
-    double4 *a264;     // (ax/2, ay/2, az/2, 0)
-    double4 *j664;     // (jx/6, jy/6, jz/6, 0)
+    double4_32a *v64;      // (vx, vy, vz, m)              FP64 copy
+    double4_32a *a264;     // (ax/2, ay/2, az/2, 0)
+    double4_32a *j664;     // (jx/6, jy/6, jz/6, 0)
     int *idx;          // particle index (-1: empty slot)
     int cap;
 };
@@ -57,8 +71,8 @@ struct Pred {
                        //     (empty tile: INT_MAX, -1); lets the force kernel
                        //     skip the per-pair self test on tiles that hold
                        //     none of its i-particles
-    double4 *p64;      // FP64: (x, y, z, m)
-    double4 *v64;      // FP64: (vx, vy, vz, index)
+    double4_32a *p64;      // FP64: (x, y, z, m)
+    double4_32a *v64;      // FP64: (vx, vy, vz, index)
 };
 
 // A force launch: kernel variant, CTA shape and the work partition.  The
@@ -112,11 +126,24 @@ cudaError_t launch_init_store(JStore js, cudaStream_t s);
 enum PredKind { PRED_DS = 0, PRED_FP64 = 1, PRED_DS_X64 = 2 };
 cudaError_t launch_predict(int kind, JStore js, Pred p, int nj, int nj_pad,
                            double t, int sm_count, cudaStream_t s);
+// The j-store update fused into the prediction launch: rec holds staged
+// records sorted by tile, tile t's at [toff[t], toff[t+1]), for tiles
+// 0 .. ntiles_all-1 (which may reach beyond nj_pad / JT).
+cudaError_t launch_update_predict(int kind, JStore js, Pred p, int nj, int nj_pad, double t,
+                                  const g6x_jrec *rec, const int *toff, int ntiles_all,
+                                  int sm_count, cudaStream_t s);
 cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
                          const g6x_irec *d_irec, int ni, double eps2,
-                         Partial *part, int *nbl_part, int *nbc_part,
+                         void *part, int *nbl_part, int *nbc_part,
                          int *d_err, cudaStream_t s);
-cudaError_t launch_reduce(const ForceConfig &cfg, const Partial *part,
+// DS force with the reduction fused in (no neighbour lists): the last CTA
+// to finish an i-tile writes its results to out.  tcnt holds one counter per
+// i-tile, zero before the launch and left zero by a launch that completes.
+cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
+                               const g6x_irec *d_irec, int ni, double eps2, void *part,
+                               int *d_err, g6x_out *out, const int *jidx, unsigned *tcnt,
+                               cudaStream_t s);
+cudaError_t launch_reduce(const ForceConfig &cfg, const void *part,
                           const int *nbl_part, const int *nbc_part,
                           const int *jidx, int ni, g6x_out *d_out,
                           int *d_nbl, int *d_nblen, cudaStream_t s);

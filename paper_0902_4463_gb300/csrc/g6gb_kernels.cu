@@ -6,7 +6,8 @@
 //   K2 k_force_ds     FP32 pair forces with double-single separations,
 //                     Eq. 3, nearest neighbour, neighbour lists (Sect. 2.3, 2.5, 4)
 //   K2d k_force_64    the same in FP64
-//   K3 k_reduce       FP64 reduction of the partial forces     (Sect. 2.3)
+//   K3 k_reduce       reduction of the partial forces          (Sect. 2.3)
+//                     (compensated FP32 for the DS path, FP64 for the FP64 path)
 //
 // Work partition of K2/K2d.  The paper spreads the j-particles over the
 // multiprocessors, gives every block all i-particles, cuts i into serial
@@ -115,6 +116,17 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// (ah, al) += (bh, bl) in compensated FP32: TwoSum of the high parts, the
+// low parts added to the error, renormalised (Fast2Sum).
+__device__ __forceinline__ void ds_acc(float &ah, float &al, float bh, float bl)
+{
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    ah = __fadd_rn(s, e);
+    al = __fsub_rn(e, __fsub_rn(ah, s));
+}
+
 // Work line helpers: CTA c owns [begin(c), begin(c+1)).
 __device__ __forceinline__ long long work_begin(long long c, long long W, long long G)
 {
@@ -148,30 +160,25 @@ __global__ void k_init_store(JStore js)
         js.v0m[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         js.a2f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         js.j6f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        js.v64[k] = make_double4(0.0, 0.0, 0.0, 0.0);
-        js.a264[k] = make_double4(0.0, 0.0, 0.0, 0.0);
-        js.j664[k] = make_double4(0.0, 0.0, 0.0, 0.0);
+        js.v64[k] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        js.a264[k] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        js.j664[k] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
         js.idx[k] = -1;
     }
 }
 
-// j-memory update (Sect. 2.1: only the corrected particles travel to the
-// GPU each step).  One thread per record; addresses within one launch are
-// distinct (the host staging keeps one record per address).
-__global__ void k_scatter(const g6x_jrec *__restrict__ rec, int n, JStore js)
+// Store one j-particle record in its j-memory slot (the j-store update of
+// Sect. 2.1: only corrected particles travel to the GPU each step).
+__device__ __forceinline__ void store_record(const g6x_jrec &r, const JStore &js)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n)
-        return;
-    const g6x_jrec &r = rec[k];
-    int a = r.address;
+    const int a = r.address;
     if (a < 0 || a >= js.cap)
         return;
     js.x0[a] = r.x[0];
     js.x0[js.cap + a] = r.x[1];
     js.x0[2 * js.cap + a] = r.x[2];
-    float hx = __double2float_rn(r.x[0]), hy = __double2float_rn(r.x[1]),
-          hz = __double2float_rn(r.x[2]);
+    const float hx = __double2float_rn(r.x[0]), hy = __double2float_rn(r.x[1]),
+                hz = __double2float_rn(r.x[2]);
     js.xds[a] = make_float4(hx, hy, hz, __double2float_rn(r.x[0] - (double)hx));
     js.xds2[a] = make_float2(__double2float_rn(r.x[1] - (double)hy),
                              __double2float_rn(r.x[2] - (double)hz));
@@ -179,10 +186,19 @@ __global__ void k_scatter(const g6x_jrec *__restrict__ rec, int n, JStore js)
     js.v0m[a] = make_float4((float)r.v[0], (float)r.v[1], (float)r.v[2], (float)r.mass);
     js.a2f[a] = make_float4((float)r.a2[0], (float)r.a2[1], (float)r.a2[2], 0.f);
     js.j6f[a] = make_float4((float)r.j6[0], (float)r.j6[1], (float)r.j6[2], 0.f);
-    js.v64[a] = make_double4(r.v[0], r.v[1], r.v[2], r.mass);
-    js.a264[a] = make_double4(r.a2[0], r.a2[1], r.a2[2], 0.0);
-    js.j664[a] = make_double4(r.j6[0], r.j6[1], r.j6[2], 0.0);
+    js.v64[a] = make_double4_32a(r.v[0], r.v[1], r.v[2], r.mass);
+    js.a264[a] = make_double4_32a(r.a2[0], r.a2[1], r.a2[2], 0.0);
+    js.j664[a] = make_double4_32a(r.j6[0], r.j6[1], r.j6[2], 0.0);
     js.idx[a] = r.index;
+}
+
+// K0: one thread per record; addresses within one launch are distinct (the
+// host staging keeps one record per address).
+__global__ void k_scatter(const g6x_jrec *__restrict__ rec, int n, JStore js)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n)
+        store_record(rec[k], js);
 }
 
 // Tuning input: i-records built from the first m j-slots of j-memory.
@@ -195,7 +211,7 @@ __global__ void k_irec_from_store(JStore js, g6x_irec *out, int m)
     r.x[0] = js.x0[k];
     r.x[1] = js.x0[js.cap + k];
     r.x[2] = js.x0[2 * js.cap + k];
-    double4 v = js.v64[k];
+    double4_32a v = js.v64[k];
     r.v[0] = v.x;
     r.v[1] = v.y;
     r.v[2] = v.z;
@@ -245,134 +261,133 @@ __device__ __forceinline__ void tile_index_range(int *s_lo, int *s_hi, int id, b
     __syncthreads();
 }
 
-// Eq. 1 and Eq. 2 as the paper evaluates them (Sect. 2.2): the Taylor
-// increment dt (v + dt (a/2 + dt j/6)) in FP32, added to the double-single
-// x0 by the DS + SP addition; the velocity in FP32.  Only dt = t - t0 is
-// formed in FP64 (block times are exact there).  One CTA of JT threads per
-// tile; the output is the tiled component-major layout (JW words per
-// particle) that the force kernel stages tile by tile, plus the tile's index
-// range.
-__global__ void __launch_bounds__(JT) k_predict_ds(JStore js, Pred p, int nj, int nj_pad,
-                                                   double t)
+// Eq. 1 and Eq. 2 for one j-slot k < nj, written as the tiled DS layout:
+// the paper's form (Sect. 2.2) -- Taylor increment dt (v + dt (a/2 + dt j/6))
+// in FP32, added to the double-single x0 by the DS + SP addition, velocity in
+// FP32; only dt = t - t0 is formed in FP64 (block times are exact there).
+__device__ __forceinline__ void predict_slot_ds(const JStore &js, int k, double t, float *o,
+                                                int id)
 {
-    __shared__ int s_lo[JT / 32], s_hi[JT / 32];
-    const int ntiles = nj_pad / JT;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int k = tile * JT + threadIdx.x;
-        float *o = p.pt + (size_t)tile * (JW * JT) + threadIdx.x;
-        const int id = k < nj ? js.idx[k] : -1;
-        tile_index_range(s_lo, s_hi, id, k < nj && id >= 0, &p.trange[tile]);
-        if (k < nj) {
-            const float h = (float)(t - js.t0[k]);
-            const float4 v = js.v0m[k], a = js.a2f[k], j = js.j6f[k];
-            const float4 xa = js.xds[k];
-            const float2 xb = js.xds2[k];
-            float hx, lx, hy, ly, hz, lz;
-            ds_add_f(xa.x, xa.w, h * fmaf(h, fmaf(h, j.x, a.x), v.x), hx, lx);
-            ds_add_f(xa.y, xb.x, h * fmaf(h, fmaf(h, j.y, a.y), v.y), hy, ly);
-            ds_add_f(xa.z, xb.y, h * fmaf(h, fmaf(h, j.z, a.z), v.z), hz, lz);
-            const float h3 = 3.0f * h;
-            o[W_XH * JT] = hx;
-            o[W_YH * JT] = hy;
-            o[W_ZH * JT] = hz;
-            o[W_M * JT] = v.w;
-            o[W_XL * JT] = lx;
-            o[W_YL * JT] = ly;
-            o[W_ZL * JT] = lz;
-            o[W_VX * JT] = fmaf(h, fmaf(h3, j.x, 2.0f * a.x), v.x);
-            o[W_VY * JT] = fmaf(h, fmaf(h3, j.y, 2.0f * a.y), v.y);
-            o[W_VZ * JT] = fmaf(h, fmaf(h3, j.z, 2.0f * a.z), v.z);
-            o[W_ID * JT] = __int_as_float(id);
-        } else {
-            o[W_XH * JT] = (float)FAR;
-            o[W_YH * JT] = (float)FAR;
-            o[W_ZH * JT] = (float)FAR;
-            o[W_M * JT] = 0.f;
-            o[W_XL * JT] = 0.f;
-            o[W_YL * JT] = 0.f;
-            o[W_ZL * JT] = 0.f;
-            o[W_VX * JT] = 0.f;
-            o[W_VY * JT] = 0.f;
-            o[W_VZ * JT] = 0.f;
-            o[W_ID * JT] = __int_as_float(-1);
-        }
+    const float h = (float)(t - js.t0[k]);
+    const float4 v = js.v0m[k], a = js.a2f[k], j = js.j6f[k];
+    const float4 xa = js.xds[k];
+    const float2 xb = js.xds2[k];
+    float hx, lx, hy, ly, hz, lz;
+    ds_add_f(xa.x, xa.w, h * fmaf(h, fmaf(h, j.x, a.x), v.x), hx, lx);
+    ds_add_f(xa.y, xb.x, h * fmaf(h, fmaf(h, j.y, a.y), v.y), hy, ly);
+    ds_add_f(xa.z, xb.y, h * fmaf(h, fmaf(h, j.z, a.z), v.z), hz, lz);
+    const float h3 = 3.0f * h;
+    o[W_XH * JT] = hx;
+    o[W_YH * JT] = hy;
+    o[W_ZH * JT] = hz;
+    o[W_M * JT] = v.w;
+    o[W_XL * JT] = lx;
+    o[W_YL * JT] = ly;
+    o[W_ZL * JT] = lz;
+    o[W_VX * JT] = fmaf(h, fmaf(h3, j.x, 2.0f * a.x), v.x);
+    o[W_VY * JT] = fmaf(h, fmaf(h3, j.y, 2.0f * a.y), v.y);
+    o[W_VZ * JT] = fmaf(h, fmaf(h3, j.z, 2.0f * a.z), v.z);
+    o[W_ID * JT] = __int_as_float(id);
+}
+
+// The same with the DS position formed through FP64: the FP32 increment is
+// added to the FP64 x0 and the sum split into hi = rn(x), lo = rn(x - hi).
+__device__ __forceinline__ void predict_slot_ds_x64(const JStore &js, int k, double t, float *o,
+                                                    int id)
+{
+    const double dt = t - js.t0[k];
+    const float h = (float)dt;
+    const float4 v = js.v0m[k], a = js.a2f[k], j = js.j6f[k];
+    const double px = js.x0[k] + (double)(h * fmaf(h, fmaf(h, j.x, a.x), v.x));
+    const double py = js.x0[js.cap + k] + (double)(h * fmaf(h, fmaf(h, j.y, a.y), v.y));
+    const double pz = js.x0[2 * js.cap + k] + (double)(h * fmaf(h, fmaf(h, j.z, a.z), v.z));
+    const float hx = __double2float_rn(px), hy = __double2float_rn(py),
+                hz = __double2float_rn(pz);
+    const float h3 = 3.0f * h;
+    o[W_XH * JT] = hx;
+    o[W_YH * JT] = hy;
+    o[W_ZH * JT] = hz;
+    o[W_M * JT] = v.w;
+    o[W_XL * JT] = __double2float_rn(px - (double)hx);
+    o[W_YL * JT] = __double2float_rn(py - (double)hy);
+    o[W_ZL * JT] = __double2float_rn(pz - (double)hz);
+    o[W_VX * JT] = fmaf(h, fmaf(h3, j.x, 2.0f * a.x), v.x);
+    o[W_VY * JT] = fmaf(h, fmaf(h3, j.y, 2.0f * a.y), v.y);
+    o[W_VZ * JT] = fmaf(h, fmaf(h3, j.z, 2.0f * a.z), v.z);
+    o[W_ID * JT] = __int_as_float(id);
+}
+
+__device__ __forceinline__ void far_slot_ds(float *o)
+{
+    o[W_XH * JT] = (float)FAR;
+    o[W_YH * JT] = (float)FAR;
+    o[W_ZH * JT] = (float)FAR;
+    o[W_M * JT] = 0.f;
+    o[W_XL * JT] = 0.f;
+    o[W_YL * JT] = 0.f;
+    o[W_ZL * JT] = 0.f;
+    o[W_VX * JT] = 0.f;
+    o[W_VY * JT] = 0.f;
+    o[W_VZ * JT] = 0.f;
+    o[W_ID * JT] = __int_as_float(-1);
+}
+
+// Eq. 1 and Eq. 2 entirely in FP64, for the FP64 force kernel.
+__device__ __forceinline__ void predict_slot_64(const JStore &js, Pred &p, int k, int nj, double t)
+{
+    if (k < nj) {
+        const double h = t - js.t0[k];
+        const double4_32a v = js.v64[k], a = js.a264[k], j = js.j664[k];
+        const double px = js.x0[k] + h * fma(h, fma(h, j.x, a.x), v.x);
+        const double py = js.x0[js.cap + k] + h * fma(h, fma(h, j.y, a.y), v.y);
+        const double pz = js.x0[2 * js.cap + k] + h * fma(h, fma(h, j.z, a.z), v.z);
+        const double h3 = 3.0 * h;
+        const double vx = fma(h, fma(h3, j.x, 2.0 * a.x), v.x);
+        const double vy = fma(h, fma(h3, j.y, 2.0 * a.y), v.y);
+        const double vz = fma(h, fma(h3, j.z, 2.0 * a.z), v.z);
+        p.p64[k] = make_double4_32a(px, py, pz, v.w);
+        p.v64[k] = make_double4_32a(vx, vy, vz, (double)js.idx[k]);
+    } else {
+        p.p64[k] = make_double4_32a(FAR, FAR, FAR, 0.0);
+        p.v64[k] = make_double4_32a(0.0, 0.0, 0.0, -1.0);
     }
 }
 
-// Eq. 1 and Eq. 2 with the DS position formed through FP64: the Taylor
-// increment in FP32, added to the FP64 x0, and the sum split into
-// hi = rn(x), lo = rn(x - hi).  The velocity is FP32.  Same output layout.
-__global__ void __launch_bounds__(JT) k_predict_ds_x64(JStore js, Pred p, int nj,
-                                                       int nj_pad, double t)
+// K1: one CTA of JT threads per tile of j-slots (grid-stride over tiles).
+// With UPD, the CTA first stores the staged j-records that fall in its tile
+// (rec sorted by tile, tile t's records at [toff[t], toff[t+1])) -- the K0
+// update fused into the same launch -- then predicts the tile.  Tiles at or
+// beyond the predicted range only take their updates.  The DS kinds also
+// record each tile's range of particle indices.
+template <int KIND, bool UPD>
+__global__ void __launch_bounds__(JT) k_predict(JStore js, Pred p, int nj, int nj_pad,
+                                                double t, const g6x_jrec *__restrict__ rec,
+                                                const int *__restrict__ toff, int ntiles_all)
 {
     __shared__ int s_lo[JT / 32], s_hi[JT / 32];
-    const int ntiles = nj_pad / JT;
+    const int ntiles_pred = nj_pad / JT;
+    const int ntiles = UPD ? ntiles_all : ntiles_pred;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int k = tile * JT + threadIdx.x;
-        float *o = p.pt + (size_t)tile * (JW * JT) + threadIdx.x;
-        const int id = k < nj ? js.idx[k] : -1;
-        tile_index_range(s_lo, s_hi, id, k < nj && id >= 0, &p.trange[tile]);
-        if (k < nj) {
-            double dt = t - js.t0[k];
-            float h = (float)dt;
-            float4 v = js.v0m[k], a = js.a2f[k], j = js.j6f[k];
-            float dx = h * fmaf(h, fmaf(h, j.x, a.x), v.x);
-            float dy = h * fmaf(h, fmaf(h, j.y, a.y), v.y);
-            float dz = h * fmaf(h, fmaf(h, j.z, a.z), v.z);
-            double px = js.x0[k] + (double)dx;
-            double py = js.x0[js.cap + k] + (double)dy;
-            double pz = js.x0[2 * js.cap + k] + (double)dz;
-            float hx = __double2float_rn(px), hy = __double2float_rn(py),
-                  hz = __double2float_rn(pz);
-            float h3 = 3.0f * h;
-            o[W_XH * JT] = hx;
-            o[W_YH * JT] = hy;
-            o[W_ZH * JT] = hz;
-            o[W_M * JT] = v.w;
-            o[W_XL * JT] = __double2float_rn(px - (double)hx);
-            o[W_YL * JT] = __double2float_rn(py - (double)hy);
-            o[W_ZL * JT] = __double2float_rn(pz - (double)hz);
-            o[W_VX * JT] = fmaf(h, fmaf(h3, j.x, 2.0f * a.x), v.x);
-            o[W_VY * JT] = fmaf(h, fmaf(h3, j.y, 2.0f * a.y), v.y);
-            o[W_VZ * JT] = fmaf(h, fmaf(h3, j.z, 2.0f * a.z), v.z);
-            o[W_ID * JT] = __int_as_float(js.idx[k]);
-        } else {
-            o[W_XH * JT] = (float)FAR;
-            o[W_YH * JT] = (float)FAR;
-            o[W_ZH * JT] = (float)FAR;
-            o[W_M * JT] = 0.f;
-            o[W_XL * JT] = 0.f;
-            o[W_YL * JT] = 0.f;
-            o[W_ZL * JT] = 0.f;
-            o[W_VX * JT] = 0.f;
-            o[W_VY * JT] = 0.f;
-            o[W_VZ * JT] = 0.f;
-            o[W_ID * JT] = __int_as_float(-1);
+        if constexpr (UPD) {
+            for (int r = toff[tile] + threadIdx.x; r < toff[tile + 1]; r += JT)
+                store_record(rec[r], js);
+            __syncthreads();
         }
-    }
-}
-
-// Eq. 1 and Eq. 2 entirely in FP64.
-__global__ void __launch_bounds__(256) k_predict_64(JStore js, Pred p, int nj,
-                                                    int nj_pad, double t)
-{
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nj_pad;
-         k += gridDim.x * blockDim.x) {
-        if (k < nj) {
-            double h = t - js.t0[k];
-            double4 v = js.v64[k], a = js.a264[k], j = js.j664[k];
-            double px = js.x0[k] + h * fma(h, fma(h, j.x, a.x), v.x);
-            double py = js.x0[js.cap + k] + h * fma(h, fma(h, j.y, a.y), v.y);
-            double pz = js.x0[2 * js.cap + k] + h * fma(h, fma(h, j.z, a.z), v.z);
-            double h3 = 3.0 * h;
-            double vx = fma(h, fma(h3, j.x, 2.0 * a.x), v.x);
-            double vy = fma(h, fma(h3, j.y, 2.0 * a.y), v.y);
-            double vz = fma(h, fma(h3, j.z, 2.0 * a.z), v.z);
-            p.p64[k] = make_double4(px, py, pz, v.w);
-            p.v64[k] = make_double4(vx, vy, vz, (double)js.idx[k]);
+        if (tile >= ntiles_pred)
+            continue;
+        const int k = tile * JT + threadIdx.x;
+        if constexpr (KIND == PRED_FP64) {
+            predict_slot_64(js, p, k, nj, t);
         } else {
-            p.p64[k] = make_double4(FAR, FAR, FAR, 0.0);
-            p.v64[k] = make_double4(0.0, 0.0, 0.0, -1.0);
+            float *o = p.pt + (size_t)tile * (JW * JT) + threadIdx.x;
+            const int id = k < nj ? js.idx[k] : -1;
+            tile_index_range(s_lo, s_hi, id, k < nj && id >= 0, &p.trange[tile]);
+            if (k >= nj)
+                far_slot_ds(o);
+            else if constexpr (KIND == PRED_DS)
+                predict_slot_ds(js, k, t, o, id);
+            else
+                predict_slot_ds_x64(js, k, t, o, id);
         }
     }
 }
@@ -382,9 +397,9 @@ __global__ void __launch_bounds__(256) k_predict_64(JStore js, Pred p, int nj,
 struct ForceArgs {
     const float *pt;                  // DS predicted j, tiled layout
     const int2 *trange;               // DS per-tile index range
-    const double4 *p64, *v64;         // FP64 predicted j
+    const double4_32a *p64, *v64;         // FP64 predicted j
     const g6x_irec *irec;
-    Partial *part;
+    void *part;                       // PartialDS (DS kernels) or Partial64 (FP64)
     int *nbl;                         // list entries  [slot][maxnb]
     int *nbc;                         // list counts   [slot]
     int *err;
@@ -392,6 +407,11 @@ struct ForceArgs {
     int J;
     int ni;
     double eps2;
+    // fused reduction: the last CTA to finish an i-tile reduces it into out
+    g6x_out *out;
+    const int *jidx;
+    unsigned *tcnt;                   // per i-tile: CTAs done (0 between launches)
+    int fused;
 };
 
 // Pair forces in FP32 with the DS separation of Eq. 3 (Sect. 2.3).  Per pair:
@@ -437,6 +457,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     __shared__ int s_abort;
     __shared__ float s_nnr[TJ > 1 ? NI * NT : 1];
     __shared__ int s_nnj[TJ > 1 ? NI * NT : 1];
+    __shared__ float s_ibuf[TJ > 1 ? 11 * ITILE : 1];
 
     const int tid = threadIdx.x;
     const int ti = tid % TI, tj = tid / TI;
@@ -496,12 +517,54 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
             }
     };
 
+    // The DS split of the i-positions (FP64, slow on GB300) is done once per
+    // i-particle: with TJ > 1 by the thread whose j-group is 0, shared with the
+    // other groups through shared memory.
     auto load_i = [&](int t) {
+        if constexpr (TJ > 1) {
+            for (int il = tid; il < ITILE; il += NT) {
+                const long long gi = (long long)t * ITILE + il;
+                float w[11];
+                if (gi < a.ni) {
+                    const g6x_irec &r = a.irec[gi];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const double x = r.x[d];
+                        const float hi = __double2float_rn(x);
+                        w[d] = hi;
+                        w[3 + d] = __double2float_rn(x - (double)hi);
+                        w[6 + d] = (float)r.v[d];
+                    }
+                    w[9] = (float)r.h2;
+                    w[10] = __int_as_float(r.index);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 10; ++q)
+                        w[q] = 0.f;
+                    w[10] = __int_as_float(-2);
+                }
+#pragma unroll
+                for (int q = 0; q < 11; ++q)
+                    s_ibuf[q * ITILE + il] = w[q];
+            }
+            __syncthreads();
+        }
 #pragma unroll
         for (int k = 0; k < NI; ++k) {
             int il = k * TI + ti;
             long long gi = (long long)t * ITILE + il;
-            if (gi < a.ni) {
+            if constexpr (TJ > 1) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float hi = s_ibuf[d * ITILE + il], lo = s_ibuf[(3 + d) * ITILE + il];
+                    const float w = -s_ibuf[(6 + d) * ITILE + il];
+                    nxh[k][d] = make_float2(-hi, -hi);
+                    nxl[k][d] = make_float2(-lo, -lo);
+                    nv[k][d] = make_float2(w, w);
+                }
+                h2[k] = s_ibuf[9 * ITILE + il];
+                iid[k] = __float_as_int(s_ibuf[10 * ITILE + il]);
+            } else if (gi < a.ni) {
                 const g6x_irec &r = a.irec[gi];
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
@@ -536,56 +599,163 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
             nbn[k] = 0;
         }
         since_flush = 0;
+        if constexpr (TJ > 1)
+            __syncthreads();          // s_ibuf is reused by the next segment
     };
 
     // First j of the thread's share of tile nnt[k] whose key equals nnr[k],
     // recomputed with the loop's arithmetic (packed lanes round like the
-    // scalar operations used here).
+    // scalar operations used here).  The loads of 8 j-particles are issued
+    // together so the rescan costs a few memory latencies, not one per j.
     auto nn_rescan = [&](int k) -> int {
         if (!(nnr[k] < INF) || nnt[k] < 0)
             return -1;
         const float *T = a.pt + (size_t)nnt[k] * JW * JT;
-        for (int kk = 0; kk < PPT; ++kk) {
-            const int jp = tj + kk * TJ;
-            for (int h = 0; h < 2; ++h) {
-                const int jj = 2 * jp + h;
-                const float dx = __fadd_rn(__fadd_rn(T[W_XH * JT + jj], nxh[k][0].x),
-                                           __fadd_rn(T[W_XL * JT + jj], nxl[k][0].x));
-                const float dy = __fadd_rn(__fadd_rn(T[W_YH * JT + jj], nxh[k][1].x),
-                                           __fadd_rn(T[W_YL * JT + jj], nxl[k][1].x));
-                const float dz = __fadd_rn(__fadd_rn(T[W_ZH * JT + jj], nxh[k][2].x),
-                                           __fadd_rn(T[W_ZL * JT + jj], nxl[k][2].x));
-                const float r2u = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-                const int id = __float_as_int(T[W_ID * JT + jj]);
-                const float key = (id == iid[k]) ? INF : r2u;
-                if (key == nnr[k])
-                    return nnt[k] * JT + jj;
+        constexpr int CH = 4;                       // j-pairs per chunk
+        for (int kk0 = 0; kk0 < PPT; kk0 += CH) {
+            float key[2 * CH];
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int kk = kk0 + u;
+                    const int jj = 2 * (tj + kk * TJ) + h;
+                    float r2u = INF;
+                    int id = -1;
+                    if (kk < PPT) {
+                        const float dx = __fadd_rn(__fadd_rn(__ldg(T + W_XH * JT + jj), nxh[k][0].x),
+                                                   __fadd_rn(__ldg(T + W_XL * JT + jj), nxl[k][0].x));
+                        const float dy = __fadd_rn(__fadd_rn(__ldg(T + W_YH * JT + jj), nxh[k][1].x),
+                                                   __fadd_rn(__ldg(T + W_YL * JT + jj), nxl[k][1].x));
+                        const float dz = __fadd_rn(__fadd_rn(__ldg(T + W_ZH * JT + jj), nxh[k][2].x),
+                                                   __fadd_rn(__ldg(T + W_ZL * JT + jj), nxl[k][2].x));
+                        r2u = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                        id = __float_as_int(__ldg(T + W_ID * JT + jj));
+                    }
+                    key[2 * u + h] = (id == iid[k]) ? INF : r2u;
+                }
             }
+#pragma unroll
+            for (int u = 0; u < 2 * CH; ++u)
+                if (key[u] == nnr[k])
+                    return nnt[k] * JT + 2 * (tj + (kk0 + u / 2) * TJ) + (u & 1);
         }
         return -1;
+    };
+
+    // Reduction of i-tile t by the last CTA that finished it (Sect. 2.3:
+    // partial forces are reduced on the GPU): every CTA that touched the tile
+    // has written its partial records; P lanes per i-particle (P a power of
+    // two, up to the warp, chosen from the number of segments) sum them in
+    // FP64, combine by shuffles and pick the nearest neighbour (ties to the
+    // lower j-slot); the launch uses this path only when a tile has few
+    // partials, so the tail it adds is short.
+    __shared__ int s_last;
+    auto reduce_tile = [&](int t, long long clo, long long chi) {
+        const int nseg = (int)(chi - clo + 1);
+        int P = 1;
+        while (P < 32 && 2 * P <= nseg)
+            P *= 2;
+        const int groups = NT / P;
+        const int rounds = (ITILE + groups - 1) / groups;
+        const int part = tid % P;
+        for (int r = 0; r < rounds; ++r) {
+            const int il = r * groups + tid / P;
+            const long long gi = (long long)t * ITILE + il;
+            const bool valid = il < ITILE && gi < a.ni;
+            float sh[7] = {0, 0, 0, 0, 0, 0, 0}, sl[7] = {0, 0, 0, 0, 0, 0, 0};
+            float br = INF;
+            int bj = -1;
+            if (valid) {
+                const PartialDS *PP = reinterpret_cast<const PartialDS *>(a.part);
+#pragma unroll 4
+                for (int q = part; q < nseg; q += P) {
+                    const PartialDS *Pp = PP + (size_t)(clo + q + t) * ITILE + il;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const float2 va = __ldcg(&Pp->acc[d]), vj = __ldcg(&Pp->jerk[d]);
+                        ds_acc(sh[d], sl[d], va.x, va.y);
+                        ds_acc(sh[3 + d], sl[3 + d], vj.x, vj.y);
+                    }
+                    const float2 vp = __ldcg(&Pp->pot);
+                    ds_acc(sh[6], sl[6], vp.x, vp.y);
+                    const float rr = __ldcg(&Pp->nnr2);
+                    const int jj = __ldcg(&Pp->nnj);
+                    if (jj >= 0 && (bj < 0 || rr < br || (rr == br && jj < bj))) {
+                        br = rr;
+                        bj = jj;
+                    }
+                }
+            }
+            for (int off = P / 2; off > 0; off >>= 1) {
+#pragma unroll
+                for (int q = 0; q < 7; ++q) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, sh[q], off);
+                    const float ol = __shfl_xor_sync(0xffffffffu, sl[q], off);
+                    ds_acc(sh[q], sl[q], oh, ol);
+                }
+                const float rr = __shfl_xor_sync(0xffffffffu, br, off);
+                const int jj = __shfl_xor_sync(0xffffffffu, bj, off);
+                if (jj >= 0 && (bj < 0 || rr < br || (rr == br && jj < bj))) {
+                    br = rr;
+                    bj = jj;
+                }
+            }
+            if (valid && part == 0) {
+                g6x_out o;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    o.acc[d] = (double)sh[d] + (double)sl[d];
+                    o.jerk[d] = (double)sh[3 + d] + (double)sl[3 + d];
+                }
+                o.pot = -((double)sh[6] + (double)sl[6]);
+                o.nnb = bj >= 0 ? a.jidx[bj] : -1;
+                o.nnr2 = bj >= 0 ? br : INF;
+                a.out[gi] = o;
+            }
+        }
+    };
+
+    // After this CTA's partials of i-tile t are written: count it in; the
+    // CTA that completes the count reduces the tile and resets the counter
+    // for the next launch.  (A launch that gives up early leaves counts
+    // behind; the host clears all counters after any reported error.)
+    auto tile_done = [&](int t) {
+        __threadfence();
+        __syncthreads();
+        const long long clo = work_owner((long long)t * a.J, a.W, G);
+        const long long chi = work_owner((long long)(t + 1) * a.J - 1, a.W, G);
+        if (tid == 0) {
+            const unsigned need = (unsigned)(chi - clo + 1);
+            const unsigned prev = atomicAdd(&a.tcnt[t], 1u);
+            s_last = (prev + 1 == need) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            reduce_tile(t, clo, chi);
+            if (tid == 0)
+                a.tcnt[t] = 0u;
+        }
+        __syncthreads();
     };
 
     auto finalize = [&](int t) {
         flush();
         const long long seg = c + t;
+        PartialDS *PP = reinterpret_cast<PartialDS *>(a.part);
         if constexpr (TJ == 1) {
 #pragma unroll
             for (int k = 0; k < NI; ++k) {
                 int il = k * TI + ti;
-                Partial *P = a.part + (size_t)seg * ITILE + il;
-                double s[7];
-#pragma unroll
-                for (int q = 0; q < 7; ++q) {
-                    float2 hl = cslot(k, q);
-                    s[q] = (double)hl.x + (double)hl.y;
-                }
+                PartialDS *P = PP + (size_t)seg * ITILE + il;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    P->acc[d] = s[d];
-                    P->jerk[d] = s[3 + d];
+                    P->acc[d] = cslot(k, d);
+                    P->jerk[d] = cslot(k, 3 + d);
                 }
-                P->pot = s[6];
-                P->nnr2 = (double)nnr[k];
+                P->pot = cslot(k, 6);
+                P->nnr2 = nnr[k];
                 P->nnj = nn_rescan(k);
                 if constexpr (LIST)
                     a.nbc[(size_t)seg * ITILE + il] = nbn[k];
@@ -594,7 +764,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
             // The TJ j-groups of an i-particle combine in place: every
             // thread's compensated sums are in comp[], its nearest neighbour
             // goes to s_nnr / s_nnj, and one thread per i-particle adds the
-            // groups in FP64 (ties of the neighbour to the lower j-slot).
+            // groups in compensated FP32 (neighbour ties to the lower j-slot).
 #pragma unroll
             for (int k = 0; k < NI; ++k) {
                 s_nnr[k * NT + tid] = nnr[k];
@@ -603,37 +773,43 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
             __syncthreads();
             for (int il = tid; il < ITILE; il += NT) {
                 const int k = il / TI, ii = il % TI;
-                double sum[7];
+                float sh[7], sl[7];
 #pragma unroll
-                for (int q = 0; q < 7; ++q)
-                    sum[q] = 0.0;
-                double br = INF;
+                for (int q = 0; q < 7; ++q) {
+                    sh[q] = 0.f;
+                    sl[q] = 0.f;
+                }
+                float br = INF;
                 int bj = -1;
                 for (int g = 0; g < TJ; ++g) {
                     const int o = g * TI + ii;
 #pragma unroll
                     for (int q = 0; q < 7; ++q) {
                         const float2 hl = comp[(k * 7 + q) * NT + o];
-                        sum[q] += (double)hl.x + (double)hl.y;
+                        ds_acc(sh[q], sl[q], hl.x, hl.y);
                     }
-                    const double r = s_nnr[k * NT + o];
+                    const float r = s_nnr[k * NT + o];
                     const int jj = s_nnj[k * NT + o];
                     if (jj >= 0 && (r < br || (r == br && (bj < 0 || jj < bj)))) {
                         br = r;
                         bj = jj;
                     }
                 }
-                Partial *P = a.part + (size_t)seg * ITILE + il;
+                PartialDS *P = PP + (size_t)seg * ITILE + il;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    P->acc[d] = sum[d];
-                    P->jerk[d] = sum[3 + d];
+                    P->acc[d] = make_float2(sh[d], sl[d]);
+                    P->jerk[d] = make_float2(sh[3 + d], sl[3 + d]);
                 }
-                P->pot = sum[6];
+                P->pot = make_float2(sh[6], sl[6]);
                 P->nnr2 = br;
                 P->nnj = bj;
             }
             __syncthreads();
+        }
+        if constexpr (!LIST) {
+            if (a.fused)
+                tile_done(t);
         }
     };
 
@@ -652,7 +828,6 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         const float2 *VY = reinterpret_cast<const float2 *>(S + W_VY * JT);
         const float2 *VZ = reinterpret_cast<const float2 *>(S + W_VZ * JT);
         const int2 *ID = reinterpret_cast<const int2 *>(S + W_ID * JT);
-        const int jbase = jt * JT;
 #pragma unroll UNR
         for (int kk = 0; kk < PPT; ++kk) {
             const int jp = tj + kk * TJ;
@@ -694,7 +869,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                 tmin[k] = fminf(tmin[k], fminf(key.x, key.y));
                 if constexpr (LIST) {
                     const int il = k * TI + ti;
-                    const int j0 = jbase + 2 * jp;
+                    const int j0 = jt * JT + 2 * jp;
                     int *dst = a.nbl + ((size_t)(c + t) * ITILE + il) * G6_MAXNB;
                     if (key.x < h2[k]) {
                         if (nbn[k] < G6_MAXNB)
@@ -762,7 +937,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
             if (tid == 0) {
                 for (int r = q; r < q + NSTAGE && r < ntile; ++r)
                     mbar_wait_bounded(&bar[r % NSTAGE], (uint32_t)((r / NSTAGE) & 1));
-                atomicCAS(a.err, 0, G6_ETIMEDOUT);
+                *(volatile int *)a.err = G6_ETIMEDOUT;
             }
             return;
         }
@@ -778,7 +953,7 @@ template <bool LIST>
 __global__ void __launch_bounds__(128) k_force_64(const ForceArgs a)
 {
     constexpr int TI = 128;
-    __shared__ double4 sp[JT], sv[JT];
+    __shared__ double4_32a sp[JT], sv[JT];
     const int tid = threadIdx.x;
     const long long G = gridDim.x, c = blockIdx.x;
     const long long wb = work_begin(c, a.W, G), we = work_begin(c + 1, a.W, G);
@@ -794,7 +969,7 @@ __global__ void __launch_bounds__(128) k_force_64(const ForceArgs a)
 
     auto finalize = [&](int t) {
         const long long seg = c + t;
-        Partial *P = a.part + (size_t)seg * TI + tid;
+        Partial64 *P = reinterpret_cast<Partial64 *>(a.part) + (size_t)seg * TI + tid;
         for (int d = 0; d < 3; ++d) {
             P->acc[d] = s[d];
             P->jerk[d] = s[3 + d];
@@ -839,7 +1014,7 @@ __global__ void __launch_bounds__(128) k_force_64(const ForceArgs a)
         __syncthreads();
         const int jbase = jt * JT;
         for (int jj = 0; jj < JT; ++jj) {
-            const double4 pj = sp[jj], vj = sv[jj];
+            const double4_32a pj = sp[jj], vj = sv[jj];
             const double dx = pj.x - xi[0], dy = pj.y - xi[1], dz = pj.z - xi[2];
             const double ux = vj.x - vi[0], uy = vj.y - vi[1], uz = vj.z - vi[2];
             const double r2u = dx * dx + dy * dy + dz * dz;
@@ -876,7 +1051,7 @@ __global__ void __launch_bounds__(128) k_force_64(const ForceArgs a)
 // ----------------------------------------------------------------- K3 ---
 
 struct ReduceArgs {
-    const Partial *part;
+    const void *part;                 // PartialDS or Partial64
     const int *nbl, *nbc;
     const int *jidx;
     g6x_out *out;
@@ -885,74 +1060,149 @@ struct ReduceArgs {
     int J, G, ni, itile, list;
 };
 
-// One warp per i-particle: lanes take the partials of the CTAs that touched
-// its i-tile, sum them in FP64 and combine with warp shuffles; the nearest
-// neighbour is the smallest |r|^2, ties to the lower j-slot (Sect. 2.3, 2.5).
+// Sum of partial records of one i-particle: compensated FP32 for the DS path
+// (converted to FP64 once, at the end), plain FP64 for the FP64 path; the
+// nearest neighbour is the smallest |r|^2, ties to the lower j-slot.
+template <class PT>
+struct PartialSum;
+
+template <>
+struct PartialSum<PartialDS> {
+    float h[7], l[7];
+    float br;
+    int bj;
+    __device__ void init()
+    {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            h[q] = 0.f;
+            l[q] = 0.f;
+        }
+        br = __int_as_float(0x7f800000);
+        bj = -1;
+    }
+    __device__ void nn(float r, int j)
+    {
+        if (j >= 0 && (bj < 0 || r < br || (r == br && j < bj))) {
+            br = r;
+            bj = j;
+        }
+    }
+    __device__ void add(const PartialDS &P)
+    {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            ds_acc(h[d], l[d], P.acc[d].x, P.acc[d].y);
+            ds_acc(h[3 + d], l[3 + d], P.jerk[d].x, P.jerk[d].y);
+        }
+        ds_acc(h[6], l[6], P.pot.x, P.pot.y);
+        nn(P.nnr2, P.nnj);
+    }
+    __device__ void shfl_combine(int off)
+    {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const float oh = __shfl_xor_sync(0xffffffffu, h[q], off);
+            const float ol = __shfl_xor_sync(0xffffffffu, l[q], off);
+            ds_acc(h[q], l[q], oh, ol);
+        }
+        const float r = __shfl_xor_sync(0xffffffffu, br, off);
+        const int j = __shfl_xor_sync(0xffffffffu, bj, off);
+        nn(r, j);
+    }
+    __device__ double value(int q) const { return (double)h[q] + (double)l[q]; }
+    __device__ float nnr2() const { return br; }
+};
+
+template <>
+struct PartialSum<Partial64> {
+    double s[7];
+    double br;
+    int bj;
+    __device__ void init()
+    {
+#pragma unroll
+        for (int q = 0; q < 7; ++q)
+            s[q] = 0.0;
+        br = __longlong_as_double(0x7ff0000000000000ll);
+        bj = -1;
+    }
+    __device__ void nn(double r, int j)
+    {
+        if (j >= 0 && (bj < 0 || r < br || (r == br && j < bj))) {
+            br = r;
+            bj = j;
+        }
+    }
+    __device__ void add(const Partial64 &P)
+    {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            s[d] += P.acc[d];
+            s[3 + d] += P.jerk[d];
+        }
+        s[6] += P.pot;
+        nn(P.nnr2, P.nnj);
+    }
+    __device__ void shfl_combine(int off)
+    {
+#pragma unroll
+        for (int q = 0; q < 7; ++q)
+            s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+        const double r = __shfl_xor_sync(0xffffffffu, br, off);
+        const int j = __shfl_xor_sync(0xffffffffu, bj, off);
+        nn(r, j);
+    }
+    __device__ double value(int q) const { return s[q]; }
+    __device__ float nnr2() const { return (float)br; }
+};
+
+template <class PS>
+__device__ __forceinline__ g6x_out result_of(const PS &acc, const int *jidx)
+{
+    g6x_out o;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        o.acc[d] = acc.value(d);
+        o.jerk[d] = acc.value(3 + d);
+    }
+    o.pot = -acc.value(6);
+    o.nnb = acc.bj >= 0 ? jidx[acc.bj] : -1;
+    o.nnr2 = acc.bj >= 0 ? acc.nnr2() : __int_as_float(0x7f800000);
+    return o;
+}
+
+// K3, one warp per i-particle: lanes take the partials of the CTAs that
+// touched its i-tile and combine with warp shuffles (Sect. 2.3, 2.5).
 // Neighbour lists are concatenated in segment order, which is ascending j,
 // and truncated at G6_MAXNB (Sect. 4).
+template <class PT>
 __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a)
 {
     const int lane = threadIdx.x & 31;
     const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= a.ni)
         return;
+    const PT *part = reinterpret_cast<const PT *>(a.part);
     const int t = (int)(i / a.itile), il = (int)(i % a.itile);
     const long long p0 = (long long)t * a.J, p1 = p0 + a.J;
     const long long clo = work_owner(p0, a.W, a.G), chi = work_owner(p1 - 1, a.W, a.G);
-    double s[7] = {0, 0, 0, 0, 0, 0, 0};
-    double br = __longlong_as_double(0x7ff0000000000000ll);
-    int bj = -1;
-    for (long long cc = clo + lane; cc <= chi; cc += 32) {
-        long long b = max(work_begin(cc, a.W, a.G), p0);
-        long long e = min(work_begin(cc + 1, a.W, a.G), p1);
-        if (e <= b)
-            continue;
-        const Partial &P = a.part[(size_t)(cc + t) * a.itile + il];
-        for (int d = 0; d < 3; ++d) {
-            s[d] += P.acc[d];
-            s[3 + d] += P.jerk[d];
-        }
-        s[6] += P.pot;
-        if (P.nnj >= 0 && (P.nnr2 < br || (P.nnr2 == br && (bj < 0 || P.nnj < bj)))) {
-            br = P.nnr2;
-            bj = P.nnj;
-        }
-    }
+    PartialSum<PT> acc;
+    acc.init();
+#pragma unroll 4
+    for (long long cc = clo + lane; cc <= chi; cc += 32)
+        acc.add(part[(size_t)(cc + t) * a.itile + il]);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-        for (int q = 0; q < 7; ++q)
-            s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
-        double r = __shfl_xor_sync(0xffffffffu, br, off);
-        int jj = __shfl_xor_sync(0xffffffffu, bj, off);
-        if (jj >= 0 && (bj < 0 || r < br || (r == br && jj < bj))) {
-            br = r;
-            bj = jj;
-        }
-    }
-    if (lane == 0) {
-        g6x_out o;
-        for (int d = 0; d < 3; ++d) {
-            o.acc[d] = s[d];
-            o.jerk[d] = s[3 + d];
-        }
-        o.pot = -s[6];
-        o.nnb = bj >= 0 ? a.jidx[bj] : -1;
-        o.nnr2 = bj >= 0 ? (float)br : __int_as_float(0x7f800000);
-        a.out[i] = o;
-    }
+    for (int off = 16; off > 0; off >>= 1)
+        acc.shfl_combine(off);
+    if (lane == 0)
+        a.out[i] = result_of(acc, a.jidx);
     if (!a.list)
         return;
     long long base = 0, total = 0;
     for (long long c0 = clo; c0 <= chi; c0 += 32) {
         long long cc = c0 + lane;
-        int cnt = 0;
-        if (cc <= chi) {
-            long long b = max(work_begin(cc, a.W, a.G), p0);
-            long long e = min(work_begin(cc + 1, a.W, a.G), p1);
-            if (e > b)
-                cnt = a.nbc[(size_t)(cc + t) * a.itile + il];
-        }
+        int cnt = cc <= chi ? a.nbc[(size_t)(cc + t) * a.itile + il] : 0;
         int kept = min(cnt, G6_MAXNB);
         int incl = kept;
 #pragma unroll
@@ -979,78 +1229,39 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a)
 // K3 for blocks whose i-tiles were split over many CTAs (small m): one CTA
 // of 256 threads per i-particle, the partials strided over all its threads,
 // combined by warp shuffles and then across the 8 warps.  No lists.
+template <class PT>
 __global__ void __launch_bounds__(256) k_reduce_wide(const ReduceArgs a)
 {
     const long long i = blockIdx.x;
     if (i >= a.ni)
         return;
+    const PT *part = reinterpret_cast<const PT *>(a.part);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t = (int)(i / a.itile), il = (int)(i % a.itile);
     const long long p0 = (long long)t * a.J, p1 = p0 + a.J;
     const long long clo = work_owner(p0, a.W, a.G), chi = work_owner(p1 - 1, a.W, a.G);
-    double s[7] = {0, 0, 0, 0, 0, 0, 0};
-    double br = __longlong_as_double(0x7ff0000000000000ll);
-    int bj = -1;
-    for (long long cc = clo + tid; cc <= chi; cc += 256) {
-        long long b = max(work_begin(cc, a.W, a.G), p0);
-        long long e = min(work_begin(cc + 1, a.W, a.G), p1);
-        if (e <= b)
-            continue;
-        const Partial &P = a.part[(size_t)(cc + t) * a.itile + il];
-        for (int d = 0; d < 3; ++d) {
-            s[d] += P.acc[d];
-            s[3 + d] += P.jerk[d];
-        }
-        s[6] += P.pot;
-        if (P.nnj >= 0 && (P.nnr2 < br || (P.nnr2 == br && (bj < 0 || P.nnj < bj)))) {
-            br = P.nnr2;
-            bj = P.nnj;
-        }
-    }
+    PartialSum<PT> acc;
+    acc.init();
+#pragma unroll 4
+    for (long long cc = clo + tid; cc <= chi; cc += 256)
+        acc.add(part[(size_t)(cc + t) * a.itile + il]);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-        for (int q = 0; q < 7; ++q)
-            s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
-        double r = __shfl_xor_sync(0xffffffffu, br, off);
-        int jj = __shfl_xor_sync(0xffffffffu, bj, off);
-        if (jj >= 0 && (bj < 0 || r < br || (r == br && jj < bj))) {
-            br = r;
-            bj = jj;
-        }
-    }
-    __shared__ double ws[8][8];
-    __shared__ int wj[8];
-    if (lane == 0) {
-        for (int q = 0; q < 7; ++q)
-            ws[warp][q] = s[q];
-        ws[warp][7] = br;
-        wj[warp] = bj;
-    }
+    for (int off = 16; off > 0; off >>= 1)
+        acc.shfl_combine(off);
+    __shared__ PartialSum<PT> ws[8];
+    if (lane == 0)
+        ws[warp] = acc;
     __syncthreads();
-    if (tid == 0) {
-        double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-        br = __longlong_as_double(0x7ff0000000000000ll);
-        bj = -1;
-        for (int w = 0; w < 8; ++w) {
-            for (int q = 0; q < 7; ++q)
-                acc[q] += ws[w][q];
-            const double r = ws[w][7];
-            const int jj = wj[w];
-            if (jj >= 0 && (bj < 0 || r < br || (r == br && jj < bj))) {
-                br = r;
-                bj = jj;
-            }
-        }
-        g6x_out o;
-        for (int d = 0; d < 3; ++d) {
-            o.acc[d] = acc[d];
-            o.jerk[d] = acc[3 + d];
-        }
-        o.pot = -acc[6];
-        o.nnb = bj >= 0 ? a.jidx[bj] : -1;
-        o.nnr2 = bj >= 0 ? (float)br : __int_as_float(0x7f800000);
-        a.out[i] = o;
+    if (warp == 0) {
+        if (lane < 8)
+            acc = ws[lane];
+        else
+            acc.init();
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1)
+            acc.shfl_combine(off);
+        if (lane == 0)
+            a.out[i] = result_of(acc, a.jidx);
     }
 }
 
@@ -1099,6 +1310,22 @@ constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 int g_occ[kNumVariants];
 bool g_smem_set[kNumVariants];
 
+// Every kernel of the library asks for the same L1 / shared-memory split
+// (the most shared memory), so consecutive launches never wait for an SM to
+// re-divide its on-chip memory.
+template <class F>
+void pin_carveout(F *fn)
+{
+    static bool done = false;      // one flag per kernel (per template instance)
+    if (!done) {
+        cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaGetLastError();
+        done = true;
+    }
+}
+
 cudaError_t prepare_variant(int v)
 {
     if (!g_smem_set[v]) {
@@ -1110,6 +1337,10 @@ cudaError_t prepare_variant(int v)
             if (e != cudaSuccess)
                 return e;
         }
+        cudaFuncSetAttribute(reinterpret_cast<const void *>(kVariants[v].fn),
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaGetLastError();
         g_smem_set[v] = true;
     }
     return cudaSuccess;
@@ -1224,16 +1455,17 @@ ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
         v = list ? 8 : 7;
     } else if (list) {
         v = ni <= 32 ? 6 : 5;
-    } else if (ni <= 16) {
-        v = 4;
     } else if (ni <= 32) {
-        v = 3;
-    } else if (ni <= 64) {
-        v = 2;
-    } else if (ni <= 8192) {
-        v = 1;
+        v = 4;                       // 16 x 16 threads, one i each
+    } else if (ni <= 128) {
+        v = 14;                      // 16 x 16 threads, two i each
+    } else if (ni <= 256) {
+        v = 15;                      // 32 x 8 threads, two i each
+    } else if (ni <= 2048) {
+        v = 16;                      // 64 x 4 threads, two i each
     } else {
-        v = 0;
+        v = 0;                       // 128 threads, two i each, whole j-tiles
+        gmul = 2;
     }
     const VariantInfo &vi = kVariants[v].info;
     ForceConfig c{};
@@ -1270,6 +1502,7 @@ cudaError_t launch_init_store(JStore js, cudaStream_t s)
     int blocks = (js.cap + 255) / 256;
     if (blocks > 65535)
         blocks = 65535;
+    pin_carveout(k_init_store);
     k_init_store<<<blocks, 256, 0, s>>>(js);
     return cudaGetLastError();
 }
@@ -1278,6 +1511,7 @@ cudaError_t launch_irec_from_store(JStore js, g6x_irec *out, int m, cudaStream_t
 {
     if (m <= 0)
         return cudaSuccess;
+    pin_carveout(k_irec_from_store);
     k_irec_from_store<<<(m + 255) / 256, 256, 0, s>>>(js, out, m);
     return cudaGetLastError();
 }
@@ -1286,6 +1520,7 @@ cudaError_t launch_scatter(const g6x_jrec *d_rec, int n, JStore js, cudaStream_t
 {
     if (n <= 0)
         return cudaSuccess;
+    pin_carveout(k_scatter);
     k_scatter<<<(n + 127) / 128, 128, 0, s>>>(d_rec, n, js);
     return cudaGetLastError();
 }
@@ -1293,24 +1528,40 @@ cudaError_t launch_scatter(const g6x_jrec *d_rec, int n, JStore js, cudaStream_t
 cudaError_t launch_predict(int kind, JStore js, Pred p, int nj, int nj_pad,
                            double t, int sm_count, cudaStream_t s)
 {
-    int blocks = (nj_pad + 255) / 256;
-    int cap = sm_count * 8;
+    return launch_update_predict(kind, js, p, nj, nj_pad, t, nullptr, nullptr, 0, sm_count, s);
+}
+
+cudaError_t launch_update_predict(int kind, JStore js, Pred p, int nj, int nj_pad, double t,
+                                  const g6x_jrec *rec, const int *toff, int ntiles_all,
+                                  int sm_count, cudaStream_t s)
+{
+    const bool upd = rec != nullptr && toff != nullptr && ntiles_all > 0;
+    const int nt = upd ? ntiles_all : nj_pad / JT;
+    int blocks = nt;
+    const int cap = sm_count * 8;
     if (blocks > cap)
         blocks = cap;
     if (blocks < 1)
         blocks = 1;
-    if (kind == PRED_FP64)
-        k_predict_64<<<blocks, 256, 0, s>>>(js, p, nj, nj_pad, t);
-    else if (kind == PRED_DS_X64)
-        k_predict_ds_x64<<<blocks, JT, 0, s>>>(js, p, nj, nj_pad, t);
-    else
-        k_predict_ds<<<blocks, JT, 0, s>>>(js, p, nj, nj_pad, t);
+#define G6_K1(K, U)                                                                       \
+    do {                                                                                  \
+        pin_carveout(k_predict<K, U>);                                                    \
+        k_predict<K, U><<<blocks, JT, 0, s>>>(js, p, nj, nj_pad, t, rec, toff, ntiles_all); \
+    } while (0)
+    if (kind == PRED_FP64) {
+        if (upd) G6_K1(PRED_FP64, true); else G6_K1(PRED_FP64, false);
+    } else if (kind == PRED_DS_X64) {
+        if (upd) G6_K1(PRED_DS_X64, true); else G6_K1(PRED_DS_X64, false);
+    } else {
+        if (upd) G6_K1(PRED_DS, true); else G6_K1(PRED_DS, false);
+    }
+#undef G6_K1
     return cudaGetLastError();
 }
 
 cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
                          const g6x_irec *d_irec, int ni, double eps2,
-                         Partial *part, int *nbl_part, int *nbc_part,
+                         void *part, int *nbl_part, int *nbc_part,
                          int *d_err, cudaStream_t s)
 {
     if (cfg.work <= 0)
@@ -1318,7 +1569,7 @@ cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
     cudaError_t e = prepare_variant(cfg.variant);
     if (e != cudaSuccess)
         return e;
-    ForceArgs a;
+    ForceArgs a{};
     a.pt = p.pt;
     a.trange = p.trange;
     a.p64 = p.p64;
@@ -1337,7 +1588,40 @@ cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(const ForceConfig &cfg, const Partial *part,
+cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
+                               const g6x_irec *d_irec, int ni, double eps2, void *part,
+                               int *d_err, g6x_out *out, const int *jidx, unsigned *tcnt,
+                               cudaStream_t s)
+{
+    if (cfg.work <= 0)
+        return cudaSuccess;
+    if (cfg.list || cfg.prec != G6X_PREC_DS)
+        return cudaErrorInvalidValue;
+    cudaError_t e = prepare_variant(cfg.variant);
+    if (e != cudaSuccess)
+        return e;
+    ForceArgs a{};
+    a.pt = p.pt;
+    a.trange = p.trange;
+    a.p64 = p.p64;
+    a.v64 = p.v64;
+    a.irec = d_irec;
+    a.part = part;
+    a.err = d_err;
+    a.W = cfg.work;
+    a.J = cfg.jtiles;
+    a.ni = ni;
+    a.eps2 = eps2;
+    a.out = out;
+    a.jidx = jidx;
+    a.tcnt = tcnt;
+    a.fused = 1;
+    const Variant &v = kVariants[cfg.variant];
+    v.fn<<<cfg.grid, v.threads, v.smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const ForceConfig &cfg, const void *part,
                           const int *nbl_part, const int *nbc_part,
                           const int *jidx, int ni, g6x_out *d_out, int *d_nbl,
                           int *d_nblen, cudaStream_t s)
@@ -1361,12 +1645,24 @@ cudaError_t launch_reduce(const ForceConfig &cfg, const Partial *part,
     // many partials per i-particle (small blocks spread over many CTAs):
     // one CTA per i-particle; otherwise one warp per i-particle
     const long long per_i = (long long)cfg.grid / cfg.n_itile + 1;
-    if (!cfg.list && per_i >= 64) {
-        k_reduce_wide<<<ni, 256, 0, s>>>(a);
+    const bool wide = !cfg.list && per_i >= 64;
+    const int blocks = wide ? ni : (int)(((long long)ni * 32 + 255) / 256);
+    if (cfg.prec == G6X_PREC_FP64) {
+        if (wide) {
+            pin_carveout(k_reduce_wide<Partial64>);
+            k_reduce_wide<Partial64><<<blocks, 256, 0, s>>>(a);
+        } else {
+            pin_carveout(k_reduce<Partial64>);
+            k_reduce<Partial64><<<blocks, 256, 0, s>>>(a);
+        }
     } else {
-        long long threads = (long long)ni * 32;
-        int blocks = (int)((threads + 255) / 256);
-        k_reduce<<<blocks, 256, 0, s>>>(a);
+        if (wide) {
+            pin_carveout(k_reduce_wide<PartialDS>);
+            k_reduce_wide<PartialDS><<<blocks, 256, 0, s>>>(a);
+        } else {
+            pin_carveout(k_reduce<PartialDS>);
+            k_reduce<PartialDS><<<blocks, 256, 0, s>>>(a);
+        }
     }
     return cudaGetLastError();
 }
