@@ -364,6 +364,109 @@ int g6h_profile(const g6h_sim *s, double *sec_sched, double *sec_force,
 
 void g6h_destroy(g6h_sim *s);
 
+/* ------------------------------------------------ batches of clusters ----
+ * Many independent star clusters in one device (Sect. 2: one library
+ * instance per cluster id, each with its own j-memory and block time).  A
+ * batch keeps the j-memory of ncl clusters side by side; one batch
+ * calculation computes, for every cluster k, the forces on its ni[k]
+ * i-particles at its own block time t_blk[k] with its own softening
+ * eps2[k] (Eq. 1 - Eq. 3, DS arithmetic), all clusters in one launch
+ * sequence: the j-update fused into the prediction, one force kernel whose
+ * work line concatenates every cluster's (i-tile, j-tile) pairs, and the
+ * partial-sum reduction.  Cluster k's particle q lives at j-address q
+ * (0 <= q < nj[k]); particle indices, self-exclusion and nearest neighbours
+ * are per cluster.  Neighbour lists are not available on batches.
+ * Threading: a batch is used from one host thread at a time. */
+
+typedef struct g6x_batch g6x_batch;
+
+/* Create a batch of ncl clusters with nj[k] >= 1 j-particles each.
+ * precision: G6X_PREC_DS or G6X_PREC_DS_X64.  variant: batch force kernel
+ * (0 .. 4: 16x16x1, 16x16x2, 32x8x2, 64x4x2, 128x1x2 threads along i x
+ * threads along j x i-particles per thread; -1 = 0).  grid_mul: CTAs =
+ * SMs x resident CTAs per SM x grid_mul (0 = 1).  Device memory comes from
+ * the allocator set with g6x_set_allocator; i-records, results and the
+ * per-step tables are in mapped pinned host memory.  Returns NULL on error
+ * (*err = G6_EINVAL, G6_ENOMEM, G6_ENODEV or G6_EIO). */
+g6x_batch *g6x_batch_create(int ncl, const int nj[], int precision, int variant,
+                            int grid_mul, int *err);
+int g6x_batch_destroy(g6x_batch *b);
+
+/* Host pointer to cluster cl's i-record array (nj[cl] records, mapped
+ * memory written by the caller before g6x_batch_calc; index = the
+ * particle's index within the cluster, used for self-exclusion; h2 unused),
+ * and to its result array (g6x_out, valid after g6x_batch_calc returns;
+ * nnb is the nearest neighbour's index within the cluster).  NULL on a bad
+ * batch or cluster. */
+g6x_irec *g6x_batch_irecs(g6x_batch *b, int cl);
+const g6x_out *g6x_batch_results(const g6x_batch *b, int cl);
+
+/* Stage particle `address` of cluster cl (same arguments and meaning as
+ * g6_set_j_particle; index is the particle's index within the cluster).
+ * The record reaches j-memory at the next g6x_batch_calc.  Returns 0,
+ * G6_EINVAL or G6_ENOMEM. */
+int g6x_batch_set_j(g6x_batch *b, int cl, int address, int index, double tj,
+                    double mass, const double j6[3], const double a2[3],
+                    const double v[3], const double x[3]);
+
+/* Stage n particles of cluster cl at once: address[n], index[n], tj[n],
+ * mass[n], j6, a2, v, x [n][3] (same meaning as g6x_batch_set_j).  Checks
+ * every address and index before staging any.  Returns 0, G6_EINVAL or
+ * G6_ENOMEM. */
+int g6x_batch_set_j_many(g6x_batch *b, int cl, int n, const int address[],
+                         const int index[], const double tj[], const double mass[],
+                         const double j6[], const double a2[], const double v[],
+                         const double x[]);
+
+/* One batch calculation: per cluster k, predict its j-particles to t_blk[k]
+ * (Eq. 1, Eq. 2) and compute forces on its first ni[k] i-records
+ * (0 <= ni[k] <= nj[k]; 0 = idle this step) with softening eps2[k].
+ * mode 0: one CUDA-graph replay of the three kernels (captured at the first
+ * call); 1: the same three kernels as plain launches; 2: one launch
+ * sequence per active cluster.  Blocks until the results are in.  Returns 0,
+ * G6_EINVAL, G6_ETIMEDOUT or G6_EIO. */
+int g6x_batch_calc(g6x_batch *b, const double t_blk[], const double eps2[],
+                   const int ni[], int mode);
+
+/* Kernels launched by the batch (a graph replay counts its three). */
+long long g6x_batch_launch_count(const g6x_batch *b);
+
+/* Hermite driver over a batch: every cluster runs the block-time-step
+ * integration of g6h_run with its own block scheduler; one g6hb_step
+ * advances each cluster that has not reached t_end by one of its block
+ * steps, all clusters' forces in one g6x_batch_calc. */
+typedef struct g6hb_sim g6hb_sim;
+
+/* ncl clusters of n[k] particles; m, x, v hold the clusters one after
+ * another (m[sum n], x and v [sum n][3]); eps2[k] per cluster; eta, eta_s,
+ * dt_max, dt_min as for g6h_create; variant and grid_mul as for
+ * g6x_batch_create; mode as for g6x_batch_calc.  Computes the initial
+ * forces.  NULL on error. */
+g6hb_sim *g6hb_create(int ncl, const int n[], const double *m, const double *x,
+                      const double *v, const double eps2[], double eta,
+                      double eta_s, double dt_max, double dt_min, int variant,
+                      int grid_mul, int mode, int *err);
+
+/* One batch step up to t_end: returns the number of clusters that stepped
+ * (0 once every cluster has reached t_end) or a negative error. */
+int g6hb_step(g6hb_sim *s, double t_end);
+
+/* Steps until every cluster reaches t_end (a multiple of dt_max). */
+int g6hb_run(g6hb_sim *s, double t_end);
+
+/* Change the launch mode (0, 1, 2 as for g6x_batch_calc). */
+int g6hb_set_mode(g6hb_sim *s, int mode);
+
+/* Counters: batch steps, sum of active particles, sum over steps and
+ * clusters of ni x nj, seconds in g6x_batch_calc and on the host. */
+int g6hb_stats(const g6hb_sim *s, long long *nsteps, long long *nactive,
+               long long *interactions, double *sec_gpu, double *sec_host);
+
+/* State of every particle in creation order: x, v [sum n][3], t [sum n]. */
+int g6hb_get_state(const g6hb_sim *s, double *x, double *v, double *t);
+
+void g6hb_destroy(g6hb_sim *s);
+
 #ifdef __cplusplus
 }
 #endif

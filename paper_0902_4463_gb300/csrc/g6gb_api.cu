@@ -160,6 +160,17 @@ struct Ctx {
 
 Ctx g_ctx[G6_MAX_CLUSTERS];
 
+}  // namespace
+
+namespace g6 {
+void *dev_alloc_hooked(size_t bytes) { return dev_alloc(bytes); }
+void dev_free_hooked(void *p) { dev_free(p); }
+void *host_alloc_zero_copy(size_t bytes, void **dev) { return host_alloc_mapped(bytes, dev); }
+void host_free_pinned(void *p) { host_free(p); }
+}  // namespace g6
+
+namespace {
+
 enum Phase { PH_SCATTER = 0, PH_PREDICT = 1, PH_FORCE = 2, PH_REDUCE = 3 };
 
 cudaEvent_t pool_event(Ctx &c)

@@ -97,6 +97,48 @@ struct VariantInfo {
     int ti, tj, nper, list, prec;
 };
 
+// Work geometry of a batch of independent clusters: cluster k holds j-tiles
+// [cl_jtile[k], cl_jtile[k] + its tile count) and i-records
+// [cl_ioff[k], cl_ioff[k] + cl_ni[k]); its active i-particles form
+// ceil(cl_ni[k] / i-tile) i-tiles, and global i-tile g covers work positions
+// [gt_start[g], gt_start[g+1]) of the one work line cut over the CTAs.
+// hdr[0] = total work, hdr[1] = number of global i-tiles.  Kernels read all
+// of it from memory, so one captured graph serves every step.
+struct BatchTables {
+    const long long *hdr;
+    const long long *gt_start;
+    const int *gt_cluster, *gt_itile;
+    const int *cl_jtile, *cl_ioff, *cl_ni;
+    const double *cl_eps2;
+};
+
+// Batch prediction: tile -> cluster map; per cluster first j-tile, particle
+// count, active count this step and block time.
+struct BatchPredTables {
+    const int *tile_cluster, *cl_jtile, *cl_nj, *cl_ni;
+    const double *cl_t;
+};
+
+// Allocation helpers of the C ABI layer (the device one honours the
+// g6x_set_allocator hook; the host one returns mapped pinned memory and its
+// device address).
+void *dev_alloc_hooked(size_t bytes);
+void dev_free_hooked(void *p);
+void *host_alloc_zero_copy(size_t bytes, void **dev);
+void host_free_pinned(void *p);
+
+int batch_variant_count();
+VariantInfo batch_variant_info(int v);
+int batch_variant_occupancy(int v);
+cudaError_t launch_predict_batch(int kind, JStore js, Pred p, BatchPredTables bp,
+                                 const g6x_jrec *rec, const int *toff, int tile0, int ntiles,
+                                 int sm_count, cudaStream_t s);
+cudaError_t launch_force_batch(int v, int grid, const Pred &p, const g6x_irec *d_irec,
+                               void *part, int *d_err, const BatchTables &bt, cudaStream_t s);
+cudaError_t launch_reduce_batch(int v, int grid, const void *part, const int *jidx,
+                                g6x_out *d_out, const BatchTables &bt, int blocks,
+                                cudaStream_t s);
+
 int variant_count();
 VariantInfo variant_info(int v);
 // Resident CTAs per SM of variant v (0 on error).

@@ -392,6 +392,44 @@ __global__ void __launch_bounds__(JT) k_predict(JStore js, Pred p, int nj, int n
     }
 }
 
+// K1 for a batch of clusters (tables described with BatchPredTables).
+template <int KIND>
+__global__ void __launch_bounds__(JT) k_predict_batch(JStore js, Pred p, BatchPredTables bp,
+                                                      const g6x_jrec *__restrict__ rec,
+                                                      const int *__restrict__ toff, int tile0,
+                                                      int ntiles)
+{
+    __shared__ int s_lo[JT / 32], s_hi[JT / 32];
+    for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const int tile = tile0 + tt;
+        if (rec && toff) {
+            for (int r = toff[tile] + threadIdx.x; r < toff[tile + 1]; r += JT)
+                store_record(rec[r], js);
+            __syncthreads();
+        }
+        const int k = bp.tile_cluster[tile];
+        if (bp.cl_ni[k] <= 0)
+            continue;                                  // cluster idle this step
+        const int local = (tile - bp.cl_jtile[k]) * JT + threadIdx.x;
+        const int slot = tile * JT + threadIdx.x;
+        const bool valid = local < bp.cl_nj[k];
+        const double t = bp.cl_t[k];
+        if constexpr (KIND == PRED_FP64) {
+            predict_slot_64(js, p, slot, valid ? slot + 1 : slot, t);
+        } else {
+            float *o = p.pt + (size_t)tile * (JW * JT) + threadIdx.x;
+            const int id = valid ? js.idx[slot] : -1;
+            tile_index_range(s_lo, s_hi, id, valid && id >= 0, &p.trange[tile]);
+            if (!valid)
+                far_slot_ds(o);
+            else if constexpr (KIND == PRED_DS)
+                predict_slot_ds(js, slot, t, o, id);
+            else
+                predict_slot_ds_x64(js, slot, t, o, id);
+        }
+    }
+}
+
 // ----------------------------------------------------------------- K2 ---
 
 struct ForceArgs {
@@ -412,6 +450,7 @@ struct ForceArgs {
     const int *jidx;
     unsigned *tcnt;                   // per i-tile: CTAs done (0 between launches)
     int fused;
+    BatchTables bt;                   // batch geometry (batch kernels only)
 };
 
 // Pair forces in FP32 with the DS separation of Eq. 3 (Sect. 2.3).  Per pair:
@@ -439,9 +478,10 @@ struct ForceArgs {
 // then folded into compensated (TwoSum) FP32 pairs kept in shared memory, so
 // rounding does not grow with n; the pairs are combined in FP64 when
 // partials are written.
-template <int TI, int TJ, int NI, bool LIST, int MINB = 1, int UNR = 2>
+template <int TI, int TJ, int NI, bool LIST, int MINB = 1, int UNR = 2, bool BATCH = false>
 __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
 {
+    static_assert(!(LIST && BATCH), "batches carry no neighbour lists");
     constexpr int NT = TI * TJ;
     constexpr int ITILE = TI * NI;
     constexpr int PPT = JT / 2 / TJ;                  // j-pairs per thread per tile
@@ -462,7 +502,53 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     const int tid = threadIdx.x;
     const int ti = tid % TI, tj = tid / TI;
     const long long G = gridDim.x, c = blockIdx.x;
-    const long long wb = work_begin(c, a.W, G), we = work_begin(c + 1, a.W, G);
+    // Work geometry: global i-tile g of a work position, its work range, its
+    // j-tile for a position, and where its i-records and results live.
+    long long W;
+    if constexpr (BATCH)
+        W = *(volatile const long long *)a.bt.hdr;
+    else
+        W = a.W;
+    auto g_start = [&](int g) -> long long {
+        if constexpr (BATCH)
+            return a.bt.gt_start[g];
+        else
+            return (long long)g * a.J;
+    };
+    auto g_of = [&](long long p) -> int {       // largest g with g_start(g) <= p
+        if constexpr (BATCH) {
+            int lo = 0, hi = (int)*(volatile const long long *)(a.bt.hdr + 1) - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.bt.gt_start[mid] <= p)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            return lo;
+        } else {
+            return (int)(p / a.J);
+        }
+    };
+    auto jt_of = [&](long long p, int g) -> int {
+        if constexpr (BATCH)
+            return a.bt.cl_jtile[a.bt.gt_cluster[g]] + (int)(p - a.bt.gt_start[g]);
+        else
+            return (int)(p - (long long)g * a.J);
+    };
+    // record index of slot il of i-tile g, or -1 past the active block
+    auto i_index = [&](int g, int il) -> long long {
+        if constexpr (BATCH) {
+            const int k = a.bt.gt_cluster[g];
+            const int li = a.bt.gt_itile[g] * ITILE + il;
+            return li < a.bt.cl_ni[k] ? (long long)a.bt.cl_ioff[k] + li : -1;
+        } else {
+            const long long gi = (long long)g * ITILE + il;
+            return gi < a.ni ? gi : -1;
+        }
+    };
+
+    const long long wb = work_begin(c, W, G), we = work_begin(c + 1, W, G);
     const int ntile = (int)(we - wb);
     if (ntile <= 0)
         return;
@@ -475,9 +561,12 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     }
     __syncthreads();
 
+    int issue_g = g_of(wb);                     // used by thread 0 only
     auto issue = [&](int q) {
-        long long p = wb + q;
-        int jt = (int)(p % a.J);
+        const long long p = wb + q;
+        while (g_start(issue_g + 1) <= p)
+            ++issue_g;
+        const int jt = jt_of(p, issue_g);
         int s = q % NSTAGE;
         mbar_expect_tx(&bar[s], TILE_BYTES);
         bulk_g2s(stage_buf + (size_t)s * JW * JT, a.pt + (size_t)jt * JW * JT, TILE_BYTES,
@@ -487,7 +576,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         for (int q = 0; q < NSTAGE && q < ntile; ++q)
             issue(q);
 
-    const float2 eps2 = make_float2((float)a.eps2, (float)a.eps2);
+    float2 eps2 = make_float2((float)a.eps2, (float)a.eps2);
     const float2 m3 = make_float2(-3.0f, -3.0f);
     const float INF = __int_as_float(0x7f800000);
     float2 nxh[NI][3], nxl[NI][3], nv[NI][3];
@@ -521,11 +610,15 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     // i-particle: with TJ > 1 by the thread whose j-group is 0, shared with the
     // other groups through shared memory.
     auto load_i = [&](int t) {
+        if constexpr (BATCH) {
+            const float e = (float)a.bt.cl_eps2[a.bt.gt_cluster[t]];
+            eps2 = make_float2(e, e);
+        }
         if constexpr (TJ > 1) {
             for (int il = tid; il < ITILE; il += NT) {
-                const long long gi = (long long)t * ITILE + il;
+                const long long gi = i_index(t, il);
                 float w[11];
-                if (gi < a.ni) {
+                if (gi >= 0) {
                     const g6x_irec &r = a.irec[gi];
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
@@ -552,7 +645,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
 #pragma unroll
         for (int k = 0; k < NI; ++k) {
             int il = k * TI + ti;
-            long long gi = (long long)t * ITILE + il;
+            const long long gi = TJ > 1 ? 0 : i_index(t, il);
             if constexpr (TJ > 1) {
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
@@ -564,7 +657,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                 }
                 h2[k] = s_ibuf[9 * ITILE + il];
                 iid[k] = __float_as_int(s_ibuf[10 * ITILE + il]);
-            } else if (gi < a.ni) {
+            } else if (gi >= 0) {
                 const g6x_irec &r = a.irec[gi];
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
@@ -661,8 +754,8 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         const int part = tid % P;
         for (int r = 0; r < rounds; ++r) {
             const int il = r * groups + tid / P;
-            const long long gi = (long long)t * ITILE + il;
-            const bool valid = il < ITILE && gi < a.ni;
+            const long long gi = il < ITILE ? i_index(t, il) : -1;
+            const bool valid = gi >= 0;
             float sh[7] = {0, 0, 0, 0, 0, 0, 0}, sl[7] = {0, 0, 0, 0, 0, 0, 0};
             float br = INF;
             int bj = -1;
@@ -723,8 +816,8 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     auto tile_done = [&](int t) {
         __threadfence();
         __syncthreads();
-        const long long clo = work_owner((long long)t * a.J, a.W, G);
-        const long long chi = work_owner((long long)(t + 1) * a.J - 1, a.W, G);
+        const long long clo = work_owner(g_start(t), W, G);
+        const long long chi = work_owner(g_start(t + 1) - 1, W, G);
         if (tid == 0) {
             const unsigned need = (unsigned)(chi - clo + 1);
             const unsigned prev = atomicAdd(&a.tcnt[t], 1u);
@@ -886,10 +979,13 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         }
     };
 
+    int cur_g = g_of(wb);
     for (int q = 0; q < ntile; ++q) {
         const long long p = wb + q;
-        const int t = (int)(p / a.J);
-        const int jt = (int)(p - (long long)t * a.J);
+        while (g_start(cur_g + 1) <= p)
+            ++cur_g;
+        const int t = cur_g;
+        const int jt = jt_of(p, t);
         if (t != cur_t) {
             if (cur_t >= 0)
                 finalize(cur_t);
@@ -1265,6 +1361,39 @@ __global__ void __launch_bounds__(256) k_reduce_wide(const ReduceArgs a)
     }
 }
 
+// K3 for a batch: one warp per (global i-tile, slot) with an active
+// i-particle; the CTAs that touched the i-tile follow from its work range.
+template <class PT>
+__global__ void __launch_bounds__(256) k_reduce_batch(const ReduceArgs a, BatchTables bt)
+{
+    const int lane = threadIdx.x & 31;
+    const long long W = *(volatile const long long *)bt.hdr;
+    const long long ngt = *(volatile const long long *)(bt.hdr + 1);
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const PT *part = reinterpret_cast<const PT *>(a.part);
+    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+         w < ngt * a.itile; w += nwarps) {
+        const int g = (int)(w / a.itile), il = (int)(w % a.itile);
+        const int k = bt.gt_cluster[g];
+        const int li = bt.gt_itile[g] * a.itile + il;
+        if (li >= bt.cl_ni[k])
+            continue;                                  // uniform within the warp
+        const long long clo = work_owner(bt.gt_start[g], W, a.G);
+        const long long chi = work_owner(bt.gt_start[g + 1] - 1, W, a.G);
+        PartialSum<PT> acc;
+        acc.init();
+#pragma unroll 4
+        for (long long cc = clo + lane; cc <= chi; cc += 32)
+            if (work_begin(cc, W, a.G) < work_begin(cc + 1, W, a.G))   // CTA had work
+                acc.add(part[(size_t)(cc + g) * a.itile + il]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            acc.shfl_combine(off);
+        if (lane == 0)
+            a.out[(long long)bt.cl_ioff[k] + li] = result_of(acc, a.jidx);
+    }
+}
+
 // ------------------------------------------------------------ variants ---
 
 namespace {
@@ -1306,6 +1435,17 @@ const Variant kVariants[] = {
     {{64, 4, 2, 0, G6X_PREC_DS}, k_force_ds<64, 4, 2, false, 2, 2>, 256, ds_smem(256, 2)},
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+
+// Batch force kernels: the same pair loop over the batch work geometry.
+const Variant kBatchVariants[] = {
+    {{16, 16, 1, 0, G6X_PREC_DS}, k_force_ds<16, 16, 1, false, 1, 2, true>, 256, ds_smem(256, 1)},
+    {{16, 16, 2, 0, G6X_PREC_DS}, k_force_ds<16, 16, 2, false, 2, 2, true>, 256, ds_smem(256, 2)},
+    {{32, 8, 2, 0, G6X_PREC_DS}, k_force_ds<32, 8, 2, false, 2, 2, true>, 256, ds_smem(256, 2)},
+    {{64, 4, 2, 0, G6X_PREC_DS}, k_force_ds<64, 4, 2, false, 2, 2, true>, 256, ds_smem(256, 2)},
+    {{128, 1, 2, 0, G6X_PREC_DS}, k_force_ds<128, 1, 2, false, 3, 2, true>, 128, ds_smem(128, 2)},
+};
+constexpr int kNumBatchVariants = (int)(sizeof(kBatchVariants) / sizeof(kBatchVariants[0]));
+int g_bocc[kNumBatchVariants];
 
 int g_occ[kNumVariants];
 bool g_smem_set[kNumVariants];
@@ -1664,6 +1804,95 @@ cudaError_t launch_reduce(const ForceConfig &cfg, const void *part,
             k_reduce<PartialDS><<<blocks, 256, 0, s>>>(a);
         }
     }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- batch ---
+
+int batch_variant_count() { return kNumBatchVariants; }
+
+VariantInfo batch_variant_info(int v) { return kBatchVariants[v].info; }
+
+int batch_variant_occupancy(int v)
+{
+    if (v < 0 || v >= kNumBatchVariants)
+        return 0;
+    if (g_bocc[v] == 0) {
+        const Variant &bv = kBatchVariants[v];
+        if (cudaFuncSetAttribute(bv.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bv.smem)
+            != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        cudaFuncSetAttribute(reinterpret_cast<const void *>(bv.fn),
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bv.fn, bv.threads, bv.smem)
+            != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        g_bocc[v] = n;
+    }
+    return g_bocc[v];
+}
+
+cudaError_t launch_predict_batch(int kind, JStore js, Pred p, BatchPredTables bp,
+                                 const g6x_jrec *rec, const int *toff, int tile0, int ntiles,
+                                 int sm_count, cudaStream_t s)
+{
+    if (ntiles <= 0)
+        return cudaSuccess;
+    int blocks = ntiles < sm_count * 8 ? ntiles : sm_count * 8;
+#define G6_KB(K)                                                                        \
+    do {                                                                                \
+        pin_carveout(k_predict_batch<K>);                                               \
+        k_predict_batch<K><<<blocks, JT, 0, s>>>(js, p, bp, rec, toff, tile0, ntiles); \
+    } while (0)
+    if (kind == PRED_FP64)
+        G6_KB(PRED_FP64);
+    else if (kind == PRED_DS_X64)
+        G6_KB(PRED_DS_X64);
+    else
+        G6_KB(PRED_DS);
+#undef G6_KB
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force_batch(int v, int grid, const Pred &p, const g6x_irec *d_irec,
+                               void *part, int *d_err, const BatchTables &bt, cudaStream_t s)
+{
+    if (v < 0 || v >= kNumBatchVariants || grid < 1)
+        return cudaErrorInvalidValue;
+    if (batch_variant_occupancy(v) < 1)
+        return cudaErrorInvalidConfiguration;
+    ForceArgs a{};
+    a.pt = p.pt;
+    a.trange = p.trange;
+    a.irec = d_irec;
+    a.part = part;
+    a.err = d_err;
+    a.bt = bt;
+    const Variant &bv = kBatchVariants[v];
+    bv.fn<<<grid, bv.threads, bv.smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_batch(int v, int grid, const void *part, const int *jidx,
+                                g6x_out *d_out, const BatchTables &bt, int blocks,
+                                cudaStream_t s)
+{
+    if (v < 0 || v >= kNumBatchVariants)
+        return cudaErrorInvalidValue;
+    ReduceArgs a{};
+    a.part = part;
+    a.jidx = jidx;
+    a.out = d_out;
+    a.G = grid;
+    a.itile = kBatchVariants[v].info.ti * kBatchVariants[v].info.nper;
+    pin_carveout(k_reduce_batch<PartialDS>);
+    k_reduce_batch<PartialDS><<<blocks, 256, 0, s>>>(a, bt);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,10 @@ EXPORTS = [
     "g6x_autotune", "g6x_load_tuning", "g6x_clear_tuning", "g6x_get_predicted", "g6x_last_config",
     "g6x_launch_count", "g6x_set_timing", "g6x_get_timing", "g6h_correct_block", "g6h_create", "g6h_run", "g6h_get_state", "g6h_energy",
     "g6h_stats", "g6h_profile", "g6h_destroy",
+    "g6x_batch_create", "g6x_batch_destroy", "g6x_batch_irecs", "g6x_batch_results",
+    "g6x_batch_set_j", "g6x_batch_set_j_many", "g6x_batch_calc", "g6x_batch_launch_count",
+    "g6hb_create", "g6hb_step", "g6hb_run", "g6hb_set_mode", "g6hb_stats", "g6hb_get_state",
+    "g6hb_destroy",
 ]
 
 _lib = None
@@ -108,6 +112,21 @@ def lib():
             "g6h_stats": (I, [P, P, P, P]),
             "g6h_profile": (I, [P, P, P, P]),
             "g6h_destroy": (None, [P]),
+            "g6x_batch_create": (P, [I, P, I, I, I, P]),
+            "g6x_batch_destroy": (I, [P]),
+            "g6x_batch_irecs": (P, [P, I]),
+            "g6x_batch_results": (P, [P, I]),
+            "g6x_batch_set_j": (I, [P, I, I, I, D, D, P, P, P, P]),
+            "g6x_batch_set_j_many": (I, [P, I, I, P, P, P, P, P, P, P, P]),
+            "g6x_batch_calc": (I, [P, P, P, P, I]),
+            "g6x_batch_launch_count": (C.c_longlong, [P]),
+            "g6hb_create": (P, [I, P, P, P, P, P, D, D, D, D, I, I, I, P]),
+            "g6hb_step": (I, [P, D]),
+            "g6hb_run": (I, [P, D]),
+            "g6hb_set_mode": (I, [P, I]),
+            "g6hb_stats": (I, [P, P, P, P, P, P]),
+            "g6hb_get_state": (I, [P, P, P, P]),
+            "g6hb_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -423,6 +442,131 @@ class G6HSim:
     def close(self):
         if self.h:
             lib().g6h_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _mapped(ptr, dtype, n):
+    """numpy view of n records of dtype at a host address (mapped memory)."""
+    buf = (C.c_char * (n * dtype.itemsize)).from_address(ptr)
+    return np.frombuffer(buf, dtype=dtype, count=n)
+
+
+class G6Batch:
+    """Owner of a g6x_batch: ncl independent clusters computed together."""
+
+    def __init__(self, nj, precision=G6X_PREC_DS, variant=-1, grid_mul=0):
+        nj = _i(nj).reshape(-1)
+        err = C.c_int(0)
+        h = lib().g6x_batch_create(len(nj), _p(nj), precision, variant, grid_mul, C.byref(err))
+        if not h:
+            raise G6Error(err.value or G6_EINVAL, "g6x_batch_create")
+        self.h = h
+        self.nj = nj
+        self.ncl = len(nj)
+
+    def irecs(self, cl):
+        """Writable IREC view of cluster cl's i-records (mapped memory)."""
+        return _mapped(lib().g6x_batch_irecs(self.h, cl), IREC, int(self.nj[cl]))
+
+    def results(self, cl, ni):
+        """Copy of cluster cl's first ni results."""
+        return _mapped(lib().g6x_batch_results(self.h, cl), OUT, int(self.nj[cl]))[:ni].copy()
+
+    def set_j(self, cl, m, x, v, a2=None, j6=None, tj=0.0, addr=None):
+        """Stage particles of cluster cl: addresses addr (default all nj[cl]),
+        index = address; a2 = a/2 and j6 = j/6 pre-scaled; tj scalar or per
+        particle."""
+        addr = np.arange(int(self.nj[cl])) if addr is None else np.asarray(addr).reshape(-1)
+        n = len(addr)
+        m = _d(m).reshape(-1)
+        x, v = _d(x, (n, 3)), _d(v, (n, 3))
+        a2 = np.zeros((n, 3)) if a2 is None else _d(a2, (n, 3))
+        j6 = np.zeros((n, 3)) if j6 is None else _d(j6, (n, 3))
+        tj = _d(np.broadcast_to(np.asarray(tj, dtype=np.float64), (n,)))
+        addr = _i(addr)
+        _check(lib().g6x_batch_set_j_many(self.h, cl, n, _p(addr), _p(addr), _p(tj), _p(m),
+                                          _p(j6), _p(a2), _p(v), _p(x)),
+               "g6x_batch_set_j_many")
+
+    def set_i(self, cl, x, v, index=None):
+        n = len(x)
+        r = self.irecs(cl)
+        r["x"][:n] = x
+        r["v"][:n] = v
+        r["h2"][:n] = 0.0
+        r["index"][:n] = np.arange(n) if index is None else index
+        r["pad"][:n] = 0
+
+    def calc(self, t_blk, eps2, ni, mode=0):
+        t_blk, eps2, ni = _d(t_blk), _d(eps2), _i(ni)
+        return _check(lib().g6x_batch_calc(self.h, _p(t_blk), _p(eps2), _p(ni), int(mode)),
+                      "g6x_batch_calc")
+
+    def launch_count(self):
+        return lib().g6x_batch_launch_count(self.h)
+
+    def close(self):
+        if self.h:
+            lib().g6x_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class G6HBatchSim:
+    """Owner of a g6hb_sim: the Hermite driver over a batch of clusters."""
+
+    def __init__(self, clusters, eps2, eta, eta_s=0.0, dt_max=2.0 ** -4, dt_min=2.0 ** -40,
+                 variant=-1, grid_mul=0, mode=0):
+        n = _i([len(c[0]) for c in clusters])
+        m = _d(np.concatenate([c[0] for c in clusters]))
+        x = _d(np.concatenate([c[1] for c in clusters]))
+        v = _d(np.concatenate([c[2] for c in clusters]))
+        eps2 = _d(np.broadcast_to(np.asarray(eps2, dtype=np.float64), (len(n),)))
+        err = C.c_int(0)
+        h = lib().g6hb_create(len(n), _p(n), _p(m), _p(x), _p(v), _p(eps2), float(eta),
+                              float(eta_s), float(dt_max), float(dt_min), int(variant),
+                              int(grid_mul), int(mode), C.byref(err))
+        if not h:
+            raise G6Error(err.value or G6_EINVAL, "g6hb_create")
+        self.h = h
+        self.n = n
+        self.off = np.concatenate([[0], np.cumsum(n)])
+
+    def step(self, t_end):
+        return _check(lib().g6hb_step(self.h, float(t_end)), "g6hb_step")
+
+    def run(self, t_end):
+        return _check(lib().g6hb_run(self.h, float(t_end)), "g6hb_run")
+
+    def set_mode(self, mode):
+        return _check(lib().g6hb_set_mode(self.h, int(mode)), "g6hb_set_mode")
+
+    def stats(self):
+        v = [C.c_longlong(0) for _ in range(3)] + [C.c_double(0), C.c_double(0)]
+        _check(lib().g6hb_stats(self.h, *[C.byref(a) for a in v]), "g6hb_stats")
+        return dict(nsteps=v[0].value, nactive=v[1].value, interactions=v[2].value,
+                    sec_gpu=v[3].value, sec_host=v[4].value)
+
+    def state(self):
+        tot = int(self.off[-1])
+        x, v, t = np.empty((tot, 3)), np.empty((tot, 3)), np.empty(tot)
+        _check(lib().g6hb_get_state(self.h, _p(x), _p(v), _p(t)), "g6hb_get_state")
+        return dict(x=x, v=v, t=t)
+
+    def close(self):
+        if self.h:
+            lib().g6hb_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,6 +1,7 @@
 """CPU checks of the C ABI: the library builds, loads, exports every symbol
 include/g6gb.h declares, and fails cleanly (no crash, an error code) where no
 GPU exists.  No compute call runs here."""
+import ctypes
 import os
 import re
 
@@ -73,6 +74,25 @@ def test_strerror_and_argument_errors_without_gpu(lib):
 def test_open_without_gpu_reports_enodev(lib):
     assert lib.g6_open(0) == g6gb.G6_ENODEV
     assert lib.g6x_open_ex(1, 1024, 256) == g6gb.G6_ENODEV
+    err = ctypes.c_int(0)
+    nj = (ctypes.c_int * 2)(300, 17)
+    assert not lib.g6x_batch_create(2, nj, 0, 0, 0, ctypes.byref(err))
+    assert err.value == g6gb.G6_ENODEV
+
+
+def test_batch_argument_checks_need_no_gpu(lib):
+    err = ctypes.c_int(0)
+    nj = (ctypes.c_int * 2)(300, 17)
+    assert not lib.g6x_batch_create(0, nj, 0, 0, 0, ctypes.byref(err))
+    assert err.value == g6gb.G6_EINVAL
+    assert not lib.g6x_batch_create(2, nj, 1, 0, 0, ctypes.byref(err))   # FP64: not batched
+    assert err.value == g6gb.G6_EINVAL
+    assert not lib.g6x_batch_create(2, nj, 0, 99, 0, ctypes.byref(err))
+    assert err.value == g6gb.G6_EINVAL
+    assert lib.g6x_batch_calc(None, None, None, None, 0) == g6gb.G6_EINVAL
+    assert lib.g6x_batch_destroy(None) == g6gb.G6_EINVAL
+    assert lib.g6hb_step(None, 1.0) == g6gb.G6_EINVAL
+    assert lib.g6x_batch_launch_count(None) == 0
 
 
 def test_binding_refuses_missing_library(tmp_path, monkeypatch):

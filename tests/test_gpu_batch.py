@@ -1,0 +1,176 @@
+"""GPU parity of the batch path: many independent clusters of uneven size and
+uneven active sets computed by one launch sequence (one graph replay, plain
+launches, or one launch sequence per cluster), against the FP64 oracle run
+cluster by cluster on the same seeded inputs.
+
+Tolerances are those of the single-context FP32 + double-single path:
+median relative force error <= 1e-6, max <= 1e-5 (jerk max 1e-4)."""
+import numpy as np
+import pytest
+
+from paper_0902_4463_gb300 import g6gb as g6
+from paper_0902_4463_gb300 import ics
+from tests.gpu_helpers import check_nn, rel_err_vec
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [1, 2, 255, 256, 257, 1000, 2048, 3001]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_0902_4463_gb300 import build
+    build.build()
+
+
+def _clusters(seed, sizes):
+    out = []
+    for k, n in enumerate(sizes):
+        st = ics.taylor_state(n, seed * 31 + k, 0.5)
+        st["idx"] = np.arange(n)
+        out.append(st)
+    return out
+
+
+def _stage(b, k, st, q=None):
+    q = np.arange(len(st["m"])) if q is None else q
+    b.set_j(k, st["m"][q], st["x0"][q], st["v0"][q], st["a0"][q] / 2.0, st["j0"][q] / 6.0,
+            st["tj"][q], addr=q)
+
+
+def _active(orc, st, t_blk, ni, seed):
+    """First ni particles of a seeded permutation, at their predicted state."""
+    xp, vp = orc.predict(st["x0"], st["v0"], st["a0"], st["j0"], st["tj"], t_blk)
+    sel = np.sort(ics.permutation(len(st["m"]), seed)[:ni])
+    return xp, vp, sel
+
+
+def _check_cluster(orc, st, t_blk, eps2, sel, res):
+    xp, vp = orc.predict(st["x0"], st["v0"], st["a0"], st["j0"], st["tj"], t_blk)
+    oa, oj, op, onn, onr = orc.force(xp[sel], vp[sel], sel, xp, vp, st["m"], st["idx"], eps2)
+    if len(st["m"]) == 1:
+        assert np.all(res["acc"] == 0) and np.all(res["pot"] == 0) and res["nnb"][0] == -1
+        return
+    ea, ej = rel_err_vec(res["acc"], oa), rel_err_vec(res["jerk"], oj)
+    ep = np.abs(res["pot"] - op) / np.abs(op)
+    assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5, (np.median(ea), ea.max())
+    assert np.median(ej) <= 1e-6 and ej.max() <= 1e-4, (np.median(ej), ej.max())
+    assert np.median(ep) <= 1e-6 and ep.max() <= 1e-5
+    assert check_nn(onn, onr, res["nnb"], xp[sel], xp, st["idx"]) > 0.98
+
+
+def _run_steps(orc, variant, mode, seed=3):
+    cl = _clusters(seed, SIZES)
+    ncl = len(cl)
+    b = g6.G6Batch([len(c["m"]) for c in cl], variant=variant)
+    try:
+        for k, st in enumerate(cl):
+            _stage(b, k, st)
+        rng = np.random.default_rng(seed)
+        eps2 = 10.0 ** rng.uniform(-6, -3, ncl)
+        outs = []
+        for step in range(2):
+            t_blk = 0.5 + 0.125 * step * np.arange(1, ncl + 1) / ncl
+            ni = [len(c["m"]) if (k + step) % 3 == 0 else
+                  (0 if (k + step) % 3 == 1 else max(1, len(c["m"]) // 5))
+                  for k, c in enumerate(cl)]
+            sels = []
+            for k, st in enumerate(cl):
+                xp, vp, sel = _active(orc, st, t_blk[k], ni[k], seed + 7 * step + k)
+                b.set_i(k, xp[sel], vp[sel], sel)
+                sels.append(sel)
+            b.calc(t_blk, eps2, ni, mode)
+            res = [b.results(k, ni[k]) for k in range(ncl)]
+            for k, st in enumerate(cl):
+                if ni[k]:
+                    _check_cluster(orc, st, t_blk[k], eps2[k], sels[k], res[k])
+            outs.append(res)
+            # between steps: move a few particles of every cluster (new Taylor
+            # data at a new time), as a block step's corrector would
+            for k, st in enumerate(cl):
+                n = len(st["m"])
+                q = np.unique(rng.integers(0, n, size=max(1, n // 7)))
+                st["x0"][q] += rng.normal(size=(len(q), 3)) * 1e-3
+                st["v0"][q] *= 1.01
+                st["tj"][q] = t_blk[k]
+                _stage(b, k, st, q)
+        return outs, b.launch_count()
+    finally:
+        b.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+def test_batch_graph_matches_oracle(orc, variant):
+    _run_steps(orc, variant, 0)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_batch_modes_match_oracle(orc, mode):
+    _run_steps(orc, 1, mode)
+
+
+def test_graph_and_plain_launches_are_identical(orc):
+    g, ng = _run_steps(orc, 2, 0)
+    p, npl = _run_steps(orc, 2, 1)
+    assert ng == npl == 6
+    for rg, rp in zip(g, p):
+        for a, c in zip(rg, rp):
+            assert np.array_equal(a, c)
+
+
+def test_per_cluster_launch_count(orc):
+    _, n = _run_steps(orc, 1, 2)
+    # 3 launches per active cluster per step (+ store launches of idle ones)
+    assert n >= 3 * 5
+
+
+def test_batch_errors():
+    with pytest.raises(g6.G6Error):
+        g6.G6Batch([])
+    with pytest.raises(g6.G6Error):
+        g6.G6Batch([10, 0])
+    with pytest.raises(g6.G6Error):
+        g6.G6Batch([10], variant=99)
+    b = g6.G6Batch([10, 20])
+    try:
+        with pytest.raises(g6.G6Error):
+            b.calc([0.0, 0.0], [1e-4, 1e-4], [11, 0])      # ni > nj
+        with pytest.raises(g6.G6Error):
+            b.calc([0.0, 0.0], [-1.0, 1e-4], [1, 0])       # eps2 < 0
+        with pytest.raises(g6.G6Error):
+            b.calc([0.0, 0.0], [1e-4, 1e-4], [1, 1], mode=3)
+        assert g6.lib().g6x_batch_irecs(b.h, 2) is None
+        z = np.zeros(3)
+        assert g6.lib().g6x_batch_set_j(b.h, 0, 10, 0, 0.0, 1.0, g6._p(z), g6._p(z),
+                                        g6._p(z), g6._p(z)) == g6.G6_EINVAL
+        # all idle: nothing to compute, still a valid call
+        assert b.calc([0.0, 0.0], [1e-4, 1e-4], [0, 0]) == 0
+    finally:
+        b.close()
+
+
+def test_batch_hermite_drift_vs_oracle(orc):
+    # Four clusters of the batch workload's kind (Salpeter masses, Plummer,
+    # eps2 = (4/N)^2), integrated to t = 0.25 with eta = 0.01: per cluster the
+    # energy drift stays within 2x the oracle's own Hermite integration (plus
+    # 1e-10 absolute for drifts at the rounding level).
+    cls = ics.cluster_batch(4, 11, nmin=256, nmax=1024)
+    sim = g6.G6HBatchSim([(c["m"], c["x"], c["v"]) for c in cls],
+                         [c["eps2"] for c in cls], 0.01)
+    try:
+        sim.run(0.25)
+        st = sim.state()
+        stats = sim.stats()
+    finally:
+        sim.close()
+    assert np.all(st["t"] == 0.25)
+    assert stats["nsteps"] > 0 and stats["interactions"] > 0
+    for k, c in enumerate(cls):
+        lo, hi = sim.off[k], sim.off[k + 1]
+        e0 = orc.energy(c["m"], c["x"], c["v"], c["eps2"])
+        e1 = orc.energy(c["m"], st["x"][lo:hi], st["v"][lo:hi], c["eps2"])
+        ref = orc.hermite_run(c["m"], c["x"], c["v"], c["eps2"], 0.01, 0.25)
+        assert ref["err"] == 0
+        e1o = orc.energy(c["m"], ref["x"], ref["v"], c["eps2"])
+        d_gpu, d_orc = abs((e1 - e0) / e0), abs((e1o - e0) / e0)
+        assert d_gpu <= 2 * d_orc + 1e-10, (k, d_gpu, d_orc)
