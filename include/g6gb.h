@@ -376,21 +376,56 @@ void g6h_destroy(g6h_sim *s);
  * partial-sum reduction.  Cluster k's particle q lives at j-address q
  * (0 <= q < nj[k]); particle indices, self-exclusion and nearest neighbours
  * are per cluster.  Neighbour lists are not available on batches.
- * Threading: a batch is used from one host thread at a time. */
+ * Threading: g6x_batch_set_j / _set_j_many calls for different clusters may
+ * run concurrently; every other call on a batch takes it alone.  The batch
+ * keeps a pool of host threads (G6GB_HOST_THREADS, default min(cores, 16))
+ * for its per-cluster host work. */
 
 typedef struct g6x_batch g6x_batch;
 
 /* Create a batch of ncl clusters with nj[k] >= 1 j-particles each.
  * precision: G6X_PREC_DS or G6X_PREC_DS_X64.  variant: batch force kernel
- * (0 .. 4: 16x16x1, 16x16x2, 32x8x2, 64x4x2, 128x1x2 threads along i x
- * threads along j x i-particles per thread; -1 = 0).  grid_mul: CTAs =
- * SMs x resident CTAs per SM x grid_mul (0 = 1).  Device memory comes from
+ * (0 .. 5: 16x16x1, 16x16x2, 32x8x2, 64x4x2, 128x1x2, 8x32x1 threads along
+ * i x threads along j x i-particles per thread; the i-tile is the product
+ * of the first and last) for a one-class schedule, or -1 for the default
+ * two-class schedule (kernel 0 for active sets of up to 32, kernel 3
+ * above).  grid_mul: CTAs = SMs x resident CTAs per SM x grid_mul (0 = 1
+ * for a given variant, 2 for the wide kernel of the default schedule;
+ * at most 16).  Device memory comes from
  * the allocator set with g6x_set_allocator; i-records, results and the
  * per-step tables are in mapped pinned host memory.  Returns NULL on error
  * (*err = G6_EINVAL, G6_ENOMEM, G6_ENODEV or G6_EIO). */
 g6x_batch *g6x_batch_create(int ncl, const int nj[], int precision, int variant,
                             int grid_mul, int *err);
 int g6x_batch_destroy(g6x_batch *b);
+
+/* Schedule: clusters whose active set has at most `threshold` particles
+ * are computed by force kernel small_variant, the others by large_variant
+ * (both as for g6x_batch_create), each over its own work line with its own
+ * grid multiplier (1 .. 16); the two kernels run concurrently.
+ * large_variant = -1: one class, small_variant for every cluster (threshold
+ * ignored).  Waits for the batch's work, reallocates the partial-sum
+ * buffers and re-captures the graph at the next call.  Returns 0,
+ * G6_EINVAL or G6_ENOMEM. */
+int g6x_batch_set_schedule(g6x_batch *b, int small_variant, int small_grid_mul,
+                           int threshold, int large_variant, int large_grid_mul);
+
+/* Current schedule: {small_variant, small_grid_mul, threshold,
+ * large_variant, large_grid_mul} (threshold 0 and large_variant -1 for a
+ * one-class schedule). */
+int g6x_batch_get_schedule(const g6x_batch *b, int sched[5]);
+
+/* Schedule autotuner: times every one-class schedule (each kernel, grid
+ * multiplier 1 and 2) and the two-class schedules (narrow kernel x wide
+ * kernel x thresholds 8 .. 128) on npat active-set patterns ni[npat][ncl]
+ * (graph mode, reps passes, at block times t_blk[ncl] with softenings
+ * eps2[ncl]) and keeps the fastest.  The calls compute on the batch's
+ * current j-memory and i-records and overwrite its results; staged records
+ * are applied by the first call.  sched (may be NULL) receives the chosen
+ * schedule as g6x_batch_get_schedule, best_ms (may be NULL) its mean
+ * milliseconds per call.  Returns 0 or an error. */
+int g6x_batch_autotune(g6x_batch *b, int npat, const int ni[], const double eps2[],
+                       const double t_blk[], int reps, int sched[5], double *best_ms);
 
 /* Host pointer to cluster cl's i-record array (nj[cl] records, mapped
  * memory written by the caller before g6x_batch_calc; index = the
@@ -428,7 +463,15 @@ int g6x_batch_set_j_many(g6x_batch *b, int cl, int n, const int address[],
 int g6x_batch_calc(g6x_batch *b, const double t_blk[], const double eps2[],
                    const int ni[], int mode);
 
-/* Kernels launched by the batch (a graph replay counts its three). */
+/* CUDA-event timing of every batch calculation (enable = 1 resets the
+ * totals): the GPU time of the launch sequence, from before the table copy
+ * to after the last kernel, summed over calls. */
+int g6x_batch_set_timing(g6x_batch *b, int enable);
+int g6x_batch_get_timing(const g6x_batch *b, double *gpu_ms, long long *calls);
+
+/* Kernels and copies launched by the batch: a graph replay counts one table
+ * copy and three (one class) or five (two classes) kernels as 1 + 2 x
+ * classes; a per-cluster sequence counts three per active cluster. */
 long long g6x_batch_launch_count(const g6x_batch *b);
 
 /* Hermite driver over a batch: every cluster runs the block-time-step
@@ -454,8 +497,21 @@ int g6hb_step(g6hb_sim *s, double t_end);
 /* Steps until every cluster reaches t_end (a multiple of dt_max). */
 int g6hb_run(g6hb_sim *s, double t_end);
 
+/* The driver's batch (for g6x_batch_set_timing and the like); NULL for a
+ * NULL driver. */
+g6x_batch *g6hb_batch(g6hb_sim *s);
+
 /* Change the launch mode (0, 1, 2 as for g6x_batch_calc). */
 int g6hb_set_mode(g6hb_sim *s, int mode);
+
+/* Tune the batch schedule (g6x_batch_autotune) on the active-set patterns
+ * of the driver's last (up to 64) batch steps.  Returns G6_EBUSY before the
+ * first step. */
+int g6hb_autotune(g6hb_sim *s, int reps, int sched[5], double *best_ms);
+
+/* Set the batch schedule (as g6x_batch_set_schedule). */
+int g6hb_set_schedule(g6hb_sim *s, int small_variant, int small_grid_mul,
+                      int threshold, int large_variant, int large_grid_mul);
 
 /* Counters: batch steps, sum of active particles, sum over steps and
  * clusters of ni x nj, seconds in g6x_batch_calc and on the host. */

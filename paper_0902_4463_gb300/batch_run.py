@@ -8,14 +8,15 @@ Two measurements, both printed as one JSON line:
 * force-only batch calls (Sect. 2: one force call per block step, here for
   every cluster at once) on seeded uneven active sets: per cluster
   ni = max(1, N >> u), u uniform in 0 .. floor(log2 N), a fifth of the
-  clusters idle per call.  Timed end to end per call (host staging, launch,
-  wait, results in mapped memory) for every batch kernel shape x grid
-  multiplier in one CUDA-graph replay (the schedule tuning: the best is
-  kept), then with that schedule as plain launches and as one launch
-  sequence per cluster;
+  clusters idle per call.  The native schedule autotuner picks the
+  schedule on these patterns; then each call is timed end to end (host
+  staging, launch, wait, results in mapped memory) as one CUDA-graph
+  replay, as plain launches and as one launch sequence per cluster, and
+  every one-class schedule is timed for comparison;
 * the Hermite batch driver (every cluster its own block scheduler, one batch
-  force call per batch step) to t_end with the tuned schedule, graph mode
-  against per-cluster launches.
+  force call per batch step) to t_end: the default schedule, then the
+  schedule its autotuner picks from the active sets of its first 64 batch
+  steps, in graph mode and with per-cluster launches.
 
 Interactions count ni x N per cluster and call; Gflop/s uses 60 flops per
 interaction (Sect. 3.1).
@@ -50,85 +51,121 @@ def _patterns(cls, seed, count):
     return out
 
 
-def _make_batch(cls, variant, grid_mul):
-    b = g6.G6Batch([c["n"] for c in cls], variant=variant, grid_mul=grid_mul)
+def _make_batch(cls, sched=None):
+    b = g6.G6Batch([c["n"] for c in cls])
+    if sched is not None:
+        b.set_schedule(*sched)
     for k, c in enumerate(cls):
         b.set_j(k, c["m"], c["x"], c["v"])
         b.set_i(k, c["x"], c["v"])
     return b
 
 
-def force_calls(cls, variant, grid_mul, mode, patterns, reps):
+def _eps2_t(cls):
+    return np.array([c["eps2"] for c in cls]), np.zeros(len(cls))
+
+
+def force_calls(cls, sched, mode, patterns, reps):
     """Mean seconds per batch call and interactions per call."""
-    b = _make_batch(cls, variant, grid_mul)
+    b = _make_batch(cls, sched)
     try:
-        eps2 = np.array([c["eps2"] for c in cls])
+        eps2, t = _eps2_t(cls)
         n = np.array([c["n"] for c in cls])
-        t = np.zeros(len(cls))
         b.calc(t, eps2, n, mode)                 # staging, graph capture, warm-up
         for p in patterns:
             b.calc(t, eps2, p, mode)
+        l0 = b.launch_count()
         t0 = time.perf_counter()
         for _ in range(reps):
             for p in patterns:
                 b.calc(t, eps2, p, mode)
         sec = (time.perf_counter() - t0) / (reps * len(patterns))
+        launches = (b.launch_count() - l0) / (reps * len(patterns))
         inter = float(np.mean([np.dot(p.astype(np.float64), n) for p in patterns]))
-        return sec, inter, b.launch_count()
+        return sec, inter, launches
     finally:
         b.close()
 
 
-def driver(cls, variant, grid_mul, mode, t_end, eta):
-    sim = g6.G6HBatchSim([(c["m"], c["x"], c["v"]) for c in cls],
-                         [c["eps2"] for c in cls], eta, variant=variant,
-                         grid_mul=grid_mul, mode=mode)
+def tune_on(cls, patterns, reps):
+    """Native schedule autotuner on the given active-set patterns."""
+    b = _make_batch(cls)
     try:
+        eps2, t = _eps2_t(cls)
+        return b.autotune(np.stack(patterns), eps2, t, reps)
+    finally:
+        b.close()
+
+
+def driver_patterns(cls, eta, steps):
+    """Active-set patterns of the driver's first batch steps, and the
+    schedule its own autotuner picks from them."""
+    sim = g6.G6HBatchSim([(c["m"], c["x"], c["v"]) for c in cls],
+                         [c["eps2"] for c in cls], eta)
+    try:
+        for _ in range(steps):
+            if sim.step(1.0) == 0:
+                break
+        return sim.autotune(2)
+    finally:
+        sim.close()
+
+
+def driver(cls, sched, mode, t_end, eta):
+    sim = g6.G6HBatchSim([(c["m"], c["x"], c["v"]) for c in cls],
+                         [c["eps2"] for c in cls], eta, mode=mode)
+    try:
+        if sched is not None:
+            sim.set_schedule(sched)
+        sim.set_timing(True)
         t0 = time.perf_counter()
         sim.run(t_end)
         wall = time.perf_counter() - t0
         st = sim.stats()
+        gpu_ms, ncalls = sim.timing()
         ok = bool(np.all(sim.state()["t"] == t_end))
     finally:
         sim.close()
-    return dict(mode=mode, wall_s=wall, batch_steps=st["nsteps"], nactive=st["nactive"],
-                interactions=st["interactions"], sec_gpu=st["sec_gpu"],
-                sec_host=st["sec_host"], interactions_per_s=st["interactions"] / wall,
+    return dict(mode=mode, schedule=sched, wall_s=wall, batch_steps=st["nsteps"],
+                nactive=st["nactive"], interactions=st["interactions"],
+                sec_gpu=st["sec_gpu"], sec_host=st["sec_host"],
+                gpu_event_s=gpu_ms / 1e3, gpu_event_us_per_call=1e3 * gpu_ms / max(1, ncalls),
+                interactions_per_s=st["interactions"] / wall,
                 gflops_60=FLOPS * st["interactions"] / wall / 1e9,
-                us_per_batch_step=1e6 * wall / max(1, st["nsteps"]), synchronised=ok)
+                us_per_batch_step=1e6 * wall / max(1, st["nsteps"]),
+                mean_active_per_cluster_step=st["nactive"] / max(1, st["nsteps"]) / len(cls),
+                synchronised=ok)
 
 
-def run(ncl=256, seed=1, t_end=0.0625, eta=0.01, npat=16, reps=3, variants=None,
-        grid_muls=(1, 2), skip_driver=False):
+def run(ncl=256, seed=1, t_end=0.0625, eta=0.01, npat=16, reps=3, skip_driver=False):
     _build.build()
     cls = ics.cluster_batch(ncl, seed)
     pats = _patterns(cls, seed + 1, npat)
-    variants = list(range(5)) if variants is None else variants
-    sweep = []
-    for v in variants:
-        for gm in grid_muls:
-            sec, inter, _ = force_calls(cls, v, gm, 0, pats, reps)
-            sweep.append(dict(variant=v, grid_mul=gm, ms_per_call=1e3 * sec,
-                              interactions_per_s=inter / sec))
-    best = min(sweep, key=lambda r: r["ms_per_call"])
-    v, gm = best["variant"], best["grid_mul"]
+    sched, ms = tune_on(cls, pats, reps)
     modes = {}
     for mode, name in ((0, "graph"), (1, "plain"), (2, "per_cluster")):
-        sec, inter, launches = force_calls(cls, v, gm, mode, pats, reps)
+        sec, inter, launches = force_calls(cls, sched, mode, pats, reps)
         modes[name] = dict(ms_per_call=1e3 * sec, interactions_per_s=inter / sec,
-                           gflops_60=FLOPS * inter / sec / 1e9,
-                           launches_per_call=launches / (1 + (reps + 1) * len(pats)))
+                           gflops_60=FLOPS * inter / sec / 1e9, launches_per_call=launches)
+    one = {}
+    for v in range(6):
+        sec, inter, _ = force_calls(cls, (v, 2, 0, -1, 1), 0, pats, reps)
+        one[v] = 1e3 * sec
     out = dict(workload="batch of %d Plummer clusters, N log-uniform [256, 16384], Salpeter, "
                "eps2=(4/N)^2, seed %d" % (ncl, seed),
                sum_n=int(sum(c["n"] for c in cls)), patterns=npat,
-               tune_sweep=sweep, tuned=dict(variant=v, grid_mul=gm), force_calls=modes,
+               tuned_schedule=sched, tuned_ms=ms, one_class_ms_gm2=one, force_calls=modes,
                speedup_graph_vs_per_cluster=modes["per_cluster"]["ms_per_call"]
                / modes["graph"]["ms_per_call"])
     if not skip_driver:
-        out["driver"] = [driver(cls, v, gm, mode, t_end, eta) for mode in (0, 2)]
+        dsched, dms = driver_patterns(cls, eta, 64)
+        out["driver_tuned_schedule"] = dsched
+        out["driver_tuned_ms"] = dms
+        out["driver"] = [driver(cls, None, 0, t_end, eta), driver(cls, dsched, 0, t_end, eta),
+                         driver(cls, dsched, 2, t_end, eta)]
         out["driver_t_end"] = t_end
-        out["driver_speedup_graph_vs_per_cluster"] = (out["driver"][1]["wall_s"]
-                                                      / out["driver"][0]["wall_s"])
+        out["driver_speedup_graph_vs_per_cluster"] = (out["driver"][2]["wall_s"]
+                                                      / out["driver"][1]["wall_s"])
     return out
 
 

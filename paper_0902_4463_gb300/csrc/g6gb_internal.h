@@ -100,14 +100,20 @@ struct VariantInfo {
 // Work geometry of a batch of independent clusters: cluster k holds j-tiles
 // [cl_jtile[k], cl_jtile[k] + its tile count) and i-records
 // [cl_ioff[k], cl_ioff[k] + cl_ni[k]); its active i-particles form
-// ceil(cl_ni[k] / i-tile) i-tiles, and global i-tile g covers work positions
-// [gt_start[g], gt_start[g+1]) of the one work line cut over the CTAs.
-// hdr[0] = total work, hdr[1] = number of global i-tiles.  Kernels read all
-// of it from memory, so one captured graph serves every step.
+// ceil(cl_ni[k] / i-tile) i-tiles.  A work line lists i-tiles as entries
+// {start, cluster, i-tile of the cluster}: entry g covers work positions
+// [start_g, start_{g+1}) of the line cut over the CTAs (each position one
+// j-tile of the entry's cluster).  hdr[0] = total work W, hdr[1] = number of
+// entries n, hdr[2] = index of the line's first entry in gt; entry n (the
+// sentinel) has start = W.  Kernels read all of it from device memory, so
+// one captured graph serves every step.
+struct BatchGT {
+    long long start;
+    int cluster, itile;
+};
 struct BatchTables {
     const long long *hdr;
-    const long long *gt_start;
-    const int *gt_cluster, *gt_itile;
+    const BatchGT *gt;
     const int *cl_jtile, *cl_ioff, *cl_ni;
     const double *cl_eps2;
 };

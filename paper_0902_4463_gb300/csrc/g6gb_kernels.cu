@@ -505,22 +505,27 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     // Work geometry: global i-tile g of a work position, its work range, its
     // j-tile for a position, and where its i-records and results live.
     long long W;
-    if constexpr (BATCH)
-        W = *(volatile const long long *)a.bt.hdr;
-    else
+    int ngt = 0;
+    const BatchGT *gt = nullptr;
+    if constexpr (BATCH) {
+        W = a.bt.hdr[0];
+        ngt = (int)a.bt.hdr[1];
+        gt = a.bt.gt + a.bt.hdr[2];
+    } else {
         W = a.W;
+    }
     auto g_start = [&](int g) -> long long {
         if constexpr (BATCH)
-            return a.bt.gt_start[g];
+            return gt[g].start;
         else
             return (long long)g * a.J;
     };
     auto g_of = [&](long long p) -> int {       // largest g with g_start(g) <= p
         if constexpr (BATCH) {
-            int lo = 0, hi = (int)*(volatile const long long *)(a.bt.hdr + 1) - 1;
+            int lo = 0, hi = ngt - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (a.bt.gt_start[mid] <= p)
+                if (gt[mid].start <= p)
                     lo = mid;
                 else
                     hi = mid - 1;
@@ -532,15 +537,15 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     };
     auto jt_of = [&](long long p, int g) -> int {
         if constexpr (BATCH)
-            return a.bt.cl_jtile[a.bt.gt_cluster[g]] + (int)(p - a.bt.gt_start[g]);
+            return a.bt.cl_jtile[gt[g].cluster] + (int)(p - gt[g].start);
         else
             return (int)(p - (long long)g * a.J);
     };
     // record index of slot il of i-tile g, or -1 past the active block
     auto i_index = [&](int g, int il) -> long long {
         if constexpr (BATCH) {
-            const int k = a.bt.gt_cluster[g];
-            const int li = a.bt.gt_itile[g] * ITILE + il;
+            const int k = gt[g].cluster;
+            const int li = gt[g].itile * ITILE + il;
             return li < a.bt.cl_ni[k] ? (long long)a.bt.cl_ioff[k] + li : -1;
         } else {
             const long long gi = (long long)g * ITILE + il;
@@ -611,7 +616,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     // other groups through shared memory.
     auto load_i = [&](int t) {
         if constexpr (BATCH) {
-            const float e = (float)a.bt.cl_eps2[a.bt.gt_cluster[t]];
+            const float e = (float)a.bt.cl_eps2[gt[t].cluster];
             eps2 = make_float2(e, e);
         }
         if constexpr (TJ > 1) {
@@ -1367,19 +1372,20 @@ template <class PT>
 __global__ void __launch_bounds__(256) k_reduce_batch(const ReduceArgs a, BatchTables bt)
 {
     const int lane = threadIdx.x & 31;
-    const long long W = *(volatile const long long *)bt.hdr;
-    const long long ngt = *(volatile const long long *)(bt.hdr + 1);
+    const long long W = bt.hdr[0];
+    const long long ngt = bt.hdr[1];
+    const BatchGT *gt = bt.gt + bt.hdr[2];
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const PT *part = reinterpret_cast<const PT *>(a.part);
     for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
          w < ngt * a.itile; w += nwarps) {
         const int g = (int)(w / a.itile), il = (int)(w % a.itile);
-        const int k = bt.gt_cluster[g];
-        const int li = bt.gt_itile[g] * a.itile + il;
+        const int k = gt[g].cluster;
+        const int li = gt[g].itile * a.itile + il;
         if (li >= bt.cl_ni[k])
             continue;                                  // uniform within the warp
-        const long long clo = work_owner(bt.gt_start[g], W, a.G);
-        const long long chi = work_owner(bt.gt_start[g + 1] - 1, W, a.G);
+        const long long clo = work_owner(gt[g].start, W, a.G);
+        const long long chi = work_owner(gt[g + 1].start - 1, W, a.G);
         PartialSum<PT> acc;
         acc.init();
 #pragma unroll 4
@@ -1443,6 +1449,7 @@ const Variant kBatchVariants[] = {
     {{32, 8, 2, 0, G6X_PREC_DS}, k_force_ds<32, 8, 2, false, 2, 2, true>, 256, ds_smem(256, 2)},
     {{64, 4, 2, 0, G6X_PREC_DS}, k_force_ds<64, 4, 2, false, 2, 2, true>, 256, ds_smem(256, 2)},
     {{128, 1, 2, 0, G6X_PREC_DS}, k_force_ds<128, 1, 2, false, 3, 2, true>, 128, ds_smem(128, 2)},
+    {{8, 32, 1, 0, G6X_PREC_DS}, k_force_ds<8, 32, 1, false, 1, 2, true>, 256, ds_smem(256, 1)},
 };
 constexpr int kNumBatchVariants = (int)(sizeof(kBatchVariants) / sizeof(kBatchVariants[0]));
 int g_bocc[kNumBatchVariants];

@@ -53,6 +53,8 @@ EXPORTS = [
     "g6h_stats", "g6h_profile", "g6h_destroy",
     "g6x_batch_create", "g6x_batch_destroy", "g6x_batch_irecs", "g6x_batch_results",
     "g6x_batch_set_j", "g6x_batch_set_j_many", "g6x_batch_calc", "g6x_batch_launch_count",
+    "g6x_batch_set_schedule", "g6x_batch_get_schedule", "g6x_batch_autotune", "g6hb_autotune",
+    "g6hb_set_schedule", "g6x_batch_set_timing", "g6x_batch_get_timing", "g6hb_batch",
     "g6hb_create", "g6hb_step", "g6hb_run", "g6hb_set_mode", "g6hb_stats", "g6hb_get_state",
     "g6hb_destroy",
 ]
@@ -120,6 +122,14 @@ def lib():
             "g6x_batch_set_j_many": (I, [P, I, I, P, P, P, P, P, P, P, P]),
             "g6x_batch_calc": (I, [P, P, P, P, I]),
             "g6x_batch_launch_count": (C.c_longlong, [P]),
+            "g6x_batch_set_schedule": (I, [P, I, I, I, I, I]),
+            "g6x_batch_get_schedule": (I, [P, P]),
+            "g6x_batch_autotune": (I, [P, I, P, P, P, I, P, P]),
+            "g6hb_autotune": (I, [P, I, P, P]),
+            "g6hb_set_schedule": (I, [P, I, I, I, I, I]),
+            "g6x_batch_set_timing": (I, [P, I]),
+            "g6x_batch_get_timing": (I, [P, P, P]),
+            "g6hb_batch": (P, [P]),
             "g6hb_create": (P, [I, P, P, P, P, P, D, D, D, D, I, I, I, P]),
             "g6hb_step": (I, [P, D]),
             "g6hb_run": (I, [P, D]),
@@ -511,6 +521,37 @@ class G6Batch:
     def launch_count(self):
         return lib().g6x_batch_launch_count(self.h)
 
+    def set_timing(self, on=True):
+        return _check(lib().g6x_batch_set_timing(self.h, int(on)), "g6x_batch_set_timing")
+
+    def timing(self):
+        ms, n = C.c_double(0), C.c_longlong(0)
+        _check(lib().g6x_batch_get_timing(self.h, C.byref(ms), C.byref(n)),
+               "g6x_batch_get_timing")
+        return ms.value, n.value
+
+    def set_schedule(self, small_variant, small_grid_mul=1, threshold=0, large_variant=-1,
+                     large_grid_mul=1):
+        return _check(lib().g6x_batch_set_schedule(self.h, small_variant, small_grid_mul,
+                                                   threshold, large_variant, large_grid_mul),
+                      "g6x_batch_set_schedule")
+
+    def schedule(self):
+        s = np.zeros(5, dtype=np.int32)
+        _check(lib().g6x_batch_get_schedule(self.h, _p(s)), "g6x_batch_get_schedule")
+        return tuple(int(v) for v in s)
+
+    def autotune(self, patterns, eps2, t_blk, reps=2):
+        """Tune the schedule on active-set patterns [npat][ncl]; returns
+        (schedule, mean ms per call)."""
+        pat = _i(patterns).reshape(-1, self.ncl)
+        s = np.zeros(5, dtype=np.int32)
+        ms = C.c_double(0)
+        _check(lib().g6x_batch_autotune(self.h, pat.shape[0], _p(pat), _p(_d(eps2)),
+                                        _p(_d(t_blk)), int(reps), _p(s), C.byref(ms)),
+               "g6x_batch_autotune")
+        return tuple(int(v) for v in s), ms.value
+
     def close(self):
         if self.h:
             lib().g6x_batch_destroy(self.h)
@@ -551,6 +592,27 @@ class G6HBatchSim:
 
     def set_mode(self, mode):
         return _check(lib().g6hb_set_mode(self.h, int(mode)), "g6hb_set_mode")
+
+    def autotune(self, reps=2):
+        s = np.zeros(5, dtype=np.int32)
+        ms = C.c_double(0)
+        _check(lib().g6hb_autotune(self.h, int(reps), _p(s), C.byref(ms)), "g6hb_autotune")
+        return tuple(int(v) for v in s), ms.value
+
+    def set_schedule(self, sched):
+        return _check(lib().g6hb_set_schedule(self.h, *[int(v) for v in sched]),
+                      "g6hb_set_schedule")
+
+    def set_timing(self, on=True):
+        return _check(lib().g6x_batch_set_timing(lib().g6hb_batch(self.h), int(on)),
+                      "g6x_batch_set_timing")
+
+    def timing(self):
+        """(GPU milliseconds summed over batch calls, calls) since set_timing."""
+        ms, n = C.c_double(0), C.c_longlong(0)
+        _check(lib().g6x_batch_get_timing(lib().g6hb_batch(self.h), C.byref(ms), C.byref(n)),
+               "g6x_batch_get_timing")
+        return ms.value, n.value
 
     def stats(self):
         v = [C.c_longlong(0) for _ in range(3)] + [C.c_double(0), C.c_double(0)]

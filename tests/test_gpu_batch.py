@@ -59,11 +59,13 @@ def _check_cluster(orc, st, t_blk, eps2, sel, res):
     assert check_nn(onn, onr, res["nnb"], xp[sel], xp, st["idx"]) > 0.98
 
 
-def _run_steps(orc, variant, mode, seed=3):
+def _run_steps(orc, variant, mode, seed=3, sched=None):
     cl = _clusters(seed, SIZES)
     ncl = len(cl)
     b = g6.G6Batch([len(c["m"]) for c in cl], variant=variant)
     try:
+        if sched is not None:
+            b.set_schedule(*sched)
         for k, st in enumerate(cl):
             _stage(b, k, st)
         rng = np.random.default_rng(seed)
@@ -99,7 +101,7 @@ def _run_steps(orc, variant, mode, seed=3):
         b.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_batch_graph_matches_oracle(orc, variant):
     _run_steps(orc, variant, 0)
 
@@ -116,6 +118,51 @@ def test_graph_and_plain_launches_are_identical(orc):
     for rg, rp in zip(g, p):
         for a, c in zip(rg, rp):
             assert np.array_equal(a, c)
+
+
+# two work classes: active sets up to the threshold on the narrow kernel
+@pytest.mark.parametrize("sched", [(0, 1, 64, 3, 2), (5, 1, 8, 4, 1), (1, 2, 16, 2, 1)])
+@pytest.mark.parametrize("mode", [0, 2])
+def test_two_class_schedule_matches_oracle(orc, sched, mode):
+    _run_steps(orc, -1, mode, sched=sched)
+
+
+def test_two_class_graph_and_plain_are_identical(orc):
+    sched = (0, 1, 64, 3, 2)
+    g, ng = _run_steps(orc, -1, 0, sched=sched)
+    p, npl = _run_steps(orc, -1, 1, sched=sched)
+    assert ng == npl == 10
+    for rg, rp in zip(g, p):
+        for a, c in zip(rg, rp):
+            assert np.array_equal(a, c)
+
+
+def test_autotune_keeps_a_valid_schedule(orc):
+    cl = _clusters(5, SIZES)
+    ncl = len(cl)
+    b = g6.G6Batch([len(c["m"]) for c in cl])
+    try:
+        for k, st in enumerate(cl):
+            _stage(b, k, st)
+        rng = np.random.default_rng(5)
+        eps2 = 10.0 ** rng.uniform(-6, -3, ncl)
+        t_blk = np.full(ncl, 0.5)
+        n = np.array([len(c["m"]) for c in cl])
+        pats = np.stack([np.maximum(0, n >> rng.integers(0, 10, ncl)) for _ in range(4)])
+        sels = []
+        for k, st in enumerate(cl):
+            xp, vp, sel = _active(orc, st, 0.5, len(st["m"]), 1)
+            b.set_i(k, xp[sel], vp[sel], sel)
+            sels.append(sel)
+        sched, ms = b.autotune(pats, eps2, t_blk, reps=1)
+        assert sched == b.schedule() and ms > 0
+        assert 0 <= sched[0] < 6 and (sched[3] == -1 or 0 <= sched[3] < 6)
+        # the tuned batch still computes the right forces
+        b.calc(t_blk, eps2, n, 0)
+        for k, st in enumerate(cl):
+            _check_cluster(orc, st, 0.5, eps2[k], sels[k], b.results(k, len(st["m"])))
+    finally:
+        b.close()
 
 
 def test_per_cluster_launch_count(orc):
@@ -174,3 +221,22 @@ def test_batch_hermite_drift_vs_oracle(orc):
         e1o = orc.energy(c["m"], ref["x"], ref["v"], c["eps2"])
         d_gpu, d_orc = abs((e1 - e0) / e0), abs((e1o - e0) / e0)
         assert d_gpu <= 2 * d_orc + 1e-10, (k, d_gpu, d_orc)
+
+
+def test_batch_driver_autotune_and_schedule():
+    cls = ics.cluster_batch(3, 12, nmin=256, nmax=512)
+    sim = g6.G6HBatchSim([(c["m"], c["x"], c["v"]) for c in cls],
+                         [c["eps2"] for c in cls], 0.01)
+    try:
+        with pytest.raises(g6.G6Error):
+            sim.autotune()                      # no steps recorded yet
+        for _ in range(5):
+            assert sim.step(0.125) > 0
+        sched, ms = sim.autotune(1)
+        assert ms > 0
+        sim.set_schedule(sched)
+        sim.set_mode(2)
+        sim.run(0.125)
+        assert np.all(sim.state()["t"] == 0.125)
+    finally:
+        sim.close()
