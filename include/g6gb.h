@@ -385,9 +385,9 @@ typedef struct g6x_batch g6x_batch;
 
 /* Create a batch of ncl clusters with nj[k] >= 1 j-particles each.
  * precision: G6X_PREC_DS or G6X_PREC_DS_X64.  variant: batch force kernel
- * (0 .. 5: 16x16x1, 16x16x2, 32x8x2, 64x4x2, 128x1x2, 8x32x1 threads along
- * i x threads along j x i-particles per thread; the i-tile is the product
- * of the first and last) for a one-class schedule, or -1 for the default
+ * (0 .. 7: 16x16x1, 16x16x2, 32x8x2, 64x4x2, 128x1x2, 8x32x1, 8x32x2,
+ * 4x64x2 threads along i x threads along j x i-particles per thread; the
+ * i-tile is the product of the first and last) for a one-class schedule, or -1 for the default
  * two-class schedule (kernel 0 for active sets of up to 32, kernel 3
  * above).  grid_mul: CTAs = SMs x resident CTAs per SM x grid_mul (0 = 1
  * for a given variant, 2 for the wide kernel of the default schedule;

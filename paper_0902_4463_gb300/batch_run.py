@@ -148,7 +148,7 @@ def run(ncl=256, seed=1, t_end=0.0625, eta=0.01, npat=16, reps=3, skip_driver=Fa
         modes[name] = dict(ms_per_call=1e3 * sec, interactions_per_s=inter / sec,
                            gflops_60=FLOPS * inter / sec / 1e9, launches_per_call=launches)
     one = {}
-    for v in range(6):
+    for v in range(8):
         sec, inter, _ = force_calls(cls, (v, 2, 0, -1, 1), 0, pats, reps)
         one[v] = 1e3 * sec
     out = dict(workload="batch of %d Plummer clusters, N log-uniform [256, 16384], Salpeter, "
@@ -169,6 +169,26 @@ def run(ncl=256, seed=1, t_end=0.0625, eta=0.01, npat=16, reps=3, skip_driver=Fa
     return out
 
 
+def driver_steps(ncl, seed, eta, steps, mode=0):
+    """A few batch steps of the driver with the default schedule (the
+    command that kernel profiles of the batch path run)."""
+    _build.build()
+    cls = ics.cluster_batch(ncl, seed)
+    sim = g6.G6HBatchSim([(c["m"], c["x"], c["v"]) for c in cls],
+                         [c["eps2"] for c in cls], eta, mode=mode)
+    try:
+        sim.set_timing(True)
+        for _ in range(steps):
+            if sim.step(1.0) == 0:
+                break
+        st = sim.stats()
+        gpu_ms, calls = sim.timing()
+    finally:
+        sim.close()
+    return dict(steps=st["nsteps"], nactive=st["nactive"], interactions=st["interactions"],
+                gpu_event_us_per_call=1e3 * gpu_ms / max(1, calls))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--ncl", type=int, default=256)
@@ -178,7 +198,12 @@ def main(argv=None):
     ap.add_argument("--patterns", type=int, default=16)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--no-driver", action="store_true")
+    ap.add_argument("--driver-steps", type=int, default=0,
+                    help="only run this many driver batch steps (profiling command)")
     a = ap.parse_args(argv)
+    if a.driver_steps:
+        print(json.dumps(driver_steps(a.ncl, a.seed, a.eta, a.driver_steps)))
+        return 0
     print(json.dumps(run(a.ncl, a.seed, a.t_end, a.eta, a.patterns, a.reps,
                          skip_driver=a.no_driver)))
     return 0

@@ -1450,6 +1450,8 @@ const Variant kBatchVariants[] = {
     {{64, 4, 2, 0, G6X_PREC_DS}, k_force_ds<64, 4, 2, false, 2, 2, true>, 256, ds_smem(256, 2)},
     {{128, 1, 2, 0, G6X_PREC_DS}, k_force_ds<128, 1, 2, false, 3, 2, true>, 128, ds_smem(128, 2)},
     {{8, 32, 1, 0, G6X_PREC_DS}, k_force_ds<8, 32, 1, false, 1, 2, true>, 256, ds_smem(256, 1)},
+    {{8, 32, 2, 0, G6X_PREC_DS}, k_force_ds<8, 32, 2, false, 2, 2, true>, 256, ds_smem(256, 2)},
+    {{4, 64, 2, 0, G6X_PREC_DS}, k_force_ds<4, 64, 2, false, 2, 2, true>, 256, ds_smem(256, 2)},
 };
 constexpr int kNumBatchVariants = (int)(sizeof(kBatchVariants) / sizeof(kBatchVariants[0]));
 int g_bocc[kNumBatchVariants];

@@ -101,7 +101,7 @@ def _run_steps(orc, variant, mode, seed=3, sched=None):
         b.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
 def test_batch_graph_matches_oracle(orc, variant):
     _run_steps(orc, variant, 0)
 
@@ -121,7 +121,8 @@ def test_graph_and_plain_launches_are_identical(orc):
 
 
 # two work classes: active sets up to the threshold on the narrow kernel
-@pytest.mark.parametrize("sched", [(0, 1, 64, 3, 2), (5, 1, 8, 4, 1), (1, 2, 16, 2, 1)])
+@pytest.mark.parametrize("sched", [(0, 1, 64, 3, 2), (5, 1, 8, 4, 1), (1, 2, 16, 2, 1),
+                                   (7, 1, 8, 6, 1)])
 @pytest.mark.parametrize("mode", [0, 2])
 def test_two_class_schedule_matches_oracle(orc, sched, mode):
     _run_steps(orc, -1, mode, sched=sched)
@@ -156,7 +157,7 @@ def test_autotune_keeps_a_valid_schedule(orc):
             sels.append(sel)
         sched, ms = b.autotune(pats, eps2, t_blk, reps=1)
         assert sched == b.schedule() and ms > 0
-        assert 0 <= sched[0] < 6 and (sched[3] == -1 or 0 <= sched[3] < 6)
+        assert 0 <= sched[0] < 8 and (sched[3] == -1 or 0 <= sched[3] < 8)
         # the tuned batch still computes the right forces
         b.calc(t_blk, eps2, n, 0)
         for k, st in enumerate(cl):
