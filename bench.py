@@ -70,6 +70,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device):
+    """The largest x over all ranks (x itself when ws == 1)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank, seconds_max, ws):
+    """Whole-job throughput of ws replicas that each processed units_per_rank
+    units, timed by the slowest rank."""
+    return ws * float(units_per_rank) / seconds_max
+
+
 def workload(n, m):
     from paper_0902_4463_gb300 import ics
     st = ics.taylor_state(n, SEED, T_BLK, dt_levels=None)
@@ -337,12 +353,9 @@ def main():
     ms_step, ms_ph, cnt, launches = timed(m, d_jact, d_irec, d_out, args.steps, args.warmup,
                                           sampler)
     cfg = g6.g6x_last_config(CID)
-    if ws > 1:
-        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, ws, dev)
     pairs = float(m) * n
-    value = ws * pairs / (ms_step * 1e-3)
+    value = replica_rate(pairs, ms_step * 1e-3, ws)
     force_ms = ms_ph[2] / max(1, cnt[2])
     achieved = FLOPS_PER_PAIR * pairs / (force_ms * 1e-3) / 1e12
     clocks = sampler.summary()
@@ -442,11 +455,8 @@ def main():
             api_step()
         torch.cuda.synchronize()
         t_e2e = (time.perf_counter() - t0) / k2
-        if ws > 1:
-            t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": ws * pairs / t_e2e, "unit": "interactions/s",
+        t_e2e = max_over_ranks(t_e2e, ws, dev)
+        e2e = {"value": replica_rate(pairs, t_e2e, ws), "unit": "interactions/s",
                "h2d_bytes_per_step": int(m * (g6.JREC.itemsize + g6.IREC.itemsize)),
                "d2h_bytes_per_step": int(m * g6.OUT.itemsize + 4),
                "ms_per_step": t_e2e * 1e3,

@@ -362,7 +362,35 @@ int g6h_stats(const g6h_sim *s, long long *nblocks, long long *nactive,
 int g6h_profile(const g6h_sim *s, double *sec_sched, double *sec_force,
                 double *sec_correct);
 
+/* Neighbour lists in the driver (Sect. 4): with h2 > 0 every block step's
+ * force call also builds the active particles' lists of neighbours within
+ * unsoftened |r|^2 < h2 and reads them back (g6_read_neighbour_list /
+ * g6_get_neighbour_list); h2 = 0 turns them off (the default).  The energy
+ * sweep never builds lists.  Returns 0, G6_EINVAL or G6_ENOMEM. */
+int g6h_set_neighbour_radius(g6h_sim *s, double h2);
+
+/* Lists read back so far, their total length (entries kept, at most
+ * G6_MAXNB per list) and how many overflowed G6_MAXNB.  Any pointer may be
+ * NULL. */
+int g6h_neighbour_stats(const g6h_sim *s, long long *lists, long long *entries,
+                        long long *overflowed);
+
 void g6h_destroy(g6h_sim *s);
+
+/* Checkpoint: write the driver's whole state (particles, block scheduler in
+ * its order, counters and parameters) to `path` (written to path.tmp, then
+ * renamed over path).  Returns 0, G6_EINVAL or G6_EIO. */
+int g6h_checkpoint(const g6h_sim *s, const char *path);
+
+/* Resume: rebuild a driver from a checkpoint on cluster id `clusterid`
+ * (opened by the caller, any precision) and send every particle's state to
+ * its j-memory; no force is computed.  Continuing a restored driver with the
+ * same library settings reproduces the original run.  Returns NULL on error
+ * (*err: G6_EIO if the file cannot be read, G6_EINVAL if its content is not
+ * a consistent checkpoint (magic, sizes, parameters, scheduler times,
+ * every particle filed once, hash), G6_ENOMEM, or the error of the first
+ * failing library call). */
+g6h_sim *g6h_restore(int clusterid, const char *path, int *err);
 
 /* ------------------------------------------------ batches of clusters ----
  * Many independent star clusters in one device (Sect. 2: one library

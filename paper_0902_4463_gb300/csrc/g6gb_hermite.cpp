@@ -6,11 +6,15 @@
 // Scheme: Makino & Aarseth (1992) predictor-corrector, as named in Sect. 2;
 // time steps from the Aarseth (1985) criterion cited in Sect. 3.1-3.2,
 // quantised to powers of two (block time steps).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "g6gb.h"
@@ -32,6 +36,12 @@ struct g6h_sim {
     // block scheduler: particles keyed by their next time t + dt (block
     // times are dyadic, so equal times compare exactly)
     std::map<double, std::vector<int>> due;
+    // neighbour lists (Sect. 4): requested with radius^2 h2 on every block
+    // step when h2 > 0, read back and counted
+    double h2 = 0;
+    std::vector<double> h2v;
+    std::vector<int> nbl;
+    long long nb_lists = 0, nb_entries = 0, nb_overflowed = 0;
 };
 
 namespace {
@@ -57,15 +67,36 @@ int send_j(g6h_sim &s, int k)
 }
 
 // Force on ni i-particles (positions xi, velocities vi, ids ii) from all n
-// j-particles predicted to t_blk.
+// j-particles predicted to t_blk; with lists, also every i's neighbour list
+// (read back and counted).
 int force(g6h_sim &s, int ni, const double *xi, const double *vi, const int *ii,
-          double *acc, double *jerk, double *pot)
+          double *acc, double *jerk, double *pot, bool lists = false)
 {
+    const double *h2 = nullptr;
+    if (lists && s.h2 > 0) {
+        std::fill(s.h2v.begin(), s.h2v.begin() + ni, s.h2);
+        h2 = s.h2v.data();
+    }
     g6calc_firsthalf(s.cid, s.n, ni, ii, (const double(*)[3])xi, (const double(*)[3])vi,
-                     nullptr, nullptr, nullptr, s.eps2, nullptr);
-    return g6calc_lasthalf(s.cid, s.n, ni, ii, (const double(*)[3])xi,
-                           (const double(*)[3])vi, s.eps2, nullptr, (double(*)[3])acc,
-                           (double(*)[3])jerk, pot);
+                     nullptr, nullptr, nullptr, s.eps2, h2);
+    int rc = g6calc_lasthalf(s.cid, s.n, ni, ii, (const double(*)[3])xi,
+                             (const double(*)[3])vi, s.eps2, h2, (double(*)[3])acc,
+                             (double(*)[3])jerk, pot);
+    if (rc || !h2)
+        return rc;
+    rc = g6_read_neighbour_list(s.cid);
+    if (rc < 0)
+        return rc;
+    for (int q = 0; q < ni; ++q) {
+        int len = 0;
+        const int r = g6_get_neighbour_list(s.cid, q, G6_MAXNB, &len, s.nbl.data());
+        if (r < 0)
+            return r;
+        s.nb_entries += std::min(len, G6_MAXNB);
+        s.nb_overflowed += r == G6_EOVERFLOW;
+    }
+    s.nb_lists += ni;
+    return 0;
 }
 
 // Makino & Aarseth (1992) corrector for one particle: from the force (a0, j0)
@@ -265,7 +296,7 @@ int g6h_run(g6h_sim *s, double t_end)
         int rc = g6_set_ti(s->cid, tb);
         if (!rc)
             rc = force(*s, na, s->xp.data(), s->vp.data(), s->aidx.data(), s->a1.data(),
-                       s->j1.data(), s->pot.data());
+                       s->j1.data(), s->pot.data(), true);
         if (rc)
             return rc;
         double w2 = now_s();
@@ -389,6 +420,267 @@ int g6h_profile(const g6h_sim *s, double *sec_sched, double *sec_force, double *
     return 0;
 }
 
+int g6h_set_neighbour_radius(g6h_sim *s, double h2)
+{
+    if (!s || !(h2 >= 0) || !std::isfinite(h2))
+        return G6_EINVAL;
+    if (h2 > 0) {
+        try {
+            s->h2v.resize(s->n);
+            s->nbl.resize(G6_MAXNB);
+        } catch (...) {
+            return G6_ENOMEM;
+        }
+    }
+    s->h2 = h2;
+    return 0;
+}
+
+int g6h_neighbour_stats(const g6h_sim *s, long long *lists, long long *entries,
+                        long long *overflowed)
+{
+    if (!s)
+        return G6_EINVAL;
+    if (lists)
+        *lists = s->nb_lists;
+    if (entries)
+        *entries = s->nb_entries;
+    if (overflowed)
+        *overflowed = s->nb_overflowed;
+    return 0;
+}
+
 void g6h_destroy(g6h_sim *s) { delete s; }
+
+}  // extern "C"
+
+// ------------------------------------------------------ checkpoint/resume
+//
+// File layout (host byte order, little-endian on every supported host):
+//   char    magic[8] = "G6HCKPT1"
+//   int64   n, nbuckets, nblocks, nactive, hist[64]
+//   double  eps2, eta, eta_s, dt_max, dt_min, t_now
+//   double  m[n], x[n][3], v[n][3], a[n][3], j[n][3], t[n], dt[n]
+//   per scheduler bucket, in time order: double time, int64 count,
+//           int32 particle[count] (in the bucket's order, which fixes the
+//           order of the block's i-particles and so the force sums' grouping)
+//   uint64  FNV-1a hash of every byte above
+
+namespace {
+
+const char kMagic[8] = {'G', '6', 'H', 'C', 'K', 'P', 'T', '1'};
+
+struct Hasher {
+    uint64_t h = 1469598103934665603ull;
+    void add(const void *p, size_t n)
+    {
+        const unsigned char *c = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) {
+            h ^= c[i];
+            h *= 1099511628211ull;
+        }
+    }
+};
+
+struct Writer {
+    FILE *f;
+    Hasher hs;
+    bool ok = true;
+    void put(const void *p, size_t n)
+    {
+        if (ok && n && std::fwrite(p, 1, n, f) != n)
+            ok = false;
+        hs.add(p, n);
+    }
+};
+
+struct Reader {
+    const std::vector<unsigned char> &buf;
+    size_t pos = 0;
+    Hasher hs;
+    bool get(void *p, size_t n)
+    {
+        if (n > buf.size() - pos)
+            return false;
+        std::memcpy(p, buf.data() + pos, n);
+        hs.add(buf.data() + pos, n);
+        pos += n;
+        return true;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int g6h_checkpoint(const g6h_sim *s, const char *path)
+{
+    if (!s || !path)
+        return G6_EINVAL;
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "wb");
+    if (!f)
+        return G6_EIO;
+    Writer w{f};
+    const size_t n = (size_t)s->n;
+    const int64_t hdr[4] = {s->n, (int64_t)s->due.size(), s->nblocks, s->nactive};
+    const double par[6] = {s->eps2, s->eta, s->eta_s, s->dt_max, s->dt_min, s->t_now};
+    w.put(kMagic, sizeof kMagic);
+    w.put(hdr, sizeof hdr);
+    w.put(s->hist, sizeof s->hist);
+    w.put(par, sizeof par);
+    w.put(s->m.data(), n * sizeof(double));
+    w.put(s->x.data(), 3 * n * sizeof(double));
+    w.put(s->v.data(), 3 * n * sizeof(double));
+    w.put(s->a.data(), 3 * n * sizeof(double));
+    w.put(s->j.data(), 3 * n * sizeof(double));
+    w.put(s->t.data(), n * sizeof(double));
+    w.put(s->dt.data(), n * sizeof(double));
+    for (const auto &b : s->due) {
+        const double tb = b.first;
+        const int64_t cnt = (int64_t)b.second.size();
+        w.put(&tb, sizeof tb);
+        w.put(&cnt, sizeof cnt);
+        w.put(b.second.data(), b.second.size() * sizeof(int));
+    }
+    const uint64_t hash = w.hs.h;
+    const bool ok = w.ok && std::fwrite(&hash, sizeof hash, 1, f) == 1;
+    if (std::fclose(f) != 0 || !ok || std::rename(tmp.c_str(), path) != 0) {
+        std::remove(tmp.c_str());
+        return G6_EIO;
+    }
+    return 0;
+}
+
+g6h_sim *g6h_restore(int cid, const char *path, int *err)
+{
+    auto fail = [&](int code) -> g6h_sim * {
+        if (err)
+            *err = code;
+        return nullptr;
+    };
+    if (err)
+        *err = 0;
+    if (!path)
+        return fail(G6_EINVAL);
+    std::vector<unsigned char> buf;
+    {
+        FILE *f = std::fopen(path, "rb");
+        if (!f)
+            return fail(G6_EIO);
+        unsigned char chunk[1 << 16];
+        size_t got;
+        bool bad = false;
+        try {
+            while ((got = std::fread(chunk, 1, sizeof chunk, f)) > 0)
+                buf.insert(buf.end(), chunk, chunk + got);
+        } catch (...) {
+            bad = true;
+        }
+        const bool rerr = std::ferror(f) != 0;
+        std::fclose(f);
+        if (bad)
+            return fail(G6_ENOMEM);
+        if (rerr)
+            return fail(G6_EIO);
+    }
+    // everything below checks the content before any state is built
+    Reader r{buf};
+    char magic[8];
+    int64_t hdr[4];
+    double par[6];
+    g6h_sim *s = new (std::nothrow) g6h_sim();
+    if (!s)
+        return fail(G6_ENOMEM);
+    auto bad = [&](int code) -> g6h_sim * {
+        delete s;
+        return fail(code);
+    };
+    if (!r.get(magic, 8) || std::memcmp(magic, kMagic, 8) != 0 || !r.get(hdr, sizeof hdr)
+        || !r.get(s->hist, sizeof s->hist) || !r.get(par, sizeof par))
+        return bad(G6_EINVAL);
+    const int64_t n = hdr[0], nb = hdr[1];
+    if (n < 1 || n > (1 << 28) || nb < 0 || nb > n || hdr[2] < 0 || hdr[3] < 0)
+        return bad(G6_EINVAL);
+    // the arrays and the scheduler's entries must fit in the file
+    if ((size_t)n * (15 * sizeof(double) + sizeof(int)) > buf.size())
+        return bad(G6_EINVAL);
+    s->cid = cid;
+    s->n = (int)n;
+    s->nblocks = hdr[2];
+    s->nactive = hdr[3];
+    s->eps2 = par[0];
+    s->eta = par[1];
+    s->eta_s = par[2];
+    s->dt_max = par[3];
+    s->dt_min = par[4];
+    s->t_now = par[5];
+    if (!(s->eps2 >= 0) || !(s->eta > 0) || !(s->eta_s > 0) || !(s->dt_max > 0)
+        || !(s->dt_min > 0) || !std::isfinite(s->t_now))
+        return bad(G6_EINVAL);
+    const size_t un = (size_t)n;
+    try {
+        s->m.resize(un);
+        s->x.resize(3 * un);
+        s->v.resize(3 * un);
+        s->a.resize(3 * un);
+        s->j.resize(3 * un);
+        s->t.resize(un);
+        s->dt.resize(un);
+        s->idx.resize(un);
+        s->act.reserve(un);
+        s->aidx.resize(un);
+        s->xp.resize(3 * un);
+        s->vp.resize(3 * un);
+        s->a1.resize(3 * un);
+        s->j1.resize(3 * un);
+        s->pot.resize(un);
+    } catch (...) {
+        return bad(G6_ENOMEM);
+    }
+    if (!r.get(s->m.data(), un * sizeof(double)) || !r.get(s->x.data(), 3 * un * sizeof(double))
+        || !r.get(s->v.data(), 3 * un * sizeof(double))
+        || !r.get(s->a.data(), 3 * un * sizeof(double))
+        || !r.get(s->j.data(), 3 * un * sizeof(double))
+        || !r.get(s->t.data(), un * sizeof(double)) || !r.get(s->dt.data(), un * sizeof(double)))
+        return bad(G6_EINVAL);
+    std::vector<char> seen(un, 0);
+    int64_t filed = 0;
+    try {
+        for (int64_t b = 0; b < nb; ++b) {
+            double tb;
+            int64_t cnt;
+            if (!r.get(&tb, sizeof tb) || !r.get(&cnt, sizeof cnt) || cnt < 1 || cnt > n - filed)
+                return bad(G6_EINVAL);
+            std::vector<int> &v = s->due[tb];
+            if (!v.empty())
+                return bad(G6_EINVAL);                 // times must be distinct
+            v.resize((size_t)cnt);
+            if (!r.get(v.data(), (size_t)cnt * sizeof(int)))
+                return bad(G6_EINVAL);
+            for (int k : v) {
+                if (k < 0 || k >= n || seen[k] || !(s->dt[k] > 0) || s->t[k] + s->dt[k] != tb)
+                    return bad(G6_EINVAL);
+                seen[k] = 1;
+            }
+            filed += cnt;
+        }
+    } catch (...) {
+        return bad(G6_ENOMEM);
+    }
+    uint64_t want = r.hs.h, hash = 0;
+    if (filed != n || !r.get(&hash, sizeof hash) || hash != want || r.pos != buf.size())
+        return bad(G6_EINVAL);
+    for (int64_t k = 0; k < n; ++k)
+        s->idx[k] = (int)k;
+    // j-memory: every particle's last corrected state, as the original run
+    // left it
+    int rc = g6x_set_ni_max(cid, s->n);
+    for (int k = 0; !rc && k < s->n; ++k)
+        rc = send_j(*s, k);
+    if (rc)
+        return bad(rc);
+    return s;
+}
 
 }  // extern "C"

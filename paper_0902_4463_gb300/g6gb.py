@@ -50,7 +50,8 @@ EXPORTS = [
     "g6x_calc_dev_noalloc", "g6x_sync", "g6x_set_variant",
     "g6x_autotune", "g6x_load_tuning", "g6x_clear_tuning", "g6x_get_predicted", "g6x_last_config",
     "g6x_launch_count", "g6x_set_timing", "g6x_get_timing", "g6h_correct_block", "g6h_create", "g6h_run", "g6h_get_state", "g6h_energy",
-    "g6h_stats", "g6h_profile", "g6h_destroy",
+    "g6h_stats", "g6h_profile", "g6h_destroy", "g6h_checkpoint", "g6h_restore",
+    "g6h_set_neighbour_radius", "g6h_neighbour_stats",
     "g6x_batch_create", "g6x_batch_destroy", "g6x_batch_irecs", "g6x_batch_results",
     "g6x_batch_set_j", "g6x_batch_set_j_many", "g6x_batch_calc", "g6x_batch_launch_count",
     "g6x_batch_set_schedule", "g6x_batch_get_schedule", "g6x_batch_autotune", "g6hb_autotune",
@@ -114,6 +115,10 @@ def lib():
             "g6h_stats": (I, [P, P, P, P]),
             "g6h_profile": (I, [P, P, P, P]),
             "g6h_destroy": (None, [P]),
+            "g6h_checkpoint": (I, [P, C.c_char_p]),
+            "g6h_set_neighbour_radius": (I, [P, D]),
+            "g6h_neighbour_stats": (I, [P, P, P, P]),
+            "g6h_restore": (P, [I, C.c_char_p, P]),
             "g6x_batch_create": (P, [I, P, I, I, I, P]),
             "g6x_batch_destroy": (I, [P]),
             "g6x_batch_irecs": (P, [P, I]),
@@ -423,6 +428,31 @@ class G6HSim:
 
     def run(self, t_end):
         return _check(lib().g6h_run(self.h, float(t_end)), "g6h_run")
+
+    def set_neighbour_radius(self, h2):
+        return _check(lib().g6h_set_neighbour_radius(self.h, float(h2)),
+                      "g6h_set_neighbour_radius")
+
+    def neighbour_stats(self):
+        v = [C.c_longlong(0) for _ in range(3)]
+        _check(lib().g6h_neighbour_stats(self.h, *[C.byref(a) for a in v]),
+               "g6h_neighbour_stats")
+        return dict(lists=v[0].value, entries=v[1].value, overflowed=v[2].value)
+
+    def checkpoint(self, path):
+        return _check(lib().g6h_checkpoint(self.h, os.fsencode(path)), "g6h_checkpoint")
+
+    @classmethod
+    def restore(cls, cid, path):
+        """A driver rebuilt from a checkpoint on the opened cluster id cid."""
+        err = C.c_int(0)
+        h = lib().g6h_restore(cid, os.fsencode(path), C.byref(err))
+        if not h:
+            raise G6Error(err.value or G6_EINVAL, "g6h_restore")
+        obj = cls.__new__(cls)
+        obj.h = h
+        obj.n = int(np.fromfile(path, dtype="<i8", count=2, offset=8)[0])
+        return obj
 
     def state(self):
         n = self.n

@@ -11,7 +11,8 @@ drift measures the integration, not the energy evaluation.
 
 Prints one JSON line: wall time, block steps, sum of block sizes, mean block
 size, interactions/s and 60-flop Gflop/s over the whole run, the block-size
-histogram (log2 bins) and dE/E = (E1 - E0)/E0 (Sect. 3.2).
+histogram (log2 bins), dE/E = (E1 - E0)/E0 (Sect. 3.2) and, with --h2, the
+neighbour lists read back (Sect. 4: count, entries, overflows).
 """
 import argparse
 import json
@@ -38,7 +39,7 @@ def energy_fp64(cid, sim, mode):
 
 
 def run(n, seed, eps2, eta, t_end, prec="ds", binaries=0.0, dt_max=2.0 ** -4, cid=0,
-        tune=None):
+        tune=None, h2=0.0):
     """Integrate and return the result dict (the context is opened and closed
     here)."""
     _build.build()
@@ -53,12 +54,15 @@ def run(n, seed, eps2, eta, t_end, prec="ds", binaries=0.0, dt_max=2.0 ** -4, ci
         if tune:
             g6.g6x_load_tuning(tune)
         sim = g6.G6HSim(cid, m, x, v, eps2, eta, dt_max=dt_max)
+        if h2 > 0:
+            sim.set_neighbour_radius(h2)
         e0 = energy_fp64(cid, sim, mode)
         t0 = time.perf_counter()
         sim.run(t_end)
         wall = time.perf_counter() - t0
         st = sim.stats()
         prof = sim.profile()
+        nbs = sim.neighbour_stats()
         e1 = energy_fp64(cid, sim, mode)
         state = sim.state()
         sim.close()
@@ -71,7 +75,7 @@ def run(n, seed, eps2, eta, t_end, prec="ds", binaries=0.0, dt_max=2.0 ** -4, ci
                 nactive=int(st["nactive"]), mean_block=st["nactive"] / max(1, st["nblocks"]),
                 interactions_per_s=inter / wall, gflops_60=60.0 * inter / wall / 1e9,
                 dE_over_E=(e1 - e0) / e0, E0=e0, E1=e1, block_hist_log2=hist,
-                profile=prof,
+                profile=prof, h2=h2, neighbour_lists=nbs,
                 synchronised=bool(np.all(state["t"] == t_end)))
 
 
@@ -86,8 +90,10 @@ def main(argv=None):
     ap.add_argument("--binaries", type=float, default=0.0,
                     help="fraction of stars in equal-mass binaries")
     ap.add_argument("--tune", default=None, help="autotuner table to load")
+    ap.add_argument("--h2", type=float, default=0.0,
+                    help="neighbour-list radius^2 requested every block step (0: none)")
     a = ap.parse_args(argv)
-    r = run(a.n, a.seed, a.eps2, a.eta, a.t_end, a.prec, a.binaries, tune=a.tune)
+    r = run(a.n, a.seed, a.eps2, a.eta, a.t_end, a.prec, a.binaries, tune=a.tune, h2=a.h2)
     print(json.dumps(r))
     return 0
 

@@ -229,3 +229,89 @@ def test_hermite_driver_plummer_32768_drift_vs_stored_oracle(name, t_end):
     assert abs(r["dE_over_E"]) <= 2 * max(abs(d_orc), 1e-12), (r["dE_over_E"], d_orc)
     # the block structure follows the oracle's closely
     assert abs(r["nactive"] / na_orc - 1) < 0.02
+
+
+@pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64])
+def test_hermite_checkpoint_resume_reproduces_the_run(orc, tmp_path, prec):
+    # Plummer N = 1024 to t = 0.125, checkpoint, continue to t = 0.25; a
+    # driver restored from the checkpoint on another cluster id reaches the
+    # same state bit for bit (same library settings, same block order).
+    from paper_0902_4463_gb300 import build
+    build.build()
+    n, eps2, eta = 1024, 1e-4, 0.01
+    m, x, v = ics.plummer(n, 1)
+    ck = str(tmp_path / "run.ckpt")
+    g6.g6x_open_ex(5, n, n)
+    try:
+        g6.g6x_set_precision(5, prec)
+        a = g6.G6HSim(5, m, x, v, eps2, eta)
+        a.run(0.125)
+        a.checkpoint(ck)
+        a.run(0.25)
+        sa, ta = a.state(), a.stats()
+        a.close()
+    finally:
+        g6.g6_close(5)
+    g6.g6x_open_ex(6, n, n)
+    try:
+        g6.g6x_set_precision(6, prec)
+        b = g6.G6HSim.restore(6, ck)
+        assert b.n == n
+        b.run(0.25)
+        sb, tb = b.state(), b.stats()
+        b.close()
+    finally:
+        g6.g6_close(6)
+    for k in ("x", "v", "acc", "jerk", "t", "dt"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert ta["nblocks"] == tb["nblocks"] and ta["nactive"] == tb["nactive"]
+    assert np.array_equal(ta["hist"], tb["hist"])
+    assert np.all(sb["t"] == 0.25)
+
+
+def test_config5_full_size_binary_members_and_lists(open_ctx, orc):
+    # Plummer N = 131072 with 10 % of the stars in binaries, eps2 = 1e-8,
+    # h2 = 1e-4 (radius 0.01): DS forces on binary members, where the DS
+    # separations matter, and their neighbour lists against the oracle.
+    n, eps2, h2 = 131072, 1e-8, 1e-4
+    m, x, v, pairs = ics.plummer_with_binaries(n, 5)
+    idx = np.arange(n)
+    cid = open_ctx(n, 4096)
+    load_j(cid, x, v, m)
+    rng = np.random.default_rng(5)
+    members = pairs[rng.choice(len(pairs), 192, replace=False)].reshape(-1)
+    act = np.concatenate([members, ics.permutation(n, 55)[:128]])
+    hv = np.full(act.size, h2)
+    acc, jerk, pot, nnb = sweep(cid, n, x[act], v[act], act, eps2, 0.0, h2=hv)
+    rc = g6.g6_read_neighbour_list(cid)
+    oa, oj, op, onn, onr = orc.force(x[act], v[act], act, x, v, m, idx, eps2)
+    ea, ep = rel_err_vec(acc, oa), np.abs(pot - op) / np.abs(op)
+    assert np.median(ea[:members.size]) <= 1e-6 and ea.max() <= 1e-5, (np.median(ea), ea.max())
+    assert np.median(ep) <= 1e-6 and ep.max() <= 1e-5
+    assert np.array_equal(nnb, onn)
+    nblen, nbl, nov = orc.neighbours(x[act], act, x, idx, hv, maxnb=g6.G6_MAXNB)
+    assert rc == (g6.G6_EOVERFLOW if nov else 0)
+    for q in range(act.size):
+        rc_q, ln, ids = g6.g6_get_neighbour_list(cid, q, g6.G6_MAXNB)
+        assert abs(ln - nblen[q]) <= 2
+        _list_ok(ids, nbl[q, :min(nblen[q], g6.G6_MAXNB)], idx, x[act[q]], x, h2)
+    # most binary members list their companion (softened pairs can be wider)
+    comp = pairs[np.isin(pairs[:, 0], members)]
+    assert np.mean([int(b) in set(g6.g6_get_neighbour_list(cid, int(np.where(act == a)[0][0]),
+                                                          g6.G6_MAXNB)[2])
+                    for a, b in comp]) > 0.5
+
+
+def test_hermite_driver_reads_neighbour_lists(open_ctx):
+    n = 2048
+    m, x, v, pairs = ics.plummer_with_binaries(n, 9)
+    cid = open_ctx(n, n)
+    sim = g6.G6HSim(cid, m, x, v, 1e-8, 0.01)
+    sim.set_neighbour_radius(1e-4)
+    sim.run(0.0625)
+    st = sim.stats()
+    nb = sim.neighbour_stats()
+    assert nb["lists"] == st["nactive"] and nb["entries"] > 0 and nb["overflowed"] == 0
+    with pytest.raises(g6.G6Error):
+        sim.set_neighbour_radius(-1.0)
+    sim.close()
