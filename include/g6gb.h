@@ -303,6 +303,21 @@ int g6x_clear_tuning(void);
 int g6x_last_config(int clusterid, int *variant, int *ti, int *tj, int *ni_per,
                     int *grid, int *jtiles);
 
+/* Limit of each bounded wait of the force kernels for a staged j-tile, in
+ * seconds, for every context (default and maximum 2 s; minimum 1e-6).  A
+ * wait that runs out makes the kernel record G6_ETIMEDOUT, which the next
+ * lasthalf / g6x_sync / g6x_batch_calc returns; the context stays usable.
+ * (The wait for the kernel's own copies in flight after a timeout always
+ * allows the full 2 s, so no copy lands after the kernel has exited.)
+ * Returns 0 or G6_EINVAL. */
+int g6x_set_wait_limit(double seconds);
+
+/* Check the timeout path: launch one bounded wait, with the current limit,
+ * on an mbarrier that nothing ever completes, on the context's stream, and
+ * return what g6x_sync then reports: G6_ETIMEDOUT when the wait ran out and
+ * was reported as the force kernels report it (0 would mean it did not). */
+int g6x_probe_wait_timeout(int clusterid);
+
 /* Number of kernels launched on the context's stream since g6_open. */
 long long g6x_launch_count(int clusterid);
 

@@ -1364,6 +1364,29 @@ int g6x_sync(int cid)
     return 0;
 }
 
+int g6x_set_wait_limit(double seconds)
+{
+    const double max_s = 1e-9 * (double)g6::max_wait_limit_ns();
+    if (!(seconds >= 1e-6) || !(seconds <= max_s))
+        return G6_EINVAL;
+    g6::set_wait_limit_ns((unsigned long long)(seconds * 1e9));
+    return 0;
+}
+
+int g6x_probe_wait_timeout(int cid)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (c->pending)
+        return G6_EBUSY;
+    cudaError_t e = g6::launch_wait_probe(c->d_err, c->stream);
+    if (e != cudaSuccess)
+        return cuda_err(e);
+    return g6x_sync(cid);
+}
+
 int g6x_get_predicted(int cid, int nj, float *hi, float *lo, float *vel, double *x64,
                       double *v64)
 {

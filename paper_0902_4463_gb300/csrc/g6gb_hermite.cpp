@@ -17,7 +17,10 @@
 #include <string>
 #include <vector>
 
+#include <memory>
+
 #include "g6gb.h"
+#include "g6gb_pool.h"
 
 struct g6h_sim {
     int cid = 0, n = 0;
@@ -42,6 +45,11 @@ struct g6h_sim {
     std::vector<double> h2v;
     std::vector<int> nbl;
     long long nb_lists = 0, nb_entries = 0, nb_overflowed = 0;
+    // host threads for the per-particle work of a block, and the block's
+    // j-records for one bulk update (tj, mass, a/2, j/6 per active particle)
+    std::unique_ptr<g6::HostPool> pool;
+    std::vector<double> tjb, mb, a2b, j6b;
+    std::vector<int> crc;
 };
 
 namespace {
@@ -147,6 +155,26 @@ double quantise(double dt, double req, double t, double dt_max)
     return dt;
 }
 
+// Particles per host work item of a block.
+constexpr int CHUNK = 64;
+
+// Per-block work arrays and the host thread pool of a driver of n particles.
+int alloc_block_work(g6h_sim &s)
+{
+    try {
+        const size_t n = (size_t)s.n;
+        s.tjb.resize(n);
+        s.mb.resize(n);
+        s.a2b.resize(3 * n);
+        s.j6b.resize(3 * n);
+        s.crc.resize((n + CHUNK - 1) / CHUNK);
+        s.pool.reset(new g6::HostPool(n > CHUNK ? g6::host_threads() : 1));
+    } catch (...) {
+        return G6_ENOMEM;
+    }
+    return 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -226,7 +254,9 @@ g6h_sim *g6h_create(int cid, int n, const double *m, const double *x, const doub
     }
     for (int k = 0; k < n; ++k)
         s->idx[k] = k;
-    rc = g6x_set_ni_max(cid, n);
+    rc = alloc_block_work(*s);
+    if (!rc)
+        rc = g6x_set_ni_max(cid, n);
     for (int k = 0; !rc && k < n; ++k)
         rc = send_j(*s, k);
     if (!rc)
@@ -278,20 +308,21 @@ int g6h_run(g6h_sim *s, double t_end)
         s->act.swap(first->second);
         s->due.erase(first);
         const int na = (int)s->act.size();
-        std::vector<int> *last_bucket = nullptr;
-        double last_time = 0.0;
+        const int nch = (na + CHUNK - 1) / CHUNK;
         // host prediction of the active i-particles (Eq. 1, Eq. 2)
-        for (int q = 0; q < na; ++q) {
-            const int k = s->act[q];
-            const double h = tb - s->t[k];
-            for (int d = 0; d < 3; ++d) {
-                const double xa = s->a[3 * k + d], xj = s->j[3 * k + d];
-                s->xp[3 * q + d] = s->x[3 * k + d]
-                                   + h * (s->v[3 * k + d] + h * (xa / 2.0 + h * xj / 6.0));
-                s->vp[3 * q + d] = s->v[3 * k + d] + h * (xa + h * xj / 2.0);
+        s->pool->run(nch, [s, tb, na](int c) {
+            for (int q = c * CHUNK, qe = std::min(na, q + CHUNK); q < qe; ++q) {
+                const int k = s->act[q];
+                const double h = tb - s->t[k];
+                for (int d = 0; d < 3; ++d) {
+                    const double xa = s->a[3 * k + d], xj = s->j[3 * k + d];
+                    s->xp[3 * q + d] = s->x[3 * k + d]
+                                       + h * (s->v[3 * k + d] + h * (xa / 2.0 + h * xj / 6.0));
+                    s->vp[3 * q + d] = s->v[3 * k + d] + h * (xa + h * xj / 2.0);
+                }
+                s->aidx[q] = k;
             }
-            s->aidx[q] = k;
-        }
+        });
         double w1 = now_s();
         int rc = g6_set_ti(s->cid, tb);
         if (!rc)
@@ -300,34 +331,60 @@ int g6h_run(g6h_sim *s, double t_end)
         if (rc)
             return rc;
         double w2 = now_s();
-        for (int q = 0; q < na; ++q) {
-            const int k = s->act[q];
-            const double h = tb - s->t[k];
-            double d2[3], d3[3], d2e[3];
-            correct(h, &s->a[3 * k], &s->j[3 * k], &s->a1[3 * q], &s->j1[3 * q],
-                    &s->xp[3 * q], &s->vp[3 * q], d2, d3);
-            for (int d = 0; d < 3; ++d)
-                d2e[d] = d2[d] + h * d3[d];
-            const double req = aarseth(&s->a1[3 * q], &s->j1[3 * q], d2e, d3, s->eta);
-            const double nd = quantise(s->dt[k], req, tb, s->dt_max);
-            if (!(nd >= s->dt_min))
-                return G6_EINVAL;
-            std::memcpy(&s->x[3 * k], &s->xp[3 * q], 3 * sizeof(double));
-            std::memcpy(&s->v[3 * k], &s->vp[3 * q], 3 * sizeof(double));
-            std::memcpy(&s->a[3 * k], &s->a1[3 * q], 3 * sizeof(double));
-            std::memcpy(&s->j[3 * k], &s->j1[3 * q], 3 * sizeof(double));
-            s->t[k] = tb;
-            s->dt[k] = nd;
-            rc = send_j(*s, k);
-            if (rc)
-                return rc;
-            // most of a block moves to one or two new times: reuse the bucket
-            const double tn = tb + nd;
-            if (!last_bucket || tn != last_time) {
-                last_bucket = &s->due[tn];
-                last_time = tn;
+        // correct, choose the next steps and fill the block's j-records
+        s->pool->run(nch, [s, tb, na](int c) {
+            int small = 0;
+            for (int q = c * CHUNK, qe = std::min(na, q + CHUNK); q < qe; ++q) {
+                const int k = s->act[q];
+                const double h = tb - s->t[k];
+                double d2[3], d3[3], d2e[3];
+                correct(h, &s->a[3 * k], &s->j[3 * k], &s->a1[3 * q], &s->j1[3 * q],
+                        &s->xp[3 * q], &s->vp[3 * q], d2, d3);
+                for (int d = 0; d < 3; ++d)
+                    d2e[d] = d2[d] + h * d3[d];
+                const double req = aarseth(&s->a1[3 * q], &s->j1[3 * q], d2e, d3, s->eta);
+                const double nd = quantise(s->dt[k], req, tb, s->dt_max);
+                small += !(nd >= s->dt_min);
+                for (int d = 0; d < 3; ++d) {
+                    s->x[3 * k + d] = s->xp[3 * q + d];
+                    s->v[3 * k + d] = s->vp[3 * q + d];
+                    s->a[3 * k + d] = s->a1[3 * q + d];
+                    s->j[3 * k + d] = s->j1[3 * q + d];
+                    s->a2b[3 * q + d] = 0.5 * s->a1[3 * q + d];
+                    s->j6b[3 * q + d] = s->j1[3 * q + d] / 6.0;
+                }
+                s->t[k] = tb;
+                s->dt[k] = nd;
+                s->tjb[q] = tb;
+                s->mb[q] = s->m[k];
             }
-            last_bucket->push_back(k);
+            s->crc[c] = small;
+        });
+        for (int c = 0; c < nch; ++c)
+            if (s->crc[c])
+                return G6_EINVAL;
+        rc = g6x_set_j_particles(s->cid, na, s->aidx.data(), s->aidx.data(), s->tjb.data(),
+                                 s->mb.data(), (const double(*)[3])s->j6b.data(),
+                                 (const double(*)[3])s->a2b.data(),
+                                 (const double(*)[3])s->vp.data(),
+                                 (const double(*)[3])s->xp.data());
+        if (rc)
+            return rc;
+        // most of a block moves to one or two new times: reuse the bucket
+        std::vector<int> *last_bucket = nullptr;
+        double last_time = 0.0;
+        try {
+            for (int q = 0; q < na; ++q) {
+                const int k = s->act[q];
+                const double tn = tb + s->dt[k];
+                if (!last_bucket || tn != last_time) {
+                    last_bucket = &s->due[tn];
+                    last_time = tn;
+                }
+                last_bucket->push_back(k);
+            }
+        } catch (...) {
+            return G6_ENOMEM;
         }
         s->act.clear();
         double w3 = now_s();
@@ -675,7 +732,9 @@ g6h_sim *g6h_restore(int cid, const char *path, int *err)
         s->idx[k] = (int)k;
     // j-memory: every particle's last corrected state, as the original run
     // left it
-    int rc = g6x_set_ni_max(cid, s->n);
+    int rc = alloc_block_work(*s);
+    if (!rc)
+        rc = g6x_set_ni_max(cid, s->n);
     for (int k = 0; !rc && k < s->n; ++k)
         rc = send_j(*s, k);
     if (rc)

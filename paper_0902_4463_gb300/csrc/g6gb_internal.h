@@ -133,6 +133,14 @@ void dev_free_hooked(void *p);
 void *host_alloc_zero_copy(size_t bytes, void **dev);
 void host_free_pinned(void *p);
 
+// Limit of each bounded wait in the force kernels (nanoseconds); the
+// compiled-in value is also the maximum.
+void set_wait_limit_ns(unsigned long long ns);
+unsigned long long wait_limit_ns();
+unsigned long long max_wait_limit_ns();
+// One bounded wait that nothing completes; records G6_ETIMEDOUT in *d_err.
+cudaError_t launch_wait_probe(int *d_err, cudaStream_t s);
+
 int batch_variant_count();
 VariantInfo batch_variant_info(int v);
 int batch_variant_occupancy(int v);

@@ -79,8 +79,9 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Wait for phase `parity` of an mbarrier for at most WAIT_LIMIT_NS.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Wait for phase `parity` of an mbarrier for at most limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  unsigned long long limit_ns)
 {
     if (mbar_try_wait(bar, parity))
         return true;
@@ -89,7 +90,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
         for (int k = 0; k < 32; ++k)
             if (mbar_try_wait(bar, parity))
                 return true;
-        if (global_ns() - t0 > WAIT_LIMIT_NS)
+        if (global_ns() - t0 > limit_ns)
             return false;
     }
 }
@@ -451,6 +452,7 @@ struct ForceArgs {
     unsigned *tcnt;                   // per i-tile: CTAs done (0 between launches)
     int fused;
     BatchTables bt;                   // batch geometry (batch kernels only)
+    unsigned long long wait_ns;       // limit of each wait for a staged tile
 };
 
 // Pair forces in FP32 with the DS separation of Eq. 3 (Sect. 2.3).  Per pair:
@@ -1009,7 +1011,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         }
         const int s = q % NSTAGE;
         const uint32_t par = (uint32_t)((q / NSTAGE) & 1);
-        const bool ready = mbar_wait_bounded(&bar[s], par);
+        const bool ready = mbar_wait_bounded(&bar[s], par, a.wait_ns);
         if (!ready) {
             s_abort = 1;
         } else {
@@ -1037,7 +1039,8 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
             // none lands in shared memory after exit, then report.
             if (tid == 0) {
                 for (int r = q; r < q + NSTAGE && r < ntile; ++r)
-                    mbar_wait_bounded(&bar[r % NSTAGE], (uint32_t)((r / NSTAGE) & 1));
+                    mbar_wait_bounded(&bar[r % NSTAGE], (uint32_t)((r / NSTAGE) & 1),
+                                      WAIT_LIMIT_NS);
                 *(volatile int *)a.err = G6_ETIMEDOUT;
             }
             return;
@@ -1400,6 +1403,24 @@ __global__ void __launch_bounds__(256) k_reduce_batch(const ReduceArgs a, BatchT
     }
 }
 
+// Limit of each wait for a staged j-tile in the force kernels (the drain of
+// copies still in flight after a timeout always allows WAIT_LIMIT_NS).
+unsigned long long g_wait_ns = WAIT_LIMIT_NS;
+
+// A wait that nothing completes: one thread waits, with the same bounded
+// wait as the force kernels, on an mbarrier that expects one arrival that
+// never comes, and reports G6_ETIMEDOUT in the error word as they do.
+__global__ void k_wait_probe(int *err, unsigned long long limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0)
+        return;
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    if (!mbar_wait_bounded(&bar, 0, limit_ns))
+        *(volatile int *)err = G6_ETIMEDOUT;
+}
+
 // ------------------------------------------------------------ variants ---
 
 namespace {
@@ -1732,6 +1753,7 @@ cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
     a.J = cfg.jtiles;
     a.ni = ni;
     a.eps2 = eps2;
+    a.wait_ns = g_wait_ns;
     const Variant &v = kVariants[cfg.variant];
     v.fn<<<cfg.grid, v.threads, v.smem, s>>>(a);
     return cudaGetLastError();
@@ -1765,6 +1787,7 @@ cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
     a.jidx = jidx;
     a.tcnt = tcnt;
     a.fused = 1;
+    a.wait_ns = g_wait_ns;
     const Variant &v = kVariants[cfg.variant];
     v.fn<<<cfg.grid, v.threads, v.smem, s>>>(a);
     return cudaGetLastError();
@@ -1883,8 +1906,21 @@ cudaError_t launch_force_batch(int v, int grid, const Pred &p, const g6x_irec *d
     a.part = part;
     a.err = d_err;
     a.bt = bt;
+    a.wait_ns = g_wait_ns;
     const Variant &bv = kBatchVariants[v];
     bv.fn<<<grid, bv.threads, bv.smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+void set_wait_limit_ns(unsigned long long ns) { g_wait_ns = ns; }
+
+unsigned long long wait_limit_ns() { return g_wait_ns; }
+
+unsigned long long max_wait_limit_ns() { return WAIT_LIMIT_NS; }
+
+cudaError_t launch_wait_probe(int *d_err, cudaStream_t s)
+{
+    k_wait_probe<<<1, 32, 0, s>>>(d_err, g_wait_ns);
     return cudaGetLastError();
 }
 

@@ -49,7 +49,7 @@ EXPORTS = [
     "g6x_set_j_particles", "g6x_strerror", "g6x_set_j_dev", "g6x_calc_dev",
     "g6x_calc_dev_noalloc", "g6x_sync", "g6x_set_variant",
     "g6x_autotune", "g6x_load_tuning", "g6x_clear_tuning", "g6x_get_predicted", "g6x_last_config",
-    "g6x_launch_count", "g6x_set_timing", "g6x_get_timing", "g6h_correct_block", "g6h_create", "g6h_run", "g6h_get_state", "g6h_energy",
+    "g6x_launch_count", "g6x_set_wait_limit", "g6x_probe_wait_timeout", "g6x_set_timing", "g6x_get_timing", "g6h_correct_block", "g6h_create", "g6h_run", "g6h_get_state", "g6h_energy",
     "g6h_stats", "g6h_profile", "g6h_destroy", "g6h_checkpoint", "g6h_restore",
     "g6h_set_neighbour_radius", "g6h_neighbour_stats",
     "g6x_batch_create", "g6x_batch_destroy", "g6x_batch_irecs", "g6x_batch_results",
@@ -105,6 +105,8 @@ def lib():
             "g6x_get_predicted": (I, [I, I, P, P, P, P, P]),
             "g6x_last_config": (I, [I, P, P, P, P, P, P]),
             "g6x_launch_count": (C.c_longlong, [I]),
+            "g6x_set_wait_limit": (I, [D]),
+            "g6x_probe_wait_timeout": (I, [I]),
             "g6x_set_timing": (I, [I, I]),
             "g6x_get_timing": (I, [I, P, P]),
             "g6h_correct_block": (I, [I, D, P, P, D, D, D, P, P, P, P, P, P, P]),
@@ -348,6 +350,16 @@ def g6x_last_config(cid):
 
 def g6x_launch_count(cid):
     return lib().g6x_launch_count(cid)
+
+
+def g6x_set_wait_limit(seconds):
+    return _check(lib().g6x_set_wait_limit(float(seconds)), "g6x_set_wait_limit")
+
+
+def g6x_probe_wait_timeout(cid):
+    """Code reported by one bounded wait that nothing completes (G6_ETIMEDOUT
+    when the timeout path works)."""
+    return lib().g6x_probe_wait_timeout(cid)
 
 
 def g6x_set_timing(cid, enable=True):

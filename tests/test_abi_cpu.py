@@ -124,3 +124,13 @@ def test_tuning_table_file_round_trip(lib, tmp_path):
     with pytest.raises(g6gb.G6Error):
         g6gb.g6x_load_tuning(bad)
     assert g6gb.g6x_clear_tuning() == 0
+
+
+def test_wait_limit_range(lib):
+    assert lib.g6x_set_wait_limit(0.0) == g6gb.G6_EINVAL
+    assert lib.g6x_set_wait_limit(1e-7) == g6gb.G6_EINVAL
+    assert lib.g6x_set_wait_limit(3.0) == g6gb.G6_EINVAL
+    assert lib.g6x_set_wait_limit(float("nan")) == g6gb.G6_EINVAL
+    assert lib.g6x_set_wait_limit(0.5) == 0
+    assert lib.g6x_set_wait_limit(2.0) == 0
+    assert lib.g6x_probe_wait_timeout(9) == g6gb.G6_ENOTOPEN

@@ -227,3 +227,54 @@ def test_argument_errors_are_reported(ctx):
     load_j(ctx, x, v, m)
     acc, *_ = sweep(ctx, 64, x, v, np.arange(64), 1e-2, 0.0)
     assert np.all(np.isfinite(acc))
+
+
+def test_bounded_wait_that_nothing_completes_is_reported(ctx, orc):
+    # Failure detection without a fault: one bounded wait on an mbarrier that
+    # nothing completes runs out after the set limit and is reported as the
+    # force kernels report it; the context stays usable.
+    import time
+    g6.g6x_set_wait_limit(0.05)
+    try:
+        t0 = time.perf_counter()
+        rc = g6.g6x_probe_wait_timeout(ctx)
+        dt = time.perf_counter() - t0
+    finally:
+        g6.g6x_set_wait_limit(2.0)
+    assert rc == g6.G6_ETIMEDOUT
+    assert 0.04 <= dt < 1.5, dt
+    n, eps2 = 1024, 1e-4
+    m, x, v = ics.plummer(n, 1)
+    idx = np.arange(n)
+    load_j(ctx, x, v, m)
+    acc, jerk, pot, nnb = sweep(ctx, n, x, v, idx, eps2, 0.0)
+    oa, *_ = orc.force(x, v, idx, x, v, m, idx, eps2)
+    assert np.median(rel_err_vec(acc, oa)) <= 1e-6
+
+
+def test_force_kernel_timeout_path_leaves_the_context_usable(ctx, orc):
+    # With a 1 us limit the force kernel's waits for staged j-tiles may run
+    # out (the hardware wait can also complete first): the call then reports
+    # G6_ETIMEDOUT after draining its copies; either way the next call with
+    # the normal limit gives correct forces.
+    n, eps2, mi = 65536, 1e-5, 8192
+    m, x, v = ics.plummer(n, 2)
+    idx = np.arange(n)
+    load_j(ctx, x, v, m)
+    act = np.sort(ics.permutation(n, 3)[:mi])
+    outcome = 0
+    g6.g6x_set_wait_limit(1e-6)
+    try:
+        for _ in range(3):
+            try:
+                sweep(ctx, n, x[act], v[act], act, eps2, 0.0)
+            except g6.G6Error as e:
+                outcome = e.code
+                break
+    finally:
+        g6.g6x_set_wait_limit(2.0)
+    assert outcome in (0, g6.G6_ETIMEDOUT)
+    acc, jerk, pot, nnb = sweep(ctx, n, x[act], v[act], act, eps2, 0.0)
+    oa, *_ = orc.force(x[act[:256]], v[act[:256]], act[:256], x, v, m, idx, eps2)
+    ea = rel_err_vec(acc[:256], oa)
+    assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5
