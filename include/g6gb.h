@@ -344,6 +344,13 @@ g6h_sim *g6h_create(int clusterid, int n, const double *m, const double *x,
  * dt_max).  Returns 0 or a negative error. */
 int g6h_run(g6h_sim *s, double t_end);
 
+/* As g6h_run, but stop after at most max_blocks block steps.  Returns the
+ * number of block steps taken (fewer than max_blocks once every particle
+ * has reached t_end) or a negative error.  Between calls the particles sit
+ * at their own last block times (g6h_get_state: t, dt), as in GRAPE-style
+ * codes between blocks. */
+long long g6h_run_blocks(g6h_sim *s, double t_end, long long max_blocks);
+
 /* The driver's corrector and time-step choice for n particles that reach
  * the block time t_blk together (Sect. 2; Makino & Aarseth 1992 corrector,
  * Aarseth 1985 criterion with a'' taken at the end of the step, power-of-two

@@ -410,11 +410,13 @@ int predict_if_stale(Ctx &c, int nj)
 // The GRAPE path's j-store update and prediction in one launch: the staged
 // records are counting-sorted by tile on the host into mapped memory, and
 // each predictor CTA stores its tile's records before predicting the tile.
-int update_and_predict(Ctx &c, int nj)
+// predict = false: only store the staged records (for a force kernel that
+// predicts the j-tiles itself); every cached prediction is then stale.
+int update_and_predict(Ctx &c, int nj, bool predict = true)
 {
     if (c.n_jst == 0)
-        return predict_if_stale(c, nj);
-    const int nj_pad = round_up(nj > 0 ? nj : 1, JT);
+        return predict ? predict_if_stale(c, nj) : 0;
+    const int nj_pad = predict ? round_up(nj > 0 ? nj : 1, JT) : 0;
     int max_tile = 0;
     for (int k = 0; k < c.n_jst; ++k) {
         const int tl = c.h_jst[k].address / JT;
@@ -482,6 +484,8 @@ int update_and_predict(Ctx &c, int nj)
         c.slot_of[c.h_jst[k].address] = -1;
     c.n_jst = 0;
     c.ver += 1;
+    if (!predict)
+        return 0;                  // c.ver moved on: every cached prediction is stale
     c.t_pred[kind] = c.t_set;
     c.nj_pred[kind] = nj;
     c.ver_pred[kind] = c.ver;
@@ -526,12 +530,42 @@ int grow_nb_out(Ctx &c, int ni)
 }
 
 // Force + reduction on ni i records already on the device.
-int run_force(Ctx &c, int nj, int ni, const g6x_irec *d_irec, double eps2, bool list,
-              g6x_out *d_out)
+// The launch for ni i-particles against nj j-particles; a fused-prediction
+// shape only with the DS + SP predictor and no lists.
+ForceConfig pick_config(const Ctx &c, int nj, int ni, bool list)
 {
-    int nj_pad = round_up(nj > 0 ? nj : 1, JT);
-    ForceConfig cfg = g6::choose_config(c.prec, ni, nj_pad, list ? 1 : 0, c.sm_count,
-                                        c.force_variant, c.force_grid);
+    const int nj_pad = round_up(nj > 0 ? nj : 1, JT);
+    return g6::choose_config(c.prec, ni, nj_pad, list ? 1 : 0, c.sm_count, c.force_variant,
+                             c.force_grid, c.pmode == G6X_PREC_DS && !list);
+}
+
+// j-store update, prediction (unless the force kernel predicts itself),
+// force and reduction.
+int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_irec,
+              double eps2, g6x_out *d_out);
+
+int predict_and_force(Ctx &c, int nj, int ni, const g6x_irec *d_irec, double eps2, bool list,
+                      g6x_out *d_out)
+{
+    const ForceConfig cfg = pick_config(c, nj, ni, list);
+    const bool fp = g6::variant_info(cfg.variant).fpred != 0 && ni > 0;
+    int rc = update_and_predict(c, nj, !fp);
+    if (!rc && ni > 0)
+        rc = run_force(c, cfg, nj, ni, d_irec, eps2, d_out);
+    return rc;
+}
+
+int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_irec,
+              double eps2, g6x_out *d_out)
+{
+    const g6::FusedPred fpa{c.js, c.t_set, nj};
+    const bool fp = g6::variant_info(cfg.variant).fpred != 0;
+    const g6::FusedPred *fpp = fp ? &fpa : nullptr;
+    if (fp) {
+        // the kernel rewrites predicted tiles (not their index ranges)
+        for (int k = 0; k < 3; ++k)
+            c.ver_pred[k] = -1;
+    }
     size_t slots = g6::partial_slots(cfg);
     int rc = grow_dev(c.d_part, c.part_cap, slots);
     if (rc)
@@ -580,13 +614,13 @@ int run_force(Ctx &c, int nj, int ni, const g6x_irec *d_irec, double eps2, bool 
         }
         PhaseTimer pt(c, PH_FORCE);
         e = g6::launch_force_fused(cfg, c.pred, d_irec, ni, eps2, c.d_part, c.d_err, d_out,
-                                   c.js.idx, c.d_tcnt, c.stream);
+                                   c.js.idx, c.d_tcnt, c.stream, fpp);
         c.launches += 1;
     } else {
         {
             PhaseTimer pt(c, PH_FORCE);
             e = g6::launch_force(cfg, c.pred, d_irec, ni, eps2, c.d_part, c.d_nbl_part,
-                                 c.d_nbc_part, c.d_err, c.stream);
+                                 c.d_nbc_part, c.d_err, c.stream, fpp);
         }
         if (e == cudaSuccess) {
             PhaseTimer pt(c, PH_REDUCE);
@@ -886,12 +920,11 @@ void g6calc_firsthalf(int cid, int nj, int ni, const int index[],
         if (h2 && h2[k] > 0.0)
             list = true;
     }
+    // the kernels read the i-records from, and write results to, the mapped
+    // host buffers: no separate copies
     if (!rc)
-        rc = update_and_predict(*c, nj);
+        rc = predict_and_force(*c, nj, ni, c->d_irec, eps2, list, c->d_out);
     if (!rc && ni > 0) {
-        // the kernels read the i-records from, and write results to, the
-        // mapped host buffers: no separate copies
-        rc = run_force(*c, nj, ni, c->d_irec, eps2, list, c->d_out);
         if (!rc && h2 && !list) {
             // every radius is <= 0: no list can have entries; skip the list
             // kernel and publish empty lists
@@ -1078,10 +1111,7 @@ int g6x_calc_dev(int cid, double ti, int nj, int ni, const g6x_irec *d_irec, dou
         || !std::isfinite(ti) || (ni > 0 && (!d_irec || !d_out)))
         return G6_EINVAL;
     c->t_set = ti;
-    int rc = update_and_predict(*c, nj);
-    if (!rc && ni > 0)
-        rc = run_force(*c, nj, ni, d_irec, eps2, nl != 0, d_out);
-    return rc;
+    return predict_and_force(*c, nj, ni, d_irec, eps2, nl != 0, d_out);
 }
 
 // ------------------------------------------------ allocation-free variant
@@ -1241,6 +1271,8 @@ extern "C" int g6x_autotune(int cid, int nj, int m_max, const char *path)
     }
     cudaError_t e = g6::launch_irec_from_store(c->js, d_i, m_cap, c->stream);
     c->launches += 1;
+    const int pkind = c->pmode == G6X_PREC_FP64 ? g6::PRED_FP64
+                      : c->pmode == G6X_PREC_DS_X64 ? g6::PRED_DS_X64 : g6::PRED_DS;
     int tuned = 0;
     bool lost_work = false;
     for (int m = 16; e == cudaSuccess && m <= m_cap; m *= 2) {
@@ -1248,7 +1280,8 @@ extern "C" int g6x_autotune(int cid, int nj, int m_max, const char *path)
         int bv = -1, bg = 1;
         for (int v = 0; v < g6::variant_count() && e == cudaSuccess; ++v) {
             const g6::VariantInfo vi = g6::variant_info(v);
-            if (vi.prec != c->prec || vi.list || vi.ti * vi.nper > 16 * m)
+            if (vi.prec != c->prec || vi.list || vi.ti * vi.nper > 16 * m
+                || (vi.fpred && c->pmode != G6X_PREC_DS))
                 continue;
             int occ = g6::variant_occupancy(v);
             if (occ < 1)
@@ -1256,7 +1289,7 @@ extern "C" int g6x_autotune(int cid, int nj, int m_max, const char *path)
             int last_grid = -1;
             for (int gm = 1; gm <= 2 && e == cudaSuccess; ++gm) {
                 ForceConfig cfg = g6::choose_config(c->prec, m, nj_pad, 0, c->sm_count, v,
-                                                    c->sm_count * occ * gm);
+                                                    c->sm_count * occ * gm, true);
                 if (cfg.grid == last_grid)
                     continue;
                 last_grid = cfg.grid;
@@ -1265,11 +1298,20 @@ extern "C" int g6x_autotune(int cid, int nj, int m_max, const char *path)
                     continue;
                 }
                 float t_best = 1e30f;
+                // a step: the prediction (inside the kernel for fused
+                // shapes) + force + reduction; the tiles predicted by either
+                // route at the same time are identical, so the cached
+                // prediction stays valid
+                const g6::FusedPred fpa{c->js, c->t_set, nj};
                 for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
                     e = cudaEventRecord(e0, c->stream);
+                    if (e == cudaSuccess && !vi.fpred)
+                        e = g6::launch_predict(pkind, c->js, c->pred, nj, nj_pad, c->t_set,
+                                               c->sm_count, c->stream);
                     if (e == cudaSuccess)
                         e = g6::launch_force(cfg, c->pred, d_i, m, 1e-6, c->d_part, nullptr,
-                                             nullptr, c->d_err, c->stream);
+                                             nullptr, c->d_err, c->stream,
+                                             vi.fpred ? &fpa : nullptr);
                     if (e == cudaSuccess)
                         e = g6::launch_reduce(cfg, c->d_part, nullptr, nullptr, c->js.idx, m,
                                               d_o, nullptr, nullptr, c->stream);

@@ -8,6 +8,7 @@
 // quantised to powers of two (block time steps).
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -292,11 +293,12 @@ g6h_sim *g6h_create(int cid, int n, const double *m, const double *x, const doub
     return s;
 }
 
-int g6h_run(g6h_sim *s, double t_end)
+long long g6h_run_blocks(g6h_sim *s, double t_end, long long max_blocks)
 {
-    if (!s || !(t_end >= 0) || std::fmod(t_end, s->dt_max) != 0.0)
+    if (!s || !(t_end >= 0) || std::fmod(t_end, s->dt_max) != 0.0 || max_blocks < 0)
         return G6_EINVAL;
-    for (;;) {
+    long long done = 0;
+    while (done < max_blocks) {
         double w0 = now_s();
         // block scheduler: the earliest next time and the particles due then
         if (s->due.empty())
@@ -398,8 +400,15 @@ int g6h_run(g6h_sim *s, double t_end)
             ++b;
         s->hist[b] += 1;
         s->t_now = tb;
+        ++done;
     }
-    return 0;
+    return done;
+}
+
+int g6h_run(g6h_sim *s, double t_end)
+{
+    const long long r = g6h_run_blocks(s, t_end, LLONG_MAX);
+    return r < 0 ? (int)r : 0;
 }
 
 int g6h_get_state(const g6h_sim *s, double *x, double *v, double *acc, double *jerk,

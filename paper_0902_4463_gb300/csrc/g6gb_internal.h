@@ -95,6 +95,16 @@ struct ForceConfig {
 // Shape of one compiled force-kernel variant.
 struct VariantInfo {
     int ti, tj, nper, list, prec;
+    int fpred = 0;     // predicts the j-tiles itself (Eq. 1, Eq. 2) from the raw j-store
+    int twin = -1;     // for fpred shapes: the same shape reading predicted tiles
+};
+
+// What a fused-prediction force kernel needs: the raw j-store, the block
+// time and the number of particles in j-memory (DS + SP predictor only).
+struct FusedPred {
+    JStore js;
+    double t;
+    int nj;
 };
 
 // Work geometry of a batch of independent clusters: cluster k holds j-tiles
@@ -158,8 +168,9 @@ VariantInfo variant_info(int v);
 // Resident CTAs per SM of variant v (0 on error).
 int variant_occupancy(int v);
 // Pick a variant and grid for ni i-particles against nj_pad j-particles.
+// allow_fpred: a fused-prediction shape may be chosen (otherwise its twin).
 ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
-                          int force_variant, int force_grid);
+                          int force_variant, int force_grid, bool allow_fpred = false);
 // Number of Partial slots a launch with this configuration writes.
 size_t partial_slots(const ForceConfig &cfg);
 
@@ -191,14 +202,14 @@ cudaError_t launch_update_predict(int kind, JStore js, Pred p, int nj, int nj_pa
 cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
                          const g6x_irec *d_irec, int ni, double eps2,
                          void *part, int *nbl_part, int *nbc_part,
-                         int *d_err, cudaStream_t s);
+                         int *d_err, cudaStream_t s, const FusedPred *fp = nullptr);
 // DS force with the reduction fused in (no neighbour lists): the last CTA
 // to finish an i-tile writes its results to out.  tcnt holds one counter per
 // i-tile, zero before the launch and left zero by a launch that completes.
 cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
                                const g6x_irec *d_irec, int ni, double eps2, void *part,
                                int *d_err, g6x_out *out, const int *jidx, unsigned *tcnt,
-                               cudaStream_t s);
+                               cudaStream_t s, const FusedPred *fp = nullptr);
 cudaError_t launch_reduce(const ForceConfig &cfg, const void *part,
                           const int *nbl_part, const int *nbc_part,
                           const int *jidx, int ni, g6x_out *d_out,

@@ -38,6 +38,18 @@ namespace {
 constexpr int NSTAGE = 3;
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s per mbarrier wait
 
+// One j-tile of the raw j-store arrays as staged by the force kernel with
+// fused prediction: t0, (v, m), a/2, j/6, (x_hi, y_hi, z_hi, x_lo),
+// (y_lo, z_lo), index -- 84 B per particle, every part 16-byte aligned.
+constexpr unsigned RAW_T0 = 0;
+constexpr unsigned RAW_V = RAW_T0 + JT * 8;
+constexpr unsigned RAW_A = RAW_V + JT * 16;
+constexpr unsigned RAW_J = RAW_A + JT * 16;
+constexpr unsigned RAW_XA = RAW_J + JT * 16;
+constexpr unsigned RAW_XB = RAW_XA + JT * 16;
+constexpr unsigned RAW_ID = RAW_XB + JT * 8;
+constexpr unsigned RAW_TILE_BYTES = RAW_ID + JT * 4;
+
 __device__ __forceinline__ float rsqrt_approx(float x)
 {
     float y;
@@ -266,13 +278,9 @@ __device__ __forceinline__ void tile_index_range(int *s_lo, int *s_hi, int id, b
 // the paper's form (Sect. 2.2) -- Taylor increment dt (v + dt (a/2 + dt j/6))
 // in FP32, added to the double-single x0 by the DS + SP addition, velocity in
 // FP32; only dt = t - t0 is formed in FP64 (block times are exact there).
-__device__ __forceinline__ void predict_slot_ds(const JStore &js, int k, double t, float *o,
-                                                int id)
+__device__ __forceinline__ void predict_ds_vals(float h, float4 xa, float2 xb, float4 v,
+                                                float4 a, float4 j, int id, float *o)
 {
-    const float h = (float)(t - js.t0[k]);
-    const float4 v = js.v0m[k], a = js.a2f[k], j = js.j6f[k];
-    const float4 xa = js.xds[k];
-    const float2 xb = js.xds2[k];
     float hx, lx, hy, ly, hz, lz;
     ds_add_f(xa.x, xa.w, h * fmaf(h, fmaf(h, j.x, a.x), v.x), hx, lx);
     ds_add_f(xa.y, xb.x, h * fmaf(h, fmaf(h, j.y, a.y), v.y), hy, ly);
@@ -289,6 +297,13 @@ __device__ __forceinline__ void predict_slot_ds(const JStore &js, int k, double 
     o[W_VY * JT] = fmaf(h, fmaf(h3, j.y, 2.0f * a.y), v.y);
     o[W_VZ * JT] = fmaf(h, fmaf(h3, j.z, 2.0f * a.z), v.z);
     o[W_ID * JT] = __int_as_float(id);
+}
+
+__device__ __forceinline__ void predict_slot_ds(const JStore &js, int k, double t, float *o,
+                                                int id)
+{
+    predict_ds_vals((float)(t - js.t0[k]), js.xds[k], js.xds2[k], js.v0m[k], js.a2f[k],
+                    js.j6f[k], id, o);
 }
 
 // The same with the DS position formed through FP64: the FP32 increment is
@@ -453,6 +468,12 @@ struct ForceArgs {
     int fused;
     BatchTables bt;                   // batch geometry (batch kernels only)
     unsigned long long wait_ns;       // limit of each wait for a staged tile
+    // prediction inside the force kernel: the j-store, the block time, the
+    // number of particles in j-memory, and where the predicted tiles go
+    JStore js;
+    double t_pred;
+    int nj;
+    float *pt_w;
 };
 
 // Pair forces in FP32 with the DS separation of Eq. 3 (Sect. 2.3).  Per pair:
@@ -480,21 +501,29 @@ struct ForceArgs {
 // then folded into compensated (TwoSum) FP32 pairs kept in shared memory, so
 // rounding does not grow with n; the pairs are combined in FP64 when
 // partials are written.
-template <int TI, int TJ, int NI, bool LIST, int MINB = 1, int UNR = 2, bool BATCH = false>
+template <int TI, int TJ, int NI, bool LIST, int MINB = 1, int UNR = 2, bool BATCH = false,
+          bool FP = false>
 __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
 {
     static_assert(!(LIST && BATCH), "batches carry no neighbour lists");
+    static_assert(!(FP && (LIST || BATCH)), "fused prediction: single context, no lists");
     constexpr int NT = TI * TJ;
     constexpr int ITILE = TI * NI;
     constexpr int PPT = JT / 2 / TJ;                  // j-pairs per thread per tile
     constexpr int FLUSH = (256 + PPT - 1) / PPT;      // tiles between flushes (>= 512 j)
     constexpr unsigned TILE_BYTES = JW * JT * sizeof(float);
+    // FP: a stage holds one tile of the raw j-store arrays (RAW_* offsets),
+    // predicted by the CTA into pbuf before the pair loop
+    constexpr unsigned STAGE_BYTES = FP ? RAW_TILE_BYTES : TILE_BYTES;
     static_assert(!LIST || TJ == 1, "neighbour lists need whole j-tiles per thread");
     static_assert(JT % (2 * TJ) == 0, "j-tile must split into j-pairs evenly");
 
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     float *stage_buf = reinterpret_cast<float *>(dyn_smem);
-    float2 *comp = reinterpret_cast<float2 *>(dyn_smem + NSTAGE * TILE_BYTES);  // [NI][7][NT]
+    float *pbuf = reinterpret_cast<float *>(dyn_smem + NSTAGE * STAGE_BYTES);    // FP only
+    float2 *comp = reinterpret_cast<float2 *>(dyn_smem + NSTAGE * STAGE_BYTES
+                                              + (FP ? TILE_BYTES : 0));         // [NI][7][NT]
+    __shared__ int s_wlo[FP ? NT / 32 : 1], s_whi[FP ? NT / 32 : 1];
     __shared__ __align__(8) uint64_t bar[NSTAGE];
     __shared__ int s_abort;
     __shared__ float s_nnr[TJ > 1 ? NI * NT : 1];
@@ -575,9 +604,62 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
             ++issue_g;
         const int jt = jt_of(p, issue_g);
         int s = q % NSTAGE;
-        mbar_expect_tx(&bar[s], TILE_BYTES);
-        bulk_g2s(stage_buf + (size_t)s * JW * JT, a.pt + (size_t)jt * JW * JT, TILE_BYTES,
-                 &bar[s]);
+        if constexpr (FP) {
+            unsigned char *d = dyn_smem + (size_t)s * RAW_TILE_BYTES;
+            const size_t j0 = (size_t)jt * JT;
+            mbar_expect_tx(&bar[s], RAW_TILE_BYTES);
+            bulk_g2s(d + RAW_T0, a.js.t0 + j0, JT * sizeof(double), &bar[s]);
+            bulk_g2s(d + RAW_V, a.js.v0m + j0, JT * sizeof(float4), &bar[s]);
+            bulk_g2s(d + RAW_A, a.js.a2f + j0, JT * sizeof(float4), &bar[s]);
+            bulk_g2s(d + RAW_J, a.js.j6f + j0, JT * sizeof(float4), &bar[s]);
+            bulk_g2s(d + RAW_XA, a.js.xds + j0, JT * sizeof(float4), &bar[s]);
+            bulk_g2s(d + RAW_XB, a.js.xds2 + j0, JT * sizeof(float2), &bar[s]);
+            bulk_g2s(d + RAW_ID, a.js.idx + j0, JT * sizeof(int), &bar[s]);
+        } else {
+            mbar_expect_tx(&bar[s], TILE_BYTES);
+            bulk_g2s(stage_buf + (size_t)s * JW * JT, a.pt + (size_t)jt * JW * JT, TILE_BYTES,
+                     &bar[s]);
+        }
+    };
+
+    // FP: Eq. 1 and Eq. 2 for the staged raw tile jt (stage s) into pbuf, with
+    // the arithmetic of K1 (bit-identical tiles); the tile is also written to
+    // the predicted-tile buffer for the nearest-neighbour rescan, and each
+    // warp's range of particle indices goes to s_wlo/s_whi.
+    auto predict_tile = [&](int s, int jt) {
+        const unsigned char *d = dyn_smem + (size_t)s * RAW_TILE_BYTES;
+        const double *T0 = reinterpret_cast<const double *>(d + RAW_T0);
+        const float4 *V = reinterpret_cast<const float4 *>(d + RAW_V);
+        const float4 *A = reinterpret_cast<const float4 *>(d + RAW_A);
+        const float4 *J = reinterpret_cast<const float4 *>(d + RAW_J);
+        const float4 *XA = reinterpret_cast<const float4 *>(d + RAW_XA);
+        const float2 *XB = reinterpret_cast<const float2 *>(d + RAW_XB);
+        const int *ID = reinterpret_cast<const int *>(d + RAW_ID);
+        int lo = INT_MAX, hi = -1;
+        for (int jj = tid; jj < JT; jj += NT) {
+            float *o = pbuf + jj;
+            if (jt * JT + jj < a.nj) {
+                const int id = ID[jj];
+                predict_ds_vals((float)(a.t_pred - T0[jj]), XA[jj], XB[jj], V[jj], A[jj], J[jj],
+                                id, o);
+                if (id >= 0) {
+                    lo = min(lo, id);
+                    hi = max(hi, id);
+                }
+            } else {
+                far_slot_ds(o);
+            }
+            float *g = a.pt_w + (size_t)jt * JW * JT + jj;
+#pragma unroll
+            for (int w = 0; w < JW; ++w)
+                g[w * JT] = o[w * JT];
+        }
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if ((tid & 31) == 0) {
+            s_wlo[tid >> 5] = lo;
+            s_whi[tid >> 5] = hi;
+        }
     };
     if (tid == 0)
         for (int q = 0; q < NSTAGE && q < ntile; ++q)
@@ -711,6 +793,13 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         if (!(nnr[k] < INF) || nnt[k] < 0)
             return -1;
         const float *T = a.pt + (size_t)nnt[k] * JW * JT;
+        // FP wrote these tiles in this launch: read them through L2
+        auto ld = [](const float *q) -> float {
+            if constexpr (FP)
+                return __ldcg(q);
+            else
+                return __ldg(q);
+        };
         constexpr int CH = 4;                       // j-pairs per chunk
         for (int kk0 = 0; kk0 < PPT; kk0 += CH) {
             float key[2 * CH];
@@ -723,14 +812,14 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                     float r2u = INF;
                     int id = -1;
                     if (kk < PPT) {
-                        const float dx = __fadd_rn(__fadd_rn(__ldg(T + W_XH * JT + jj), nxh[k][0].x),
-                                                   __fadd_rn(__ldg(T + W_XL * JT + jj), nxl[k][0].x));
-                        const float dy = __fadd_rn(__fadd_rn(__ldg(T + W_YH * JT + jj), nxh[k][1].x),
-                                                   __fadd_rn(__ldg(T + W_YL * JT + jj), nxl[k][1].x));
-                        const float dz = __fadd_rn(__fadd_rn(__ldg(T + W_ZH * JT + jj), nxh[k][2].x),
-                                                   __fadd_rn(__ldg(T + W_ZL * JT + jj), nxl[k][2].x));
+                        const float dx = __fadd_rn(__fadd_rn(ld(T + W_XH * JT + jj), nxh[k][0].x),
+                                                   __fadd_rn(ld(T + W_XL * JT + jj), nxl[k][0].x));
+                        const float dy = __fadd_rn(__fadd_rn(ld(T + W_YH * JT + jj), nxh[k][1].x),
+                                                   __fadd_rn(ld(T + W_YL * JT + jj), nxl[k][1].x));
+                        const float dz = __fadd_rn(__fadd_rn(ld(T + W_ZH * JT + jj), nxh[k][2].x),
+                                                   __fadd_rn(ld(T + W_ZL * JT + jj), nxl[k][2].x));
                         r2u = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-                        id = __float_as_int(__ldg(T + W_ID * JT + jj));
+                        id = __float_as_int(ld(T + W_ID * JT + jj));
                     }
                     key[2 * u + h] = (id == iid[k]) ? INF : r2u;
                 }
@@ -999,23 +1088,17 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
             load_i(t);
             cur_t = t;
         }
+        const int s = q % NSTAGE;
+        const uint32_t par = (uint32_t)((q / NSTAGE) & 1);
         // Does this tile hold the j-particle of one of the warp's i-particles?
-        bool self_tile = LIST;
-        if constexpr (!LIST) {
-            const int2 rg = a.trange[jt];
+        auto self_test = [&](int2 rg) -> bool {
             bool mine = false;
 #pragma unroll
             for (int k = 0; k < NI; ++k)
                 mine |= (iid[k] >= rg.x && iid[k] <= rg.y);
-            self_tile = __any_sync(0xffffffffu, mine);
-        }
-        const int s = q % NSTAGE;
-        const uint32_t par = (uint32_t)((q / NSTAGE) & 1);
-        const bool ready = mbar_wait_bounded(&bar[s], par, a.wait_ns);
-        if (!ready) {
-            s_abort = 1;
-        } else {
-            const float *S = stage_buf + (size_t)s * JW * JT;
+            return __any_sync(0xffffffffu, mine);
+        };
+        auto pairs_of_tile = [&](const float *S, bool self_tile) {
             if (self_tile)
                 tile_pass(S, t, jt, std::true_type{});
             else
@@ -1032,21 +1115,56 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                 flush();
                 since_flush = 0;
             }
-        }
-        __syncthreads();
-        if (s_abort) {
-            // Give up: wait (bounded) for this CTA's copies still in flight so
-            // none lands in shared memory after exit, then report.
+        };
+        // Give up: wait (bounded, always the full limit) for this CTA's
+        // copies still in flight so none lands in shared memory after exit,
+        // then report.
+        auto give_up = [&]() {
             if (tid == 0) {
                 for (int r = q; r < q + NSTAGE && r < ntile; ++r)
                     mbar_wait_bounded(&bar[r % NSTAGE], (uint32_t)((r / NSTAGE) & 1),
                                       WAIT_LIMIT_NS);
                 *(volatile int *)a.err = G6_ETIMEDOUT;
             }
-            return;
+        };
+        if constexpr (FP) {
+            const bool ready = mbar_wait_bounded(&bar[s], par, a.wait_ns);
+            if (!ready)
+                s_abort = 1;
+            else
+                predict_tile(s, jt);
+            __syncthreads();
+            if (s_abort) {
+                give_up();
+                return;
+            }
+            if (tid == 0 && q + NSTAGE < ntile)
+                issue(q + NSTAGE);               // the raw stage is free again
+            int2 rg = make_int2(INT_MAX, -1);
+#pragma unroll
+            for (int w = 0; w < NT / 32; ++w) {
+                rg.x = min(rg.x, s_wlo[w]);
+                rg.y = max(rg.y, s_whi[w]);
+            }
+            pairs_of_tile(pbuf, self_test(rg));
+            __syncthreads();                     // pbuf is rewritten by the next tile
+        } else {
+            bool self_tile = LIST;
+            if constexpr (!LIST)
+                self_tile = self_test(a.trange[jt]);
+            const bool ready = mbar_wait_bounded(&bar[s], par, a.wait_ns);
+            if (!ready)
+                s_abort = 1;
+            else
+                pairs_of_tile(stage_buf + (size_t)s * JW * JT, self_tile);
+            __syncthreads();
+            if (s_abort) {
+                give_up();
+                return;
+            }
+            if (tid == 0 && q + NSTAGE < ntile)
+                issue(q + NSTAGE);
         }
-        if (tid == 0 && q + NSTAGE < ntile)
-            issue(q + NSTAGE);
     }
     finalize(cur_t);
 }
@@ -1440,6 +1558,13 @@ constexpr int ds_smem(int nt, int ni)
     return NSTAGE * JW * JT * (int)sizeof(float) + ni * 7 * nt * (int)sizeof(float2);
 }
 
+// ... with fused prediction: NSTAGE raw tiles + one predicted tile + sums
+constexpr int fp_smem(int nt, int ni)
+{
+    return NSTAGE * (int)RAW_TILE_BYTES + JW * JT * (int)sizeof(float)
+           + ni * 7 * nt * (int)sizeof(float2);
+}
+
 const Variant kVariants[] = {
     {{128, 1, 2, 0, G6X_PREC_DS}, k_force_ds<128, 1, 2, false, 3, 2>, 128, ds_smem(128, 2)},
     {{128, 1, 1, 0, G6X_PREC_DS}, k_force_ds<128, 1, 1, false>, 128, ds_smem(128, 1)},
@@ -1460,6 +1585,16 @@ const Variant kVariants[] = {
     {{16, 16, 2, 0, G6X_PREC_DS}, k_force_ds<16, 16, 2, false, 2, 2>, 256, ds_smem(256, 2)},
     {{32, 8, 2, 0, G6X_PREC_DS}, k_force_ds<32, 8, 2, false, 2, 2>, 256, ds_smem(256, 2)},
     {{64, 4, 2, 0, G6X_PREC_DS}, k_force_ds<64, 4, 2, false, 2, 2>, 256, ds_smem(256, 2)},
+    // fused prediction (Eq. 1, Eq. 2 inside the force kernel, no separate
+    // predictor launch) for small blocks: twins of variants 4, 14, 15, 16
+    {{16, 16, 1, 0, G6X_PREC_DS, 1, 4}, k_force_ds<16, 16, 1, false, 1, 2, false, true>, 256,
+     fp_smem(256, 1)},
+    {{16, 16, 2, 0, G6X_PREC_DS, 1, 14}, k_force_ds<16, 16, 2, false, 2, 2, false, true>, 256,
+     fp_smem(256, 2)},
+    {{32, 8, 2, 0, G6X_PREC_DS, 1, 15}, k_force_ds<32, 8, 2, false, 2, 2, false, true>, 256,
+     fp_smem(256, 2)},
+    {{64, 4, 2, 0, G6X_PREC_DS, 1, 16}, k_force_ds<64, 4, 2, false, 2, 2, false, true>, 256,
+     fp_smem(256, 2)},
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
@@ -1609,7 +1744,7 @@ void tune_clear()
 }
 
 ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
-                          int force_variant, int force_grid)
+                          int force_variant, int force_grid, bool allow_fpred)
 {
     int v;
     int gmul = 1, tv = -1;
@@ -1637,6 +1772,10 @@ ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
         v = 0;                       // 128 threads, two i each, whole j-tiles
         gmul = 2;
     }
+    // a fused-prediction shape only where the caller can use it (DS
+    // predictor, the j-store current); otherwise its separate twin
+    if (kVariants[v].info.fpred && (!allow_fpred || list))
+        v = kVariants[v].info.twin;
     const VariantInfo &vi = kVariants[v].info;
     ForceConfig c{};
     c.variant = v;
@@ -1729,10 +1868,25 @@ cudaError_t launch_update_predict(int kind, JStore js, Pred p, int nj, int nj_pa
     return cudaGetLastError();
 }
 
+// Arguments of the fused prediction (variants with fpred set).
+static bool set_fused_pred(ForceArgs &a, const ForceConfig &cfg, const Pred &p,
+                           const FusedPred *fp)
+{
+    if (!kVariants[cfg.variant].info.fpred)
+        return true;
+    if (!fp)
+        return false;
+    a.js = fp->js;
+    a.t_pred = fp->t;
+    a.nj = fp->nj;
+    a.pt_w = p.pt;
+    return true;
+}
+
 cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
                          const g6x_irec *d_irec, int ni, double eps2,
                          void *part, int *nbl_part, int *nbc_part,
-                         int *d_err, cudaStream_t s)
+                         int *d_err, cudaStream_t s, const FusedPred *fp)
 {
     if (cfg.work <= 0)
         return cudaSuccess;
@@ -1754,6 +1908,8 @@ cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
     a.ni = ni;
     a.eps2 = eps2;
     a.wait_ns = g_wait_ns;
+    if (!set_fused_pred(a, cfg, p, fp))
+        return cudaErrorInvalidValue;
     const Variant &v = kVariants[cfg.variant];
     v.fn<<<cfg.grid, v.threads, v.smem, s>>>(a);
     return cudaGetLastError();
@@ -1762,7 +1918,7 @@ cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
 cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
                                const g6x_irec *d_irec, int ni, double eps2, void *part,
                                int *d_err, g6x_out *out, const int *jidx, unsigned *tcnt,
-                               cudaStream_t s)
+                               cudaStream_t s, const FusedPred *fp)
 {
     if (cfg.work <= 0)
         return cudaSuccess;
@@ -1788,6 +1944,8 @@ cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
     a.tcnt = tcnt;
     a.fused = 1;
     a.wait_ns = g_wait_ns;
+    if (!set_fused_pred(a, cfg, p, fp))
+        return cudaErrorInvalidValue;
     const Variant &v = kVariants[cfg.variant];
     v.fn<<<cfg.grid, v.threads, v.smem, s>>>(a);
     return cudaGetLastError();

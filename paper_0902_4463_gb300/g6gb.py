@@ -51,7 +51,7 @@ EXPORTS = [
     "g6x_autotune", "g6x_load_tuning", "g6x_clear_tuning", "g6x_get_predicted", "g6x_last_config",
     "g6x_launch_count", "g6x_set_wait_limit", "g6x_probe_wait_timeout", "g6x_set_timing", "g6x_get_timing", "g6h_correct_block", "g6h_create", "g6h_run", "g6h_get_state", "g6h_energy",
     "g6h_stats", "g6h_profile", "g6h_destroy", "g6h_checkpoint", "g6h_restore",
-    "g6h_set_neighbour_radius", "g6h_neighbour_stats",
+    "g6h_set_neighbour_radius", "g6h_neighbour_stats", "g6h_run_blocks",
     "g6x_batch_create", "g6x_batch_destroy", "g6x_batch_irecs", "g6x_batch_results",
     "g6x_batch_set_j", "g6x_batch_set_j_many", "g6x_batch_calc", "g6x_batch_launch_count",
     "g6x_batch_set_schedule", "g6x_batch_get_schedule", "g6x_batch_autotune", "g6hb_autotune",
@@ -112,6 +112,7 @@ def lib():
             "g6h_correct_block": (I, [I, D, P, P, D, D, D, P, P, P, P, P, P, P]),
             "g6h_create": (P, [I, I, P, P, P, D, D, D, D, D, P]),
             "g6h_run": (I, [P, D]),
+            "g6h_run_blocks": (C.c_longlong, [P, D, C.c_longlong]),
             "g6h_get_state": (I, [P, P, P, P, P, P, P]),
             "g6h_energy": (I, [P, P, P]),
             "g6h_stats": (I, [P, P, P, P]),
@@ -450,6 +451,14 @@ class G6HSim:
         _check(lib().g6h_neighbour_stats(self.h, *[C.byref(a) for a in v]),
                "g6h_neighbour_stats")
         return dict(lists=v[0].value, entries=v[1].value, overflowed=v[2].value)
+
+    def run_blocks(self, t_end, max_blocks):
+        """Advance at most max_blocks block steps toward t_end; returns the
+        number taken."""
+        r = lib().g6h_run_blocks(self.h, float(t_end), int(max_blocks))
+        if r < 0:
+            raise G6Error(int(r), "g6h_run_blocks")
+        return int(r)
 
     def checkpoint(self, path):
         return _check(lib().g6h_checkpoint(self.h, os.fsencode(path)), "g6h_checkpoint")

@@ -278,3 +278,50 @@ def test_force_kernel_timeout_path_leaves_the_context_usable(ctx, orc):
     oa, *_ = orc.force(x[act[:256]], v[act[:256]], act[:256], x, v, m, idx, eps2)
     ea = rel_err_vec(acc[:256], oa)
     assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5
+
+
+@pytest.mark.parametrize("fv,twin,m", [(17, 4, 16), (18, 14, 100), (19, 15, 256),
+                                       (20, 16, 1000)])
+def test_fused_prediction_is_identical_to_separate(ctx, orc, fv, twin, m):
+    # A force kernel that predicts its j-tiles itself (Eq. 1, Eq. 2 with the
+    # predictor's own arithmetic) gives bit-identical results to the separate
+    # predictor + force kernel of the same shape, also after j-updates
+    # between calls; both agree with the oracle.
+    n, eps2, t_blk = 50001, 1e-5, 0.375
+    st = ics.taylor_state(n, 21, t_blk)
+    load_j(ctx, st["x0"], st["v0"], st["m"], st["a0"], st["j0"], st["tj"])
+    act = np.sort(ics.permutation(n, 21)[:m])
+    xi, vi = st["x0"][act], st["v0"][act]
+
+    def run(v, t):
+        g6.g6x_set_variant(ctx, v, 0)
+        r = sweep(ctx, n, xi, vi, act, eps2, t)
+        assert g6.g6x_last_config(ctx)["variant"] == v
+        return r
+
+    try:
+        a = run(twin, t_blk)
+        b = run(fv, t_blk)
+        for u, w in zip(a, b):
+            assert np.array_equal(u, w)
+        # j-updates: new Taylor data for some particles, then the fused
+        # shape first (it stores the records and predicts itself)
+        q = ics.permutation(n, 5)[:777]
+        st["x0"][q] += 1e-3
+        st["tj"][q] = t_blk
+        g6.g6x_set_j_particles(ctx, q.astype(np.int32), q.astype(np.int32), st["tj"][q],
+                               st["m"][q], st["j0"][q] / 6.0, st["a0"][q] / 2.0, st["v0"][q],
+                               st["x0"][q])
+        t2 = t_blk + 2.0 ** -6
+        b2 = run(fv, t2)
+        a2 = run(twin, t2)
+        for u, w in zip(a2, b2):
+            assert np.array_equal(u, w)
+    finally:
+        g6.g6x_set_variant(ctx, -1, 0)
+    xp, vp = orc.predict(st["x0"], st["v0"], st["a0"], st["j0"], st["tj"], t2)
+    idx = np.arange(n)
+    oa, oj, op, onn, onr = orc.force(xi, vi, act, xp, vp, st["m"], idx, eps2)
+    ea = rel_err_vec(b2[0], oa)
+    assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5
+    check_nn(onn, onr, b2[3], xi, xp, idx)

@@ -315,3 +315,53 @@ def test_hermite_driver_reads_neighbour_lists(open_ctx):
     with pytest.raises(g6.G6Error):
         sim.set_neighbour_radius(-1.0)
     sim.close()
+
+
+def test_config2_force_errors_at_natural_block_steps(orc):
+    # Plummer N = 32768, eps2 = 1e-5, eta = 0.01: the DS driver runs to
+    # t = 1/4; at 20 points of the run its j-state (every particle at its own
+    # last block time, with its a and jerk) is taken as it is, and the next
+    # natural block (uneven size, 1 .. N) is evaluated both by the library
+    # (j predicted on the GPU) and by the oracle (j predicted in FP64), with
+    # the i-particles predicted on the host as the driver does.
+    from paper_0902_4463_gb300 import build
+    build.build()
+    n, eps2, eta, t_end = 32768, 1e-5, 0.01, 0.25
+    m, x, v = ics.plummer(n, 2)
+    idx = np.arange(n)
+    g6.g6x_open_ex(7, n, n)
+    g6.g6x_open_ex(8, n, n)
+    rows = []
+    try:
+        sim = g6.G6HSim(7, m, x, v, eps2, eta)
+        for snap in range(20):
+            if sim.run_blocks(t_end, 229 if snap else 1) == 0:
+                break
+            st = sim.state()
+            tn = st["t"] + st["dt"]
+            tb = tn.min()
+            act = np.where(tn == tb)[0]
+            h = (tb - st["t"][act])[:, None]
+            a0, j0 = st["acc"][act], st["jerk"][act]
+            xi = st["x"][act] + h * (st["v"][act] + h * (a0 / 2.0 + h * j0 / 6.0))
+            vi = st["v"][act] + h * (a0 + h * j0 / 2.0)
+            load_j(8, st["x"], st["v"], m, st["acc"], st["jerk"], st["t"])
+            acc, jerk, pot, nnb = sweep(8, n, xi, vi, act, eps2, tb)
+            xp, vp = orc.predict(st["x"], st["v"], st["acc"], st["jerk"], st["t"], tb)
+            oa, oj, op, onn, onr = orc.force(xi, vi, act, xp, vp, m, idx, eps2)
+            ea, ej = rel_err_vec(acc, oa), rel_err_vec(jerk, oj)
+            ep = np.abs(pot - op) / np.abs(op)
+            rows.append((float(tb), act.size, np.median(ea), ea.max(), np.median(ej), ej.max(),
+                         np.median(ep), float(np.mean(nnb == onn))))
+            assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5, rows[-1]
+            assert np.median(ej) <= 3e-6 and ej.max() <= 3e-4, rows[-1]
+            assert np.median(ep) <= 1e-6 and ep.max() <= 1e-5, rows[-1]
+            check_nn(onn, onr, nnb, xi, xp, idx)
+        sim.close()
+    finally:
+        g6.g6_close(7)
+        g6.g6_close(8)
+    assert len(rows) == 20 and len({r[1] for r in rows}) > 3     # uneven block sizes
+    print("\nconfig2 block errors (t, m, acc med, acc max, jerk med, jerk max, pot med, nn):")
+    for r in rows:
+        print("%.6f %6d %.2e %.2e %.2e %.2e %.2e %.4f" % r)
