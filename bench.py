@@ -380,6 +380,11 @@ def main():
     msds, phds, cds, _ = timed(m64, d_j64, d_i64, d_o64, 3, 2)
     rate64 = m64 * n / (ph64[2] / max(1, c64[2]) * 1e-3)
     rateds = m64 * n / (phds[2] / max(1, cds[2]) * 1e-3)
+    # accuracy ablation: separations by the full DS subtraction
+    g6.g6x_set_precision(CID, g6.G6X_PREC_DS_DSSUB)
+    _, phss, css, _ = timed(m64, d_j64, d_i64, d_o64, 3, 2)
+    g6.g6x_set_precision(CID, DS_MODE)
+    ratess = m64 * n / (phss[2] / max(1, css[2]) * 1e-3)
 
     sweep = None
     if args.sweep:
@@ -515,6 +520,9 @@ def main():
                      "gflops_60": rate64 * FLOPS_PER_PAIR / 1e9,
                      "ds_force_interactions_per_s_same_m": rateds,
                      "speedup_ds_over_fp64": rateds / rate64},
+            "ablation_full_ds_subtraction": {"m": m64, "force_interactions_per_s": ratess,
+                                             "eq3_force_interactions_per_s": rateds,
+                                             "eq3_speedup": rateds / ratess},
             "accuracy": accuracy,
             "cpu_baseline": cpu,
             "e2e": e2e,

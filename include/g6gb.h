@@ -20,6 +20,12 @@
  * Self-interaction is excluded by index: the j-particle whose `index` equals
  * the i-particle's index does not act on it.  Indices must be >= 0.
  *
+ * Host threads: the library's host loops over large blocks (i-record and
+ * j-record staging, sorting, copies of results, the drivers' prediction and
+ * correction, per-cluster batch work) run on one process-wide pool of
+ * G6GB_HOST_THREADS threads (default min(cores, 16)), started on first use;
+ * a loop that finds the pool busy (another caller) runs on its own thread.
+ *
  * Calling sequence (Sect. 2.1, Sect. 2.5; the same order as GRAPE-6):
  *   g6_open(cid);
  *   per block step:  g6_set_j_particle(...) for each particle corrected last
@@ -156,6 +162,12 @@ int g6_get_neighbour_list(int clusterid, int ipipe, int maxlength, int *nblen,
 #define G6X_PREC_FP64   1 /* all-FP64 prediction and force                 */
 #define G6X_PREC_DS_X64 2 /* as G6X_PREC_DS, but predicted positions are
                              formed in FP64 and then split into DS           */
+#define G6X_PREC_DS_DSSUB 3 /* as G6X_PREC_DS, but each separation by the full
+                             DS subtraction (TwoSum of the high parts, low
+                             parts added, one rounding: 9 FP32 operations
+                             instead of Eq. 3's 3), an accuracy ablation
+                             (Sect. 2.3); neighbour lists and the autotuner
+                             use the G6X_PREC_DS kernels                    */
 
 /* As g6_open with an explicit j capacity and i-per-call limit. */
 int g6x_open_ex(int clusterid, int nj_max, int ni_max);
@@ -178,7 +190,9 @@ typedef void (*g6x_free_fn)(void *ptr, void *user);
 int g6x_set_allocator(g6x_alloc_fn alloc, g6x_free_fn release, void *user);
 
 /* Bulk form of g6_set_j_particle for n particles (arrays of n entries;
- * j6, a2, v, x are n x 3).  Stops at the first error and returns it. */
+ * j6, a2, v, x are n x 3).  Calls with fewer than 8192 particles stop at
+ * the first error and return it; larger ones check every entry before
+ * staging any (and fill the records on host threads). */
 int g6x_set_j_particles(int clusterid, int n, const int address[],
                         const int index[], const double tj[],
                         const double mass[], const double j6[][3],
@@ -286,8 +300,11 @@ int g6x_get_timing(int clusterid, double ms[4], long long count[4]);
  * resident CTAs, against the nj j-particles in j-memory (i-particles taken
  * from the first m slots), and keep the fastest in a process-wide table that
  * later calculations without a pinned variant use.  Writes the table to
- * `path` when not NULL.  Synchronous; allocates two scratch buffers.
- * Returns the number of sizes tuned or a negative error. */
+ * `path` when not NULL.  Each candidate is timed as one step: prediction
+ * (inside the kernel for the fused-prediction shapes, which take part only
+ * with G6X_PREC_DS) + force + reduction.  Synchronous; allocates two
+ * scratch buffers.  Returns the number of sizes tuned or a negative error
+ * (G6_EINVAL under G6X_PREC_DS_DSSUB, which has no table). */
 int g6x_autotune(int clusterid, int nj, int m_max, const char *path);
 
 /* Load a table written by g6x_autotune (g6_open loads the file named by
@@ -427,9 +444,7 @@ g6h_sim *g6h_restore(int clusterid, const char *path, int *err);
  * (0 <= q < nj[k]); particle indices, self-exclusion and nearest neighbours
  * are per cluster.  Neighbour lists are not available on batches.
  * Threading: g6x_batch_set_j / _set_j_many calls for different clusters may
- * run concurrently; every other call on a batch takes it alone.  The batch
- * keeps a pool of host threads (G6GB_HOST_THREADS, default min(cores, 16))
- * for its per-cluster host work. */
+ * run concurrently; every other call on a batch takes it alone. */
 
 typedef struct g6x_batch g6x_batch;
 

@@ -5,12 +5,15 @@
 // per block time), launches and the copy back.  All arithmetic of the method
 // runs in the kernels of g6gb_kernels.cu; this file only moves data.
 #include "g6gb_internal.h"
+#include "g6gb_pool.h"
 
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <fstream>
+#include <memory>
 #include <mutex>
 #include <sstream>
 #include <string>
@@ -156,9 +159,31 @@ struct Ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[4];
     double t_ms[4] = {0, 0, 0, 0};
     long long t_cnt[4] = {0, 0, 0, 0};
+    // per-call marks that detect an address given twice to one bulk call,
+    // staging indices, and per-chunk tile counts of the parallel sort
+    std::vector<unsigned> stamp;
+    unsigned stamp_now = 0;
+    std::vector<int> sidx;
+    std::vector<int> cnt;                 // per worker chunk x tile counts
 };
 
 Ctx g_ctx[G6_MAX_CLUSTERS];
+
+// Host loops over at least this many particles run on the host threads.
+constexpr int PAR_MIN = 8192;
+constexpr int PAR_CHUNK = 4096;
+
+// f(k0, k1) over [0, n): serially for small n, else in chunks on the host threads.
+template <class F>
+void par_for(Ctx &, int n, const F &f)
+{
+    if (n < PAR_MIN) {
+        f(0, n);
+        return;
+    }
+    const int nch = (n + PAR_CHUNK - 1) / PAR_CHUNK;
+    g6::parallel_run(nch, [&](int i) { f(i * PAR_CHUNK, std::min(n, (i + 1) * PAR_CHUNK)); });
+}
 
 }  // namespace
 
@@ -410,6 +435,60 @@ int predict_if_stale(Ctx &c, int nj)
 // The GRAPE path's j-store update and prediction in one launch: the staged
 // records are counting-sorted by tile on the host into mapped memory, and
 // each predictor CTA stores its tile's records before predicting the tile.
+// Counting sort of the staged records by j-tile into the mapped buffer,
+// with the per-tile ranges in h_toff; large batches in parallel chunks
+// (per-chunk counts, one prefix pass, per-chunk scatter -- the same order
+// within a tile as the serial sort).  False if out of memory.
+bool sort_by_tile(Ctx &c, int ntiles)
+{
+    const int n = c.n_jst;
+    g6::HostPool *pool = n < PAR_MIN ? nullptr : g6::shared_pool();
+    if (!pool) {
+        try {
+            c.tcur.assign(ntiles + 1, 0);
+        } catch (...) {
+            return false;
+        }
+        for (int k = 0; k < n; ++k)
+            ++c.tcur[c.h_jst[k].address / JT + 1];
+        for (int tl = 0; tl < ntiles; ++tl)
+            c.tcur[tl + 1] += c.tcur[tl];
+        std::memcpy(c.h_toff, c.tcur.data(), sizeof(int) * (ntiles + 1));
+        for (int k = 0; k < n; ++k)
+            c.h_jsort[c.tcur[c.h_jst[k].address / JT]++] = c.h_jst[k];
+        return true;
+    }
+    const int nch = std::min(2 * pool->size(), (n + PAR_CHUNK - 1) / PAR_CHUNK);
+    const int per = (n + nch - 1) / nch;
+    try {
+        c.cnt.assign((size_t)nch * ntiles, 0);
+    } catch (...) {
+        return false;
+    }
+    int *cnt = c.cnt.data();
+    g6::parallel_run(nch, [&](int i) {
+        int *ci = cnt + (size_t)i * ntiles;
+        for (int k = i * per, ke = std::min(n, (i + 1) * per); k < ke; ++k)
+            ++ci[c.h_jst[k].address / JT];
+    });
+    int run = 0;
+    for (int tl = 0; tl < ntiles; ++tl) {
+        c.h_toff[tl] = run;
+        for (int i = 0; i < nch; ++i) {
+            const int v = cnt[(size_t)i * ntiles + tl];
+            cnt[(size_t)i * ntiles + tl] = run;
+            run += v;
+        }
+    }
+    c.h_toff[ntiles] = run;
+    g6::parallel_run(nch, [&](int i) {
+        int *ci = cnt + (size_t)i * ntiles;
+        for (int k = i * per, ke = std::min(n, (i + 1) * per); k < ke; ++k)
+            c.h_jsort[ci[c.h_jst[k].address / JT]++] = c.h_jst[k];
+    });
+    return true;
+}
+
 // predict = false: only store the staged records (for a force kernel that
 // predicts the j-tiles itself); every cached prediction is then stale.
 int update_and_predict(Ctx &c, int nj, bool predict = true)
@@ -454,18 +533,8 @@ int update_and_predict(Ctx &c, int nj, bool predict = true)
         c.d_toff = (int *)d;
         c.toff_cap = cap;
     }
-    try {
-        c.tcur.assign(ntiles_all + 1, 0);
-    } catch (...) {
+    if (!sort_by_tile(c, ntiles_all))
         return G6_ENOMEM;
-    }
-    for (int k = 0; k < c.n_jst; ++k)
-        ++c.tcur[c.h_jst[k].address / JT + 1];
-    for (int tl = 0; tl < ntiles_all; ++tl)
-        c.tcur[tl + 1] += c.tcur[tl];
-    std::memcpy(c.h_toff, c.tcur.data(), sizeof(int) * (ntiles_all + 1));
-    for (int k = 0; k < c.n_jst; ++k)
-        c.h_jsort[c.tcur[c.h_jst[k].address / JT]++] = c.h_jst[k];
     const int kind = c.pmode == G6X_PREC_FP64 ? g6::PRED_FP64
                      : c.pmode == G6X_PREC_DS_X64 ? g6::PRED_DS_X64 : g6::PRED_DS;
     cudaError_t e;
@@ -480,8 +549,10 @@ int update_and_predict(Ctx &c, int nj, bool predict = true)
         return cuda_err(e);
     c.launches += 1;
     c.jsort_inflight = true;
-    for (int k = 0; k < c.n_jst; ++k)
-        c.slot_of[c.h_jst[k].address] = -1;
+    par_for(c, c.n_jst, [&](int k0, int k1) {
+        for (int k = k0; k < k1; ++k)
+            c.slot_of[c.h_jst[k].address] = -1;
+    });
     c.n_jst = 0;
     c.ver += 1;
     if (!predict)
@@ -558,14 +629,10 @@ int predict_and_force(Ctx &c, int nj, int ni, const g6x_irec *d_irec, double eps
 int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_irec,
               double eps2, g6x_out *d_out)
 {
+    // fused-prediction shapes read the j-store itself (the predicted tiles
+    // and their cache entry are left as they are)
     const g6::FusedPred fpa{c.js, c.t_set, nj};
-    const bool fp = g6::variant_info(cfg.variant).fpred != 0;
-    const g6::FusedPred *fpp = fp ? &fpa : nullptr;
-    if (fp) {
-        // the kernel rewrites predicted tiles (not their index ranges)
-        for (int k = 0; k < 3; ++k)
-            c.ver_pred[k] = -1;
-    }
+    const g6::FusedPred *fpp = g6::variant_info(cfg.variant).fpred ? &fpa : nullptr;
     size_t slots = g6::partial_slots(cfg);
     int rc = grow_dev(c.d_part, c.part_cap, slots);
     if (rc)
@@ -780,10 +847,11 @@ int g6x_set_precision(int cid, int mode)
     Ctx *c = get(cid, &err);
     if (!c)
         return err;
-    if (mode != G6X_PREC_DS && mode != G6X_PREC_FP64 && mode != G6X_PREC_DS_X64)
+    if (mode != G6X_PREC_DS && mode != G6X_PREC_FP64 && mode != G6X_PREC_DS_X64
+        && mode != G6X_PREC_DS_DSSUB)
         return G6_EINVAL;
     c->pmode = mode;
-    c->prec = mode == G6X_PREC_FP64 ? G6X_PREC_FP64 : G6X_PREC_DS;
+    c->prec = mode == G6X_PREC_FP64 || mode == G6X_PREC_DS_DSSUB ? mode : G6X_PREC_DS;
     return 0;
 }
 
@@ -903,23 +971,30 @@ void g6calc_firsthalf(int cid, int nj, int ni, const int index[],
         return;
     }
     int rc = ensure_io(*c, ni);
-    bool list = false;
-    for (int k = 0; !rc && k < ni; ++k) {
-        if (index[k] < 0) {
-            rc = G6_EINVAL;
-            break;
-        }
-        g6x_irec &r = c->h_irec[k];
-        for (int d = 0; d < 3; ++d) {
-            r.x[d] = xi[k][d];
-            r.v[d] = vi[k][d];
-        }
-        r.h2 = h2 ? h2[k] : 0.0;
-        r.index = index[k];
-        r.pad = 0;
-        if (h2 && h2[k] > 0.0)
-            list = true;
-    }
+    std::atomic<int> bad{0}, any_list{0};
+    if (!rc)
+        par_for(*c, ni, [&](int k0, int k1) {
+            int b = 0, l = 0;
+            for (int k = k0; k < k1; ++k) {
+                g6x_irec &r = c->h_irec[k];
+                for (int d = 0; d < 3; ++d) {
+                    r.x[d] = xi[k][d];
+                    r.v[d] = vi[k][d];
+                }
+                r.h2 = h2 ? h2[k] : 0.0;
+                r.index = index[k];
+                r.pad = 0;
+                b |= index[k] < 0;
+                l |= h2 && h2[k] > 0.0;
+            }
+            if (b)
+                bad.store(1);
+            if (l)
+                any_list.store(1);
+        });
+    if (!rc && bad.load())
+        rc = G6_EINVAL;
+    const bool list = any_list.load() != 0;
     // the kernels read the i-records from, and write results to, the mapped
     // host buffers: no separate copies
     if (!rc)
@@ -966,19 +1041,21 @@ static int lasthalf_common(int cid, int nj, int ni, double acc[][3], double jerk
         c->tcnt_dirty = true;
         return code < 0 ? code : G6_EIO;
     }
-    for (int k = 0; k < ni; ++k) {
-        const g6x_out &o = c->h_out[k];
-        for (int d = 0; d < 3; ++d) {
-            if (acc)
-                acc[k][d] = o.acc[d];
-            if (jerk)
-                jerk[k][d] = o.jerk[d];
+    par_for(*c, ni, [&](int k0, int k1) {
+        for (int k = k0; k < k1; ++k) {
+            const g6x_out &o = c->h_out[k];
+            for (int d = 0; d < 3; ++d) {
+                if (acc)
+                    acc[k][d] = o.acc[d];
+                if (jerk)
+                    jerk[k][d] = o.jerk[d];
+            }
+            if (pot)
+                pot[k] = o.pot;
+            if (nnb)
+                nnb[k] = o.nnb;
         }
-        if (pot)
-            pot[k] = o.pot;
-        if (nnb)
-            nnb[k] = o.nnb;
-    }
+    });
     return 0;
 }
 
@@ -1066,12 +1143,75 @@ int g6x_set_j_particles(int cid, int n, const int address[], const int index[],
         if (rc)
             return rc;
     }
-    for (int k = 0; k < n; ++k) {
-        int rc = g6_set_j_particle(cid, address[k], index[k], tj[k], 0.0, mass[k], nullptr,
-                                   j6[k], a2[k], v[k], x[k]);
-        if (rc)
-            return rc;
+    if (n < PAR_MIN) {
+        for (int k = 0; k < n; ++k) {
+            int rc = g6_set_j_particle(cid, address[k], index[k], tj[k], 0.0, mass[k], nullptr,
+                                       j6[k], a2[k], v[k], x[k]);
+            if (rc)
+                return rc;
+        }
+        return 0;
     }
+    // large calls: check everything, give every address its staging record
+    // (in order, so an address given twice keeps its last values), then fill
+    // the records on the pool
+    for (int k = 0; k < n; ++k)
+        if (address[k] < 0 || address[k] >= c->cap || index[k] < 0)
+            return G6_EINVAL;
+    if (c->jst_inflight) {             // staging may still be read by the GPU
+        if (cudaEventQuery(c->ev_jst) != cudaSuccess)
+            cudaEventSynchronize(c->ev_jst);
+        cudaGetLastError();
+        c->jst_inflight = false;
+    }
+    try {
+        c->sidx.resize(n);
+        if (c->stamp.size() < (size_t)c->jst_cap)
+            c->stamp.resize(c->jst_cap, 0);
+    } catch (...) {
+        return G6_ENOMEM;
+    }
+    if (++c->stamp_now == 0) {
+        std::fill(c->stamp.begin(), c->stamp.end(), 0u);
+        c->stamp_now = 1;
+    }
+    bool twice = false;
+    for (int k = 0; k < n; ++k) {
+        int slot = c->slot_of[address[k]];
+        if (slot < 0) {
+            if (c->n_jst + 1 > c->jst_cap) {
+                int rc = ensure_jstage(*c, c->n_jst + 1);
+                if (rc)
+                    return rc;
+                if (c->stamp.size() < (size_t)c->jst_cap)
+                    c->stamp.resize(c->jst_cap, 0);
+            }
+            slot = c->n_jst++;
+            c->slot_of[address[k]] = slot;
+        }
+        twice |= c->stamp[slot] == c->stamp_now;
+        c->stamp[slot] = c->stamp_now;
+        c->sidx[k] = slot;
+    }
+    auto fill = [&](int k0, int k1) {
+        for (int k = k0; k < k1; ++k) {
+            g6x_jrec &r = c->h_jst[c->sidx[k]];
+            for (int d = 0; d < 3; ++d) {
+                r.x[d] = x[k][d];
+                r.v[d] = v[k][d];
+                r.a2[d] = a2[k][d];
+                r.j6[d] = j6[k][d];
+            }
+            r.mass = mass[k];
+            r.tj = tj[k];
+            r.address = address[k];
+            r.index = index[k];
+        }
+    };
+    if (twice)
+        fill(0, n);                    // in order: the last values win
+    else
+        par_for(*c, n, fill);
     return 0;
 }
 
@@ -1246,7 +1386,7 @@ extern "C" int g6x_autotune(int cid, int nj, int m_max, const char *path)
     Ctx *c = get(cid, &err);
     if (!c)
         return err;
-    if (c->pending || nj < 1 || nj > c->cap || m_max < 16)
+    if (c->pending || nj < 1 || nj > c->cap || m_max < 16 || c->prec > G6X_PREC_FP64)
         return G6_EINVAL;
     if (m_max > nj)
         m_max = nj;
@@ -1445,7 +1585,7 @@ int g6x_get_predicted(int cid, int nj, float *hi, float *lo, float *vel, double 
         return rc;
     cudaError_t e = cudaSuccess;
     size_t d4 = sizeof(double4_32a) * (size_t)nj;
-    if (c->prec == G6X_PREC_DS) {
+    if (c->prec != G6X_PREC_FP64) {
         // copy the tiled layout back and unpack it into (x, y, z, w) rows
         const int ntile = (nj + JT - 1) / JT;
         std::vector<float> t((size_t)ntile * JT * g6::JW);

@@ -24,7 +24,7 @@
 // The C++ batch driver (g6hb_*) runs a Hermite block-time-step integration in
 // every cluster with its own block scheduler, advancing each cluster by one
 // of its own block steps per batch step; the per-cluster host work (i
-// prediction, correction, staging) runs on a small pool of host threads.
+// prediction, correction, staging) runs on the library's host threads.
 #include "g6gb_internal.h"
 #include "g6gb_pool.h"
 
@@ -44,9 +44,7 @@
 #include <vector>
 
 using g6::BatchGT;
-using g6::HostPool;
 using g6::JT;
-using g6::host_threads;
 
 namespace {
 
@@ -102,7 +100,6 @@ struct g6x_batch {
     bool timing = false;
     double gpu_ms = 0.0;
     long long timed = 0;
-    HostPool *pool = nullptr;
 };
 
 namespace {
@@ -182,7 +179,6 @@ void free_batch(g6x_batch *b)
         cudaStreamDestroy(b->stream);
     if (b->stream2)
         cudaStreamDestroy(b->stream2);
-    delete b->pool;
     delete b;
 }
 
@@ -308,7 +304,7 @@ void stage_sorted(g6x_batch *b)
         b->base[k] = total;
         total += (int)b->stage[k].size();
     }
-    b->pool->run(b->ncl, [b](int k) {
+    g6::parallel_run(b->ncl, [b](int k) {
         const int t0 = b->jtile[k], nt = b->ntile[k];
         int *off = b->h_toff + t0;
         std::vector<g6x_jrec> &st = b->stage[k];
@@ -595,7 +591,6 @@ g6x_batch *g6x_batch_create(int ncl, const int nj[], int precision, int variant,
     b->ncl = ncl;
     b->pmode = precision;
     try {
-        b->pool = new HostPool(host_threads());
         b->nj.assign(nj, nj + ncl);
         b->jtile.resize(ncl);
         b->ntile.resize(ncl);
@@ -1229,8 +1224,7 @@ int g6hb_step(g6hb_sim *s, double t_end)
     if (!s)
         return G6_EINVAL;
     auto w0 = std::chrono::steady_clock::now();
-    HostPool &pool = *s->b->pool;
-    pool.run(s->ncl, [s, t_end](int k) { hb_pop(*s, k, t_end); });
+    g6::parallel_run(s->ncl, [s, t_end](int k) { hb_pop(*s, k, t_end); });
     int stepping = 0;
     s->chunks.clear();
     for (int k = 0; k < s->ncl; ++k)
@@ -1244,7 +1238,7 @@ int g6hb_step(g6hb_sim *s, double t_end)
     if (stepping == 0)
         return 0;
     const int nch = (int)s->chunks.size();
-    pool.run(nch, [s](int c) { hb_predict(*s, s->chunks[c]); });
+    g6::parallel_run(nch, [s](int c) { hb_predict(*s, s->chunks[c]); });
     std::memcpy(&s->hist[(size_t)s->hist_pos * s->ncl], s->ni.data(), sizeof(int) * s->ncl);
     s->hist_pos = (s->hist_pos + 1) % HIST;
     s->hist_n = std::min(s->hist_n + 1, HIST);
@@ -1265,13 +1259,13 @@ int g6hb_step(g6hb_sim *s, double t_end)
     } catch (...) {
         return G6_ENOMEM;
     }
-    pool.run(nch, [s](int c) { s->crc[c] = hb_correct(*s, s->chunks[c]); });
+    g6::parallel_run(nch, [s](int c) { s->crc[c] = hb_correct(*s, s->chunks[c]); });
     for (int c = 0; c < nch; ++c)
         if (s->crc[c]) {
             hb_unstage(*s);
             return s->crc[c];
         }
-    pool.run(s->ncl, [s](int k) { s->rc[k] = hb_file(*s, k); });
+    g6::parallel_run(s->ncl, [s](int k) { s->rc[k] = hb_file(*s, k); });
     for (int k = 0; k < s->ncl; ++k)
         if (s->rc[k])
             return s->rc[k];

@@ -18,7 +18,9 @@
 #include <string>
 #include <vector>
 
+#include <atomic>
 #include <memory>
+#include <mutex>
 
 #include "g6gb.h"
 #include "g6gb_pool.h"
@@ -48,7 +50,6 @@ struct g6h_sim {
     long long nb_lists = 0, nb_entries = 0, nb_overflowed = 0;
     // host threads for the per-particle work of a block, and the block's
     // j-records for one bulk update (tj, mass, a/2, j/6 per active particle)
-    std::unique_ptr<g6::HostPool> pool;
     std::vector<double> tjb, mb, a2b, j6b;
     std::vector<int> crc;
 };
@@ -159,7 +160,7 @@ double quantise(double dt, double req, double t, double dt_max)
 // Particles per host work item of a block.
 constexpr int CHUNK = 64;
 
-// Per-block work arrays and the host thread pool of a driver of n particles.
+// Per-block work arrays of a driver of n particles.
 int alloc_block_work(g6h_sim &s)
 {
     try {
@@ -169,7 +170,6 @@ int alloc_block_work(g6h_sim &s)
         s.a2b.resize(3 * n);
         s.j6b.resize(3 * n);
         s.crc.resize((n + CHUNK - 1) / CHUNK);
-        s.pool.reset(new g6::HostPool(n > CHUNK ? g6::host_threads() : 1));
     } catch (...) {
         return G6_ENOMEM;
     }
@@ -186,23 +186,33 @@ int g6h_correct_block(int n, double t_blk, const double *t0, const double *dt, d
 {
     if (n < 0 || (n > 0 && (!t0 || !dt || !xp || !vp || !a0 || !j0 || !a1 || !j1 || !dt_new)))
         return G6_EINVAL;
-    int small = 0;
-    for (int k = 0; k < n; ++k) {
-        const double h = t_blk - t0[k];
-        double d2[3], d3[3], d2e[3];
-        correct(h, &a0[3 * k], &j0[3 * k], &a1[3 * k], &j1[3 * k], &xp[3 * k], &vp[3 * k], d2,
-                d3);
-        for (int d = 0; d < 3; ++d)
-            d2e[d] = d2[d] + h * d3[d];
-        const double req = aarseth(&a1[3 * k], &j1[3 * k], d2e, d3, eta);
-        double nd = quantise(dt[k], req, t_blk, dt_max);
-        if (!(nd >= dt_min)) {
-            nd = -1.0;
-            ++small;
+    auto block = [=](int k0, int k1) -> int {
+        int small = 0;
+        for (int k = k0; k < k1; ++k) {
+            const double h = t_blk - t0[k];
+            double d2[3], d3[3], d2e[3];
+            correct(h, &a0[3 * k], &j0[3 * k], &a1[3 * k], &j1[3 * k], &xp[3 * k], &vp[3 * k],
+                    d2, d3);
+            for (int d = 0; d < 3; ++d)
+                d2e[d] = d2[d] + h * d3[d];
+            const double req = aarseth(&a1[3 * k], &j1[3 * k], d2e, d3, eta);
+            double nd = quantise(dt[k], req, t_blk, dt_max);
+            if (!(nd >= dt_min)) {
+                nd = -1.0;
+                ++small;
+            }
+            dt_new[k] = nd;
         }
-        dt_new[k] = nd;
-    }
-    return small;
+        return small;
+    };
+    // large blocks on the process-wide host threads
+    constexpr int BIG = 8192, PART = 4096;
+    if (n < BIG)
+        return block(0, n);
+    const int nch = (n + PART - 1) / PART;
+    std::atomic<int> small{0};
+    g6::parallel_run(nch, [&](int i) { small += block(i * PART, std::min(n, (i + 1) * PART)); });
+    return small.load();
 }
 
 g6h_sim *g6h_create(int cid, int n, const double *m, const double *x, const double *v,
@@ -312,7 +322,7 @@ long long g6h_run_blocks(g6h_sim *s, double t_end, long long max_blocks)
         const int na = (int)s->act.size();
         const int nch = (na + CHUNK - 1) / CHUNK;
         // host prediction of the active i-particles (Eq. 1, Eq. 2)
-        s->pool->run(nch, [s, tb, na](int c) {
+        g6::parallel_run(nch, [s, tb, na](int c) {
             for (int q = c * CHUNK, qe = std::min(na, q + CHUNK); q < qe; ++q) {
                 const int k = s->act[q];
                 const double h = tb - s->t[k];
@@ -334,7 +344,7 @@ long long g6h_run_blocks(g6h_sim *s, double t_end, long long max_blocks)
             return rc;
         double w2 = now_s();
         // correct, choose the next steps and fill the block's j-records
-        s->pool->run(nch, [s, tb, na](int c) {
+        g6::parallel_run(nch, [s, tb, na](int c) {
             int small = 0;
             for (int q = c * CHUNK, qe = std::min(na, q + CHUNK); q < qe; ++q) {
                 const int k = s->act[q];

@@ -36,6 +36,7 @@ namespace g6 {
 namespace {
 
 constexpr int NSTAGE = 3;
+constexpr int FP_NSTAGE = 2;        // raw-tile stages of the fused-prediction kernels
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s per mbarrier wait
 
 // One j-tile of the raw j-store arrays as staged by the force kernel with
@@ -278,21 +279,28 @@ __device__ __forceinline__ void tile_index_range(int *s_lo, int *s_hi, int id, b
 // the paper's form (Sect. 2.2) -- Taylor increment dt (v + dt (a/2 + dt j/6))
 // in FP32, added to the double-single x0 by the DS + SP addition, velocity in
 // FP32; only dt = t - t0 is formed in FP64 (block times are exact there).
+// The DS position part of Eq. 1 (hi, lo per component).
+__device__ __forceinline__ void predict_ds_pos(float h, float4 xa, float2 xb, float4 v,
+                                               float4 a, float4 j, float *hi, float *lo)
+{
+    ds_add_f(xa.x, xa.w, h * fmaf(h, fmaf(h, j.x, a.x), v.x), hi[0], lo[0]);
+    ds_add_f(xa.y, xb.x, h * fmaf(h, fmaf(h, j.y, a.y), v.y), hi[1], lo[1]);
+    ds_add_f(xa.z, xb.y, h * fmaf(h, fmaf(h, j.z, a.z), v.z), hi[2], lo[2]);
+}
+
 __device__ __forceinline__ void predict_ds_vals(float h, float4 xa, float2 xb, float4 v,
                                                 float4 a, float4 j, int id, float *o)
 {
-    float hx, lx, hy, ly, hz, lz;
-    ds_add_f(xa.x, xa.w, h * fmaf(h, fmaf(h, j.x, a.x), v.x), hx, lx);
-    ds_add_f(xa.y, xb.x, h * fmaf(h, fmaf(h, j.y, a.y), v.y), hy, ly);
-    ds_add_f(xa.z, xb.y, h * fmaf(h, fmaf(h, j.z, a.z), v.z), hz, lz);
+    float hi[3], lo[3];
+    predict_ds_pos(h, xa, xb, v, a, j, hi, lo);
     const float h3 = 3.0f * h;
-    o[W_XH * JT] = hx;
-    o[W_YH * JT] = hy;
-    o[W_ZH * JT] = hz;
+    o[W_XH * JT] = hi[0];
+    o[W_YH * JT] = hi[1];
+    o[W_ZH * JT] = hi[2];
     o[W_M * JT] = v.w;
-    o[W_XL * JT] = lx;
-    o[W_YL * JT] = ly;
-    o[W_ZL * JT] = lz;
+    o[W_XL * JT] = lo[0];
+    o[W_YL * JT] = lo[1];
+    o[W_ZL * JT] = lo[2];
     o[W_VX * JT] = fmaf(h, fmaf(h3, j.x, 2.0f * a.x), v.x);
     o[W_VY * JT] = fmaf(h, fmaf(h3, j.y, 2.0f * a.y), v.y);
     o[W_VZ * JT] = fmaf(h, fmaf(h3, j.z, 2.0f * a.z), v.z);
@@ -446,6 +454,28 @@ __global__ void __launch_bounds__(JT) k_predict_batch(JStore js, Pred p, BatchPr
     }
 }
 
+// Separation of two DS positions by the full DS subtraction (the accuracy
+// ablation of Sect. 2.3): TwoSum of the high parts, the low parts added to
+// its error, one final rounding -- nine FP32 operations against the three
+// of Eq. 3.  nh, nl are the negated high and low parts of x_i.
+__device__ __forceinline__ float ds_sep1(float h, float l, float nh, float nl)
+{
+    const float s = __fadd_rn(h, nh);
+    const float bb = __fsub_rn(s, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(nh, bb));
+    return __fadd_rn(s, __fadd_rn(e, __fadd_rn(l, nl)));
+}
+
+__device__ __forceinline__ float2 ds_sep2(float2 h, float2 l, float2 nh, float2 nl)
+{
+    const float2 s = __fadd2_rn(h, nh);
+    const float2 bb = __fadd2_rn(s, make_float2(-h.x, -h.y));
+    const float2 sb = __fadd2_rn(s, make_float2(-bb.x, -bb.y));
+    const float2 e = __fadd2_rn(__fadd2_rn(h, make_float2(-sb.x, -sb.y)),
+                                __fadd2_rn(nh, make_float2(-bb.x, -bb.y)));
+    return __fadd2_rn(s, __fadd2_rn(e, __fadd2_rn(l, nl)));
+}
+
 // ----------------------------------------------------------------- K2 ---
 
 struct ForceArgs {
@@ -468,12 +498,11 @@ struct ForceArgs {
     int fused;
     BatchTables bt;                   // batch geometry (batch kernels only)
     unsigned long long wait_ns;       // limit of each wait for a staged tile
-    // prediction inside the force kernel: the j-store, the block time, the
-    // number of particles in j-memory, and where the predicted tiles go
+    // prediction inside the force kernel: the j-store, the block time and
+    // the number of particles in j-memory
     JStore js;
     double t_pred;
     int nj;
-    float *pt_w;
 };
 
 // Pair forces in FP32 with the DS separation of Eq. 3 (Sect. 2.3).  Per pair:
@@ -502,7 +531,7 @@ struct ForceArgs {
 // rounding does not grow with n; the pairs are combined in FP64 when
 // partials are written.
 template <int TI, int TJ, int NI, bool LIST, int MINB = 1, int UNR = 2, bool BATCH = false,
-          bool FP = false>
+          bool FP = false, bool DSS = false>
 __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
 {
     static_assert(!(LIST && BATCH), "batches carry no neighbour lists");
@@ -515,16 +544,17 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     // FP: a stage holds one tile of the raw j-store arrays (RAW_* offsets),
     // predicted by the CTA into pbuf before the pair loop
     constexpr unsigned STAGE_BYTES = FP ? RAW_TILE_BYTES : TILE_BYTES;
+    constexpr int NS = FP ? FP_NSTAGE : NSTAGE;         // stages in the ring
     static_assert(!LIST || TJ == 1, "neighbour lists need whole j-tiles per thread");
     static_assert(JT % (2 * TJ) == 0, "j-tile must split into j-pairs evenly");
 
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     float *stage_buf = reinterpret_cast<float *>(dyn_smem);
-    float *pbuf = reinterpret_cast<float *>(dyn_smem + NSTAGE * STAGE_BYTES);    // FP only
-    float2 *comp = reinterpret_cast<float2 *>(dyn_smem + NSTAGE * STAGE_BYTES
+    float *pbuf = reinterpret_cast<float *>(dyn_smem + NS * STAGE_BYTES);    // FP only
+    float2 *comp = reinterpret_cast<float2 *>(dyn_smem + NS * STAGE_BYTES
                                               + (FP ? TILE_BYTES : 0));         // [NI][7][NT]
     __shared__ int s_wlo[FP ? NT / 32 : 1], s_whi[FP ? NT / 32 : 1];
-    __shared__ __align__(8) uint64_t bar[NSTAGE];
+    __shared__ __align__(8) uint64_t bar[NS];
     __shared__ int s_abort;
     __shared__ float s_nnr[TJ > 1 ? NI * NT : 1];
     __shared__ int s_nnj[TJ > 1 ? NI * NT : 1];
@@ -590,7 +620,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         return;
 
     if (tid == 0) {
-        for (int s = 0; s < NSTAGE; ++s)
+        for (int s = 0; s < NS; ++s)
             mbar_init(&bar[s], 1);
         fence_barrier_init();
         s_abort = 0;
@@ -603,7 +633,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         while (g_start(issue_g + 1) <= p)
             ++issue_g;
         const int jt = jt_of(p, issue_g);
-        int s = q % NSTAGE;
+        int s = q % NS;
         if constexpr (FP) {
             unsigned char *d = dyn_smem + (size_t)s * RAW_TILE_BYTES;
             const size_t j0 = (size_t)jt * JT;
@@ -623,9 +653,8 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     };
 
     // FP: Eq. 1 and Eq. 2 for the staged raw tile jt (stage s) into pbuf, with
-    // the arithmetic of K1 (bit-identical tiles); the tile is also written to
-    // the predicted-tile buffer for the nearest-neighbour rescan, and each
-    // warp's range of particle indices goes to s_wlo/s_whi.
+    // the arithmetic of K1 (bit-identical tiles); each warp's range of
+    // particle indices goes to s_wlo/s_whi.
     auto predict_tile = [&](int s, int jt) {
         const unsigned char *d = dyn_smem + (size_t)s * RAW_TILE_BYTES;
         const double *T0 = reinterpret_cast<const double *>(d + RAW_T0);
@@ -649,10 +678,6 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
             } else {
                 far_slot_ds(o);
             }
-            float *g = a.pt_w + (size_t)jt * JW * JT + jj;
-#pragma unroll
-            for (int w = 0; w < JW; ++w)
-                g[w * JT] = o[w * JT];
         }
         lo = __reduce_min_sync(0xffffffffu, lo);
         hi = __reduce_max_sync(0xffffffffu, hi);
@@ -662,7 +687,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         }
     };
     if (tid == 0)
-        for (int q = 0; q < NSTAGE && q < ntile; ++q)
+        for (int q = 0; q < NS && q < ntile; ++q)
             issue(q);
 
     float2 eps2 = make_float2((float)a.eps2, (float)a.eps2);
@@ -793,13 +818,6 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         if (!(nnr[k] < INF) || nnt[k] < 0)
             return -1;
         const float *T = a.pt + (size_t)nnt[k] * JW * JT;
-        // FP wrote these tiles in this launch: read them through L2
-        auto ld = [](const float *q) -> float {
-            if constexpr (FP)
-                return __ldcg(q);
-            else
-                return __ldg(q);
-        };
         constexpr int CH = 4;                       // j-pairs per chunk
         for (int kk0 = 0; kk0 < PPT; kk0 += CH) {
             float key[2 * CH];
@@ -811,15 +829,36 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                     const int jj = 2 * (tj + kk * TJ) + h;
                     float r2u = INF;
                     int id = -1;
-                    if (kk < PPT) {
-                        const float dx = __fadd_rn(__fadd_rn(ld(T + W_XH * JT + jj), nxh[k][0].x),
-                                                   __fadd_rn(ld(T + W_XL * JT + jj), nxl[k][0].x));
-                        const float dy = __fadd_rn(__fadd_rn(ld(T + W_YH * JT + jj), nxh[k][1].x),
-                                                   __fadd_rn(ld(T + W_YL * JT + jj), nxl[k][1].x));
-                        const float dz = __fadd_rn(__fadd_rn(ld(T + W_ZH * JT + jj), nxh[k][2].x),
-                                                   __fadd_rn(ld(T + W_ZL * JT + jj), nxl[k][2].x));
-                        r2u = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-                        id = __float_as_int(ld(T + W_ID * JT + jj));
+                    // FP: the tile was never stored; predict this j again
+                    // with the same arithmetic (empty slots cannot win)
+                    const int slot = nnt[k] * JT + jj;
+                    if (kk < PPT && (!FP || slot < a.nj)) {
+                        float ph[3], pl[3];
+                        if constexpr (FP) {
+                            const float hh = (float)(a.t_pred - a.js.t0[slot]);
+                            predict_ds_pos(hh, a.js.xds[slot], a.js.xds2[slot], a.js.v0m[slot],
+                                           a.js.a2f[slot], a.js.j6f[slot], ph, pl);
+                            id = a.js.idx[slot];
+                        } else {
+                            ph[0] = __ldg(T + W_XH * JT + jj);
+                            ph[1] = __ldg(T + W_YH * JT + jj);
+                            ph[2] = __ldg(T + W_ZH * JT + jj);
+                            pl[0] = __ldg(T + W_XL * JT + jj);
+                            pl[1] = __ldg(T + W_YL * JT + jj);
+                            pl[2] = __ldg(T + W_ZL * JT + jj);
+                            id = __float_as_int(__ldg(T + W_ID * JT + jj));
+                        }
+                        // the loop's own separation arithmetic, lane by lane
+                        float dd[3];
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            if constexpr (DSS)
+                                dd[d] = ds_sep1(ph[d], pl[d], nxh[k][d].x, nxl[k][d].x);
+                            else
+                                dd[d] = __fadd_rn(__fadd_rn(ph[d], nxh[k][d].x),
+                                                  __fadd_rn(pl[d], nxl[k][d].x));
+                        }
+                        r2u = __fmaf_rn(dd[2], dd[2], __fmaf_rn(dd[1], dd[1], __fmul_rn(dd[0], dd[0])));
                     }
                     key[2 * u + h] = (id == iid[k]) ? INF : r2u;
                 }
@@ -1028,9 +1067,16 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                 id = ID[jp];
 #pragma unroll
             for (int k = 0; k < NI; ++k) {
-                const float2 dx = __fadd2_rn(__fadd2_rn(xh, nxh[k][0]), __fadd2_rn(xl, nxl[k][0]));
-                const float2 dy = __fadd2_rn(__fadd2_rn(yh, nxh[k][1]), __fadd2_rn(yl, nxl[k][1]));
-                const float2 dz = __fadd2_rn(__fadd2_rn(zh, nxh[k][2]), __fadd2_rn(zl, nxl[k][2]));
+                float2 dx, dy, dz;
+                if constexpr (DSS) {
+                    dx = ds_sep2(xh, xl, nxh[k][0], nxl[k][0]);
+                    dy = ds_sep2(yh, yl, nxh[k][1], nxl[k][1]);
+                    dz = ds_sep2(zh, zl, nxh[k][2], nxl[k][2]);
+                } else {
+                    dx = __fadd2_rn(__fadd2_rn(xh, nxh[k][0]), __fadd2_rn(xl, nxl[k][0]));
+                    dy = __fadd2_rn(__fadd2_rn(yh, nxh[k][1]), __fadd2_rn(yl, nxl[k][1]));
+                    dz = __fadd2_rn(__fadd2_rn(zh, nxh[k][2]), __fadd2_rn(zl, nxl[k][2]));
+                }
                 const float2 ux = __fadd2_rn(vx, nv[k][0]);
                 const float2 uy = __fadd2_rn(vy, nv[k][1]);
                 const float2 uz = __fadd2_rn(vz, nv[k][2]);
@@ -1088,8 +1134,8 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
             load_i(t);
             cur_t = t;
         }
-        const int s = q % NSTAGE;
-        const uint32_t par = (uint32_t)((q / NSTAGE) & 1);
+        const int s = q % NS;
+        const uint32_t par = (uint32_t)((q / NS) & 1);
         // Does this tile hold the j-particle of one of the warp's i-particles?
         auto self_test = [&](int2 rg) -> bool {
             bool mine = false;
@@ -1121,8 +1167,8 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         // then report.
         auto give_up = [&]() {
             if (tid == 0) {
-                for (int r = q; r < q + NSTAGE && r < ntile; ++r)
-                    mbar_wait_bounded(&bar[r % NSTAGE], (uint32_t)((r / NSTAGE) & 1),
+                for (int r = q; r < q + NS && r < ntile; ++r)
+                    mbar_wait_bounded(&bar[r % NS], (uint32_t)((r / NS) & 1),
                                       WAIT_LIMIT_NS);
                 *(volatile int *)a.err = G6_ETIMEDOUT;
             }
@@ -1138,8 +1184,8 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                 give_up();
                 return;
             }
-            if (tid == 0 && q + NSTAGE < ntile)
-                issue(q + NSTAGE);               // the raw stage is free again
+            if (tid == 0 && q + NS < ntile)
+                issue(q + NS);               // the raw stage is free again
             int2 rg = make_int2(INT_MAX, -1);
 #pragma unroll
             for (int w = 0; w < NT / 32; ++w) {
@@ -1162,8 +1208,8 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                 give_up();
                 return;
             }
-            if (tid == 0 && q + NSTAGE < ntile)
-                issue(q + NSTAGE);
+            if (tid == 0 && q + NS < ntile)
+                issue(q + NS);
         }
     }
     finalize(cur_t);
@@ -1558,10 +1604,10 @@ constexpr int ds_smem(int nt, int ni)
     return NSTAGE * JW * JT * (int)sizeof(float) + ni * 7 * nt * (int)sizeof(float2);
 }
 
-// ... with fused prediction: NSTAGE raw tiles + one predicted tile + sums
+// ... with fused prediction: FP_NSTAGE raw tiles + one predicted tile + sums
 constexpr int fp_smem(int nt, int ni)
 {
-    return NSTAGE * (int)RAW_TILE_BYTES + JW * JT * (int)sizeof(float)
+    return FP_NSTAGE * (int)RAW_TILE_BYTES + JW * JT * (int)sizeof(float)
            + ni * 7 * nt * (int)sizeof(float2);
 }
 
@@ -1595,6 +1641,11 @@ const Variant kVariants[] = {
      fp_smem(256, 2)},
     {{64, 4, 2, 0, G6X_PREC_DS, 1, 16}, k_force_ds<64, 4, 2, false, 2, 2, false, true>, 256,
      fp_smem(256, 2)},
+    // full DS subtraction for the separations (accuracy ablation)
+    {{128, 1, 2, 0, G6X_PREC_DS_DSSUB}, k_force_ds<128, 1, 2, false, 3, 2, false, false, true>,
+     128, ds_smem(128, 2)},
+    {{16, 16, 1, 0, G6X_PREC_DS_DSSUB}, k_force_ds<16, 16, 1, false, 1, 2, false, false, true>,
+     256, ds_smem(256, 1)},
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
@@ -1758,6 +1809,9 @@ ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
         v = force_variant;
     } else if (prec == G6X_PREC_FP64) {
         v = list ? 8 : 7;
+    } else if (prec == G6X_PREC_DS_DSSUB && !list) {
+        v = ni <= 32 ? 22 : 21;
+        gmul = ni > 2048 ? 2 : 1;
     } else if (list) {
         v = ni <= 32 ? 6 : 5;
     } else if (ni <= 32) {
@@ -1869,8 +1923,7 @@ cudaError_t launch_update_predict(int kind, JStore js, Pred p, int nj, int nj_pa
 }
 
 // Arguments of the fused prediction (variants with fpred set).
-static bool set_fused_pred(ForceArgs &a, const ForceConfig &cfg, const Pred &p,
-                           const FusedPred *fp)
+static bool set_fused_pred(ForceArgs &a, const ForceConfig &cfg, const FusedPred *fp)
 {
     if (!kVariants[cfg.variant].info.fpred)
         return true;
@@ -1879,7 +1932,6 @@ static bool set_fused_pred(ForceArgs &a, const ForceConfig &cfg, const Pred &p,
     a.js = fp->js;
     a.t_pred = fp->t;
     a.nj = fp->nj;
-    a.pt_w = p.pt;
     return true;
 }
 
@@ -1908,7 +1960,7 @@ cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
     a.ni = ni;
     a.eps2 = eps2;
     a.wait_ns = g_wait_ns;
-    if (!set_fused_pred(a, cfg, p, fp))
+    if (!set_fused_pred(a, cfg, fp))
         return cudaErrorInvalidValue;
     const Variant &v = kVariants[cfg.variant];
     v.fn<<<cfg.grid, v.threads, v.smem, s>>>(a);
@@ -1944,7 +1996,7 @@ cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
     a.tcnt = tcnt;
     a.fused = 1;
     a.wait_ns = g_wait_ns;
-    if (!set_fused_pred(a, cfg, p, fp))
+    if (!set_fused_pred(a, cfg, fp))
         return cudaErrorInvalidValue;
     const Variant &v = kVariants[cfg.variant];
     v.fn<<<cfg.grid, v.threads, v.smem, s>>>(a);

@@ -1,6 +1,7 @@
-// g6gb_pool.h -- a small persistent pool of host threads for the drivers'
-// per-particle and per-cluster host work (prediction of the active
-// i-particles, correction, staging).  Internal to the library.
+// g6gb_pool.h -- one persistent pool of host threads for the library's
+// per-particle and per-cluster host loops (prediction of the active
+// i-particles, correction, staging, copies of large blocks).  Internal to the
+// library.
 #pragma once
 
 #include <algorithm>
@@ -8,6 +9,7 @@
 #include <condition_variable>
 #include <cstdlib>
 #include <functional>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -105,6 +107,37 @@ inline int host_threads()
     }
     const unsigned hw = std::thread::hardware_concurrency();
     return (int)std::max(1u, std::min(hw, 16u));
+}
+
+// The process-wide pool (started on first use; NULL if threads cannot be
+// started).
+inline HostPool *shared_pool()
+{
+    static std::unique_ptr<HostPool> pool;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        try {
+            pool.reset(new HostPool(host_threads()));
+        } catch (...) {
+            pool.reset();
+        }
+    });
+    return pool.get();
+}
+
+// f(0 .. n-1) on the process-wide pool; serially when the pool is in use by
+// another caller (or by this one: nested calls), has no threads, or n < 2.
+inline void parallel_run(int n, const std::function<void(int)> &f)
+{
+    static std::mutex busy;
+    std::unique_lock<std::mutex> lk(busy, std::try_to_lock);
+    HostPool *p = n > 1 && lk.owns_lock() ? shared_pool() : nullptr;
+    if (!p) {
+        for (int i = 0; i < n; ++i)
+            f(i);
+        return;
+    }
+    p->run(n, f);
 }
 
 }  // namespace g6

@@ -27,6 +27,7 @@ G6_MAX_CLUSTERS = 16
 G6X_PREC_DS = 0
 G6X_PREC_FP64 = 1
 G6X_PREC_DS_X64 = 2
+G6X_PREC_DS_DSSUB = 3
 G6X_NOALLOC_NI_MAX = 16384
 G6X_NOALLOC_SCRATCH_BYTES = 147456 * 72
 

@@ -26,7 +26,8 @@ from . import build as _build
 from . import g6gb as g6
 from . import ics
 
-PREC = {"ds": g6.G6X_PREC_DS, "fp64": g6.G6X_PREC_FP64, "ds_x64": g6.G6X_PREC_DS_X64}
+PREC = {"ds": g6.G6X_PREC_DS, "fp64": g6.G6X_PREC_FP64, "ds_x64": g6.G6X_PREC_DS_X64,
+        "ds_dssub": g6.G6X_PREC_DS_DSSUB}
 
 
 def energy_fp64(cid, sim, mode):

@@ -325,3 +325,65 @@ def test_fused_prediction_is_identical_to_separate(ctx, orc, fv, twin, m):
     ea = rel_err_vec(b2[0], oa)
     assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5
     check_nn(onn, onr, b2[3], xi, xp, idx)
+
+
+@pytest.mark.parametrize("m", [16, 3001])
+def test_full_ds_subtraction_ablation(ctx, orc, m):
+    # Separations by the full DS subtraction instead of Eq. 3's form: the
+    # same tolerances on close binaries and on a Plummer subset; the DS forms
+    # agree with each other far more closely than with FP32 positions.
+    n = 4096
+    mm, x, v, pairs = ics.plummer_with_binaries(n, 5)
+    idx = np.arange(n)
+    eps2 = 1e-8
+    load_j(ctx, x, v, mm)
+    act = np.sort(np.concatenate([pairs[:8].reshape(-1),
+                                  ics.permutation(n, 6)[:max(0, min(m, n) - 16)]]))[:m]
+    act = np.unique(act)
+    res = {}
+    for prec in (g6.G6X_PREC_DS, g6.G6X_PREC_DS_DSSUB):
+        g6.g6x_set_precision(ctx, prec)
+        res[prec] = sweep(ctx, n, x[act], v[act], act, eps2, 0.0)
+    cfg = g6.g6x_last_config(ctx)
+    assert cfg["variant"] in (21, 22)
+    oa, oj, op, onn, onr = orc.force(x[act], v[act], act, x, v, mm, idx, eps2)
+    for prec, (acc, jerk, pot, nnb) in res.items():
+        ea, ep = rel_err_vec(acc, oa), np.abs(pot - op) / np.abs(op)
+        assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5, (prec, np.median(ea), ea.max())
+        assert np.median(ep) <= 1e-6 and ep.max() <= 1e-5
+        check_nn(onn, onr, nnb, x[act], x, idx)
+    g6.g6x_set_precision(ctx, g6.G6X_PREC_DS)
+
+
+def test_large_bulk_staging_keeps_the_last_values(ctx, orc):
+    # A bulk j-update above the threaded size that names every address twice
+    # (first with wrong data) stages the last values, as the per-particle
+    # calls do; a large update without repeats equals per-particle staging.
+    n, eps2, t_blk = 20000, 1e-5, 0.375
+    st = ics.taylor_state(n, 31, t_blk)
+    addr = np.arange(n, dtype=np.int32)
+    both = np.concatenate([addr, addr])
+    junk = st["x0"] + 1.0
+    g6.g6x_set_j_particles(ctx, both, both, np.concatenate([st["tj"], st["tj"]]),
+                           np.concatenate([st["m"], st["m"]]),
+                           np.concatenate([st["j0"], st["j0"]]) / 6.0,
+                           np.concatenate([st["a0"], st["a0"]]) / 2.0,
+                           np.concatenate([st["v0"], st["v0"]]),
+                           np.concatenate([junk, st["x0"]]))
+    act = np.sort(ics.permutation(n, 32)[:512])
+    xi, vi = st["x0"][act], st["v0"][act]
+    bulk = sweep(ctx, n, xi, vi, act, eps2, t_blk)
+    xp, vp = orc.predict(st["x0"], st["v0"], st["a0"], st["j0"], st["tj"], t_blk)
+    oa, *_ = orc.force(xi, vi, act, xp, vp, st["m"], np.arange(n), eps2)
+    ea = rel_err_vec(bulk[0], oa)
+    assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5
+    load_j(ctx, st["x0"] + 0.5, st["v0"], st["m"], st["a0"], st["j0"], st["tj"])
+    for k in range(n):                         # per-particle staging, same data
+        g6.g6_set_j_particle(ctx, k, k, st["tj"][k], 0.0, st["m"][k], np.zeros(3),
+                             st["j0"][k] / 6.0, st["a0"][k] / 2.0, st["v0"][k], st["x0"][k])
+    single = sweep(ctx, n, xi, vi, act, eps2, t_blk + 2.0 ** -8)
+    g6.g6x_set_j_particles(ctx, addr, addr, st["tj"], st["m"], st["j0"] / 6.0,
+                           st["a0"] / 2.0, st["v0"], st["x0"])
+    again = sweep(ctx, n, xi, vi, act, eps2, t_blk + 2.0 ** -8)
+    for u, w in zip(single, again):
+        assert np.array_equal(u, w)
