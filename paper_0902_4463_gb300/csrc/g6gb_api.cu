@@ -7,6 +7,8 @@
 #include "g6gb_internal.h"
 #include "g6gb_pool.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -214,17 +216,25 @@ cudaEvent_t pool_event(Ctx &c)
 }
 
 // Bracket one launch with events when timing is on.
+// One phase of a calculation: an NVTX range on the host (visible to
+// profilers that collect NVTX; near free otherwise) and, with timing on, a
+// pair of CUDA events on the context's stream.
+const char *const kPhaseName[4] = {"g6gb j-update", "g6gb predict", "g6gb force",
+                                   "g6gb reduce"};
+
 struct PhaseTimer {
     Ctx &c;
     int ph;
     cudaEvent_t e0 = nullptr;
     PhaseTimer(Ctx &cc, int p) : c(cc), ph(p)
     {
+        nvtxRangePushA(kPhaseName[p]);
         if (c.timing && (e0 = pool_event(c)) != nullptr)
             cudaEventRecord(e0, c.stream);
     }
     ~PhaseTimer()
     {
+        nvtxRangePop();
         if (!e0)
             return;
         cudaEvent_t e1 = pool_event(c);
