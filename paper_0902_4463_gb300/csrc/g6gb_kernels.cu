@@ -1435,8 +1435,11 @@ __device__ __forceinline__ g6x_out result_of(const PS &acc, const int *jidx)
         o.jerk[d] = acc.value(3 + d);
     }
     o.pot = -acc.value(6);
-    o.nnb = acc.bj >= 0 ? jidx[acc.bj] : -1;
-    o.nnr2 = acc.bj >= 0 ? acc.nnr2() : __int_as_float(0x7f800000);
+    // a winner that far away is an empty slot (parked at FAR), not a particle:
+    // no other j-particle took part
+    const bool has_nn = acc.bj >= 0 && acc.nnr2() < 1e30f;
+    o.nnb = has_nn ? jidx[acc.bj] : -1;
+    o.nnr2 = has_nn ? acc.nnr2() : __int_as_float(0x7f800000);
     return o;
 }
 

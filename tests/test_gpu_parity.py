@@ -387,3 +387,57 @@ def test_large_bulk_staging_keeps_the_last_values(ctx, orc):
     again = sweep(ctx, n, xi, vi, act, eps2, t_blk + 2.0 ** -8)
     for u, w in zip(single, again):
         assert np.array_equal(u, w)
+
+
+@pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64])
+def test_empty_calls(ctx, orc, prec):
+    # ni = 0 is a no-op; nj = 0 leaves every i-particle without partners:
+    # zero acceleration, jerk and potential, no nearest neighbour (the slots
+    # holding particles beyond nj must not act, not even as a neighbour).
+    n = 300
+    m, x, v = ics.plummer(n, 3)
+    g6.g6x_set_precision(ctx, prec)
+    load_j(ctx, x, v, m)
+    acc, jerk, pot, nnb = sweep(ctx, n, x[:0], v[:0], np.arange(0), 1e-4, 0.0)
+    assert acc.shape == (0, 3) and nnb.shape == (0,)
+    acc, jerk, pot, nnb = sweep(ctx, 0, x[:5], v[:5], np.arange(5), 1e-4, 0.0)
+    assert np.all(acc == 0) and np.all(jerk == 0) and np.all(pot == 0)
+    assert np.all(nnb == -1)
+    # and the context still computes normally afterwards
+    # one j-particle, which is the i-particle itself: alone again
+    acc, jerk, pot, nnb = sweep(ctx, 1, x[:1], v[:1], np.arange(1), 1e-4, 0.0)
+    assert np.all(acc == 0) and np.all(pot == 0) and nnb[0] == -1
+    acc, *_ = sweep(ctx, n, x, v, np.arange(n), 1e-4, 0.0)
+    oa, *_ = orc.force(x, v, np.arange(n), x, v, m, np.arange(n), 1e-4)
+    assert np.median(rel_err_vec(acc, oa)) <= _tol(prec)[0]
+
+
+@pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64])
+def test_capacity_sized_call_and_massless_particles(orc, prec):
+    # nj equal to the context's j capacity and ni equal to its i limit; a
+    # tenth of the particles massless (they feel forces, exert none).
+    from paper_0902_4463_gb300 import build
+    build.build()
+    cap, nimax, cid = 8192, 1000, 12
+    m, x, v = ics.plummer(cap, 4)
+    m = m.copy()
+    m[::10] = 0.0
+    idx = np.arange(cap)
+    g6.g6x_open_ex(cid, cap, nimax)
+    try:
+        g6.g6x_set_precision(cid, prec)
+        load_j(cid, x, v, m)
+        act = np.sort(ics.permutation(cap, 8)[:nimax])
+        acc, jerk, pot, nnb = sweep(cid, cap, x[act], v[act], act, 1e-5, 0.0)
+        with pytest.raises(g6.G6Error):                    # one more i than allowed
+            sweep(cid, cap, x[:nimax + 1], v[:nimax + 1], idx[:nimax + 1], 1e-5, 0.0)
+        with pytest.raises(g6.G6Error):                    # one more j than capacity
+            sweep(cid, cap + 1, x[:5], v[:5], idx[:5], 1e-5, 0.0)
+    finally:
+        g6.g6_close(cid)
+    oa, oj, op, onn, onr = orc.force(x[act], v[act], act, x, v, m, idx, 1e-5)
+    med, mx = _tol(prec)
+    ea, ep = rel_err_vec(acc, oa), np.abs(pot - op) / np.abs(op)
+    assert np.median(ea) <= med and ea.max() <= mx
+    assert np.median(ep) <= med and ep.max() <= mx
+    check_nn(onn, onr, nnb, x[act], x, idx)
