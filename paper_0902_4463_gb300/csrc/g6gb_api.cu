@@ -501,8 +501,15 @@ bool sort_by_tile(Ctx &c, int ntiles)
 
 // predict = false: only store the staged records (for a force kernel that
 // predicts the j-tiles itself); every cached prediction is then stale.
-int update_and_predict(Ctx &c, int nj, bool predict = true)
+// fold_jtiles > 0 (with predict = false): when every staged record lies in
+// the first fold_jtiles tiles, only sort them; the force kernel stores them
+// (one i-tile: each j-tile read by one CTA) and *folded is set -- the caller
+// then records ev_jsort after that launch.
+int update_and_predict(Ctx &c, int nj, bool predict = true, int fold_jtiles = 0,
+                       bool *folded = nullptr)
 {
+    if (folded)
+        *folded = false;
     if (c.n_jst == 0)
         return predict ? predict_if_stale(c, nj) : 0;
     const int nj_pad = predict ? round_up(nj > 0 ? nj : 1, JT) : 0;
@@ -512,7 +519,9 @@ int update_and_predict(Ctx &c, int nj, bool predict = true)
         if (tl > max_tile)
             max_tile = tl;
     }
-    const int ntiles_all = nj_pad / JT > max_tile + 1 ? nj_pad / JT : max_tile + 1;
+    const bool fold = !predict && folded && fold_jtiles > 0 && max_tile + 1 <= fold_jtiles;
+    const int ntiles_all = fold ? fold_jtiles
+                           : nj_pad / JT > max_tile + 1 ? nj_pad / JT : max_tile + 1;
     if (c.jsort_inflight) {                 // the previous sorted batch is still read
         if (cudaEventQuery(c.ev_jsort) != cudaSuccess)
             cudaEventSynchronize(c.ev_jsort);
@@ -547,18 +556,22 @@ int update_and_predict(Ctx &c, int nj, bool predict = true)
         return G6_ENOMEM;
     const int kind = c.pmode == G6X_PREC_FP64 ? g6::PRED_FP64
                      : c.pmode == G6X_PREC_DS_X64 ? g6::PRED_DS_X64 : g6::PRED_DS;
-    cudaError_t e;
-    {
-        PhaseTimer pt(c, PH_PREDICT);
-        e = g6::launch_update_predict(kind, c.js, c.pred, nj, nj_pad, c.t_set, c.d_jsort, c.d_toff,
-                                      ntiles_all, c.sm_count, c.stream);
+    if (fold) {
+        *folded = true;
+    } else {
+        cudaError_t e;
+        {
+            PhaseTimer pt(c, PH_PREDICT);
+            e = g6::launch_update_predict(kind, c.js, c.pred, nj, nj_pad, c.t_set, c.d_jsort,
+                                          c.d_toff, ntiles_all, c.sm_count, c.stream);
+        }
+        if (e == cudaSuccess)
+            e = cudaEventRecord(c.ev_jsort, c.stream);
+        if (e != cudaSuccess)
+            return cuda_err(e);
+        c.launches += 1;
+        c.jsort_inflight = true;
     }
-    if (e == cudaSuccess)
-        e = cudaEventRecord(c.ev_jsort, c.stream);
-    if (e != cudaSuccess)
-        return cuda_err(e);
-    c.launches += 1;
-    c.jsort_inflight = true;
     par_for(c, c.n_jst, [&](int k0, int k1) {
         for (int k = k0; k < k1; ++k)
             c.slot_of[c.h_jst[k].address] = -1;
@@ -623,25 +636,47 @@ ForceConfig pick_config(const Ctx &c, int nj, int ni, bool list)
 // j-store update, prediction (unless the force kernel predicts itself),
 // force and reduction.
 int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_irec,
-              double eps2, g6x_out *d_out);
+              double eps2, g6x_out *d_out, bool folded);
 
 int predict_and_force(Ctx &c, int nj, int ni, const g6x_irec *d_irec, double eps2, bool list,
                       g6x_out *d_out)
 {
     const ForceConfig cfg = pick_config(c, nj, ni, list);
     const bool fp = g6::variant_info(cfg.variant).fpred != 0 && ni > 0;
-    int rc = update_and_predict(c, nj, !fp);
+    // a small block is one launch: the fused-prediction kernel also stores
+    // the staged records of its tiles
+    bool folded = false;
+    int rc = update_and_predict(c, nj, !fp, fp && cfg.n_itile == 1 ? cfg.jtiles : 0, &folded);
     if (!rc && ni > 0)
-        rc = run_force(c, cfg, nj, ni, d_irec, eps2, d_out);
+        rc = run_force(c, cfg, nj, ni, d_irec, eps2, d_out, folded);
+    if (folded) {
+        if (rc) {
+            // no kernel stored the sorted records: store them now
+            const int kind = c.pmode == G6X_PREC_DS_X64 ? g6::PRED_DS_X64 : g6::PRED_DS;
+            if (g6::launch_update_predict(kind, c.js, c.pred, nj, 0, c.t_set, c.d_jsort, c.d_toff,
+                                          cfg.jtiles, c.sm_count, c.stream) == cudaSuccess)
+                c.launches += 1;
+            else
+                cudaGetLastError();
+        }
+        if (cudaEventRecord(c.ev_jsort, c.stream) != cudaSuccess)
+            cudaGetLastError();
+        c.jsort_inflight = true;
+    }
     return rc;
 }
 
 int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_irec,
-              double eps2, g6x_out *d_out)
+              double eps2, g6x_out *d_out, bool folded)
 {
     // fused-prediction shapes read the j-store itself (the predicted tiles
-    // and their cache entry are left as they are)
-    const g6::FusedPred fpa{c.js, c.t_set, nj};
+    // and their cache entry are left as they are); folded: they also store
+    // the staged records first
+    g6::FusedPred fpa{c.js, c.t_set, nj};
+    if (folded) {
+        fpa.rec = c.d_jsort;
+        fpa.toff = c.d_toff;
+    }
     const g6::FusedPred *fpp = g6::variant_info(cfg.variant).fpred ? &fpa : nullptr;
     size_t slots = g6::partial_slots(cfg);
     int rc = grow_dev(c.d_part, c.part_cap, slots);

@@ -105,6 +105,10 @@ struct FusedPred {
     JStore js;
     double t;
     int nj;
+    // staged j-records sorted by tile (toff: per-tile ranges), stored by
+    // the force kernel itself; only with one i-tile (NULL: none staged)
+    const g6x_jrec *rec = nullptr;
+    const int *toff = nullptr;
 };
 
 // Work geometry of a batch of independent clusters: cluster k holds j-tiles

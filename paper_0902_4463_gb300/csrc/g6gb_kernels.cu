@@ -122,6 +122,13 @@ __device__ __forceinline__ void fence_barrier_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Order this thread's earlier global stores before later bulk asynchronous
+// copies (the async proxy) that read them.
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // Knuth's TwoSum: s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
@@ -499,10 +506,14 @@ struct ForceArgs {
     BatchTables bt;                   // batch geometry (batch kernels only)
     unsigned long long wait_ns;       // limit of each wait for a staged tile
     // prediction inside the force kernel: the j-store, the block time and
-    // the number of particles in j-memory
+    // the number of particles in j-memory; with one i-tile (each j-tile
+    // handled by one CTA) also the staged j-records, sorted by tile, that
+    // each CTA stores for its own tiles before it reads them
     JStore js;
     double t_pred;
     int nj;
+    const g6x_jrec *rec;
+    const int *toff;
 };
 
 // Pair forces in FP32 with the DS separation of Eq. 3 (Sect. 2.3).  Per pair:
@@ -686,6 +697,19 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
             s_whi[tid >> 5] = hi;
         }
     };
+    if constexpr (FP) {
+        // staged j-records of this CTA's tiles (one i-tile: no other CTA
+        // reads these tiles), stored before the bulk copies read them
+        if (a.rec) {
+            for (int q = 0; q < ntile; ++q) {
+                const int jt = (int)(wb + q);
+                for (int r = a.toff[jt] + tid; r < a.toff[jt + 1]; r += NT)
+                    store_record(a.rec[r], a.js);
+            }
+            fence_proxy_async_global();
+            __syncthreads();
+        }
+    }
     if (tid == 0)
         for (int q = 0; q < NS && q < ntile; ++q)
             issue(q);
@@ -1935,7 +1959,9 @@ static bool set_fused_pred(ForceArgs &a, const ForceConfig &cfg, const FusedPred
     a.js = fp->js;
     a.t_pred = fp->t;
     a.nj = fp->nj;
-    return true;
+    a.rec = fp->rec;
+    a.toff = fp->toff;
+    return fp->rec == nullptr || (cfg.n_itile == 1 && fp->toff != nullptr);
 }
 
 cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,

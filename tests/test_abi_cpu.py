@@ -134,3 +134,29 @@ def test_wait_limit_range(lib):
     assert lib.g6x_set_wait_limit(0.5) == 0
     assert lib.g6x_set_wait_limit(2.0) == 0
     assert lib.g6x_probe_wait_timeout(9) == g6gb.G6_ENOTOPEN
+
+
+def _build_c_client(tmp_path):
+    """Compile and link the plain-C GRAPE client against the header and the
+    library (the library's directory as its run path)."""
+    import subprocess
+    libdir = os.path.join(ROOT, "paper_0902_4463_gb300")
+    exe = str(tmp_path / "grape_client")
+    cmd = ["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-O1",
+           os.path.join(ROOT, "tests", "c_client", "grape_client.c"),
+           "-I", os.path.join(ROOT, "include"), "-L", libdir, "-lg6gb",
+           "-Wl,-rpath," + libdir, "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return exe
+
+
+def test_c_client_builds_against_the_header_and_library(lib, tmp_path):
+    import subprocess
+    exe = _build_c_client(tmp_path)
+    inp = tmp_path / "in.txt"
+    inp.write_text("2\n0.5 0 0 0 0 0 0\n0.5 1 0 0 0 0 0\n")
+    r = subprocess.run([exe, str(inp), str(tmp_path / "out.txt"), "1e-4", "0"],
+                       capture_output=True, text=True)
+    if not os.path.exists("/dev/nvidia0"):
+        assert r.returncode == -g6gb.G6_ENODEV          # no GPU here

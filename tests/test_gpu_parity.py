@@ -441,3 +441,33 @@ def test_capacity_sized_call_and_massless_particles(orc, prec):
     assert np.median(ea) <= med and ea.max() <= mx
     assert np.median(ep) <= med and ep.max() <= mx
     check_nn(onn, onr, nnb, x[act], x, idx)
+
+
+def test_plain_c_client_matches_oracle(orc, tmp_path):
+    # The GRAPE calling sequence from a C program (no Python between it and
+    # the library): Plummer N = 1024, forces, nearest neighbours and list
+    # lengths against the oracle.
+    import subprocess
+    from tests.test_abi_cpu import _build_c_client
+    from paper_0902_4463_gb300 import build
+    build.build()
+    exe = _build_c_client(tmp_path)
+    n, eps2, h2 = 1024, 1e-4, 0.01
+    m, x, v = ics.plummer(n, 1)
+    lines = ["%d" % n] + ["%.17g %.17g %.17g %.17g %.17g %.17g %.17g" % (m[k], *x[k], *v[k])
+                          for k in range(n)]
+    (tmp_path / "in.txt").write_text("\n".join(lines) + "\n")
+    out = tmp_path / "out.txt"
+    r = subprocess.run([exe, str(tmp_path / "in.txt"), str(out), repr(eps2), repr(h2)],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    res = np.loadtxt(out)
+    acc, jerk, pot = res[:, 0:3], res[:, 3:6], res[:, 6]
+    nnb, nblen = res[:, 7].astype(int), res[:, 8].astype(int)
+    idx = np.arange(n)
+    oa, oj, op, onn, onr = orc.force(x, v, idx, x, v, m, idx, eps2)
+    assert np.median(rel_err_vec(acc, oa)) <= 1e-6 and rel_err_vec(acc, oa).max() <= 1e-5
+    assert np.median(np.abs(pot - op) / np.abs(op)) <= 1e-6
+    check_nn(onn, onr, nnb, x, x, idx)
+    olen, _, _ = orc.neighbours(x, idx, x, idx, np.full(n, h2), maxnb=g6.G6_MAXNB)
+    assert np.all(np.abs(nblen - olen) <= 1)
