@@ -381,6 +381,27 @@ int g6h_correct_block(int n, double t_blk, const double *t0, const double *dt,
                       double *vp, const double *a0, const double *j0,
                       const double *a1, const double *j1, double *dt_new);
 
+/* g6h_correct_block with a time-step choice that allows for a relative
+ * force error force_noise (>= 0; 0 gives g6h_correct_block): before
+ * Aarseth's criterion, the magnitudes of the second and third derivatives
+ * are reduced by what force errors of that relative size alone can put into
+ * them through the corrector's differences (up to (24 na + 12 h nj)/h^3 and
+ * (36 na + 18 h nj)/h^2 with na = force_noise |a|, nj = force_noise |j|), so
+ * that force noise is not read as structure that shrinks the steps (Sect.
+ * 3.1: with low-precision forces small steps tend to become much smaller).
+ * The request is the larger of the plain one and the reduced one, so the
+ * allowance never shortens a step.  Not in the paper; off unless asked for. */
+int g6h_correct_block_ex(int n, double t_blk, const double *t0, const double *dt,
+                         double eta, double dt_max, double dt_min, double *xp,
+                         double *vp, const double *a0, const double *j0,
+                         const double *a1, const double *j1, double *dt_new,
+                         double force_noise);
+
+/* Use g6h_correct_block_ex's time-step choice with relative force error
+ * rel (0 <= rel < 1; 0, the default, is the plain criterion).  Returns 0 or
+ * G6_EINVAL. */
+int g6h_set_force_noise(g6h_sim *s, double rel);
+
 /* Copy the current state out (any pointer may be NULL): x, v, acc, jerk
  * [n][3]; t, dt [n]. */
 int g6h_get_state(const g6h_sim *s, double *x, double *v, double *acc,
@@ -565,6 +586,9 @@ int g6hb_run(g6hb_sim *s, double t_end);
 /* The driver's batch (for g6x_batch_set_timing and the like); NULL for a
  * NULL driver. */
 g6x_batch *g6hb_batch(g6hb_sim *s);
+
+/* As g6h_set_force_noise, for every cluster of a batch driver. */
+int g6hb_set_force_noise(g6hb_sim *s, double rel);
 
 /* Change the launch mode (0, 1, 2 as for g6x_batch_calc). */
 int g6hb_set_mode(g6hb_sim *s, int mode);

@@ -936,6 +936,7 @@ struct g6hb_sim {
     g6x_batch *b = nullptr;
     int ncl = 0, mode = 0;
     double eta = 0, eta_s = 0, dt_max = 0, dt_min = 0;
+    double noise = 0;                        // relative force error for the time steps
     std::vector<int> n, off;                 // particles per cluster, offset into arrays
     std::vector<double> eps2;
     std::vector<double> m, x, v, a, j, t, dt;
@@ -1027,9 +1028,9 @@ int hb_correct(g6hb_sim &s, const g6hb_sim::Chunk &c)
         const int q = s.act[k][i];
         const int p = s.off[k] + q;
         double t0[1] = {s.t[p]}, dtv[1] = {s.dt[p]}, dn[1];
-        const int rc = g6h_correct_block(1, tb, t0, dtv, s.eta, s.dt_max, s.dt_min, &s.xp[3 * p],
-                                         &s.vp[3 * p], &s.a[3 * p], &s.j[3 * p], o[i].acc,
-                                         o[i].jerk, dn);
+        const int rc = g6h_correct_block_ex(1, tb, t0, dtv, s.eta, s.dt_max, s.dt_min,
+                                            &s.xp[3 * p], &s.vp[3 * p], &s.a[3 * p], &s.j[3 * p],
+                                            o[i].acc, o[i].jerk, dn, s.noise);
         if (rc != 0)
             return rc < 0 ? rc : G6_EINVAL;
         const size_t si = s.sbase[k] + i;
@@ -1340,6 +1341,14 @@ int g6hb_get_state(const g6hb_sim *s, double *x, double *v, double *t)
         std::memcpy(v, s->v.data(), 3 * tot * sizeof(double));
     if (t)
         std::memcpy(t, s->t.data(), tot * sizeof(double));
+    return 0;
+}
+
+int g6hb_set_force_noise(g6hb_sim *s, double rel)
+{
+    if (!s || !(rel >= 0) || !(rel < 1))
+        return G6_EINVAL;
+    s->noise = rel;
     return 0;
 }
 

@@ -46,6 +46,8 @@ struct g6h_sim {
     // step when h2 > 0, read back and counted
     double h2 = 0;
     std::vector<double> h2v;
+    // relative force error allowed for in the time-step choice (0: none)
+    double noise = 0;
     std::vector<int> nbl;
     long long nb_lists = 0, nb_entries = 0, nb_overflowed = 0;
     // host threads for the per-particle work of a block, and the block's
@@ -137,6 +139,33 @@ double aarseth(const double *a, const double *j, const double *d2, const double 
     return std::sqrt(eta * (std::sqrt(a_2 * d2_2) + j_2) / (std::sqrt(j_2 * d3_2) + d2_2));
 }
 
+// Aarseth's request from the end-of-step derivatives.  With noise > 0 (the
+// relative error of the force evaluation) the magnitudes of a'' and a''' are
+// first reduced by what force errors of that size alone can put into them:
+// a''' = (12 (a0 - a1) + 6 h (j0 + j1)) / h^3 and a''(t1) = a'' + h a''' take
+// differences of nearly equal forces, so errors of na = noise |a| and
+// nj = noise |j| in each force give up to (24 na + 12 h nj) / h^3 in a''' and
+// (36 na + 18 h nj) / h^2 in a''(t1).  Without this, force noise read as
+// structure shrinks the steps, which makes the noise larger still.  The
+// allowance only ever lengthens a step: with a near-zero jerk, a reduced a''
+// of 0 would leave sqrt(eta |j| / |a'''|) and collapse the request, so the
+// larger of the plain and the reduced request is taken (a 0/0 of the reduced
+// one, no measurable derivative at all, also gives the plain one).
+double step_request(const double *a1, const double *j1, const double *d2e, const double *d3,
+                    double h, double eta, double noise)
+{
+    const double plain = aarseth(a1, j1, d2e, d3, eta);
+    if (!(noise > 0))
+        return plain;
+    const double am = norm3(a1), jm = norm3(j1);
+    const double na = noise * am, nj = noise * jm;
+    const double e3 = (24.0 * na + 12.0 * h * nj) / (h * h * h);
+    const double e2 = (36.0 * na + 18.0 * h * nj) / (h * h);
+    const double m3 = std::max(norm3(d3) - e3, 0.0), m2 = std::max(norm3(d2e) - e2, 0.0);
+    const double reduced = std::sqrt(eta * (am * m2 + jm * jm) / (jm * m3 + m2 * m2));
+    return plain < reduced ? reduced : plain;
+}
+
 // Is t an integer multiple of the power of two p?  t * (1/p) is exact.
 bool multiple_of(double t, double p)
 {
@@ -184,6 +213,17 @@ int g6h_correct_block(int n, double t_blk, const double *t0, const double *dt, d
                       double dt_max, double dt_min, double *xp, double *vp, const double *a0,
                       const double *j0, const double *a1, const double *j1, double *dt_new)
 {
+    return g6h_correct_block_ex(n, t_blk, t0, dt, eta, dt_max, dt_min, xp, vp, a0, j0, a1, j1,
+                                dt_new, 0.0);
+}
+
+int g6h_correct_block_ex(int n, double t_blk, const double *t0, const double *dt, double eta,
+                         double dt_max, double dt_min, double *xp, double *vp, const double *a0,
+                         const double *j0, const double *a1, const double *j1, double *dt_new,
+                         double force_noise)
+{
+    if (!(force_noise >= 0))
+        return G6_EINVAL;
     if (n < 0 || (n > 0 && (!t0 || !dt || !xp || !vp || !a0 || !j0 || !a1 || !j1 || !dt_new)))
         return G6_EINVAL;
     auto block = [=](int k0, int k1) -> int {
@@ -195,7 +235,8 @@ int g6h_correct_block(int n, double t_blk, const double *t0, const double *dt, d
                     d2, d3);
             for (int d = 0; d < 3; ++d)
                 d2e[d] = d2[d] + h * d3[d];
-            const double req = aarseth(&a1[3 * k], &j1[3 * k], d2e, d3, eta);
+            const double req = step_request(&a1[3 * k], &j1[3 * k], d2e, d3, h, eta,
+                                            force_noise);
             double nd = quantise(dt[k], req, t_blk, dt_max);
             if (!(nd >= dt_min)) {
                 nd = -1.0;
@@ -354,7 +395,8 @@ long long g6h_run_blocks(g6h_sim *s, double t_end, long long max_blocks)
                         &s->xp[3 * q], &s->vp[3 * q], d2, d3);
                 for (int d = 0; d < 3; ++d)
                     d2e[d] = d2[d] + h * d3[d];
-                const double req = aarseth(&s->a1[3 * q], &s->j1[3 * q], d2e, d3, s->eta);
+                const double req = step_request(&s->a1[3 * q], &s->j1[3 * q], d2e, d3, h,
+                                                s->eta, s->noise);
                 const double nd = quantise(s->dt[k], req, tb, s->dt_max);
                 small += !(nd >= s->dt_min);
                 for (int d = 0; d < 3; ++d) {
@@ -509,6 +551,14 @@ int g6h_set_neighbour_radius(g6h_sim *s, double h2)
         }
     }
     s->h2 = h2;
+    return 0;
+}
+
+int g6h_set_force_noise(g6h_sim *s, double rel)
+{
+    if (!s || !(rel >= 0) || !(rel < 1))
+        return G6_EINVAL;
+    s->noise = rel;
     return 0;
 }
 

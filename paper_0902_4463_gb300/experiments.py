@@ -8,7 +8,8 @@ integrated with the library's Hermite block-time-step driver.
   N): N = nmin .. nmax in powers of two, eta = 0.01, to t = 1/4.
 * eta (Sect. 3.2, dE/E against the accuracy parameter): eta from 1e-4 to
   0.3 at the given N, to t = 1/4; with --fp64 also the all-FP64 GPU path,
-  whose error floor is set by the integrator alone.
+  whose error floor is set by the integrator alone; with --noise R the DS
+  runs choose their steps allowing for a relative force error R.
 
 The paper does not state its softening; the runs here use eps = 4/N (the
 close-encounter length of an N-body system in Henon units).  Energies are
@@ -28,10 +29,10 @@ def eps2_of(n):
     return (4.0 / n) ** 2
 
 
-def one(n, eta, prec, seed=1, t_end=0.25):
-    r = hermite_run.run(n, seed, eps2_of(n), eta, t_end, prec)
+def one(n, eta, prec, seed=1, t_end=0.25, noise=0.0):
+    r = hermite_run.run(n, seed, eps2_of(n), eta, t_end, prec, noise=noise)
     keep = ("n", "eta", "prec", "eps2", "t_end", "wall_s", "nblocks", "nactive", "mean_block",
-            "interactions_per_s", "gflops_60", "dE_over_E", "synchronised")
+            "interactions_per_s", "gflops_60", "dE_over_E", "synchronised", "force_noise")
     out = {k: r[k] for k in keep}
     out["force_s"] = r["profile"]["force_s"]
     out["host_s"] = r["profile"]["sched_s"] + r["profile"]["correct_s"]
@@ -52,12 +53,12 @@ def scaling(nmin, nmax, fp64_max=0, seed=1):
     return rows
 
 
-def eta_sweep(ns, fp64=False, seed=1, etas=ETAS):
+def eta_sweep(ns, fp64=False, seed=1, etas=ETAS, noise=0.0):
     rows = []
     for n in ns:
         for eta in etas:
             for prec in (("ds", "fp64") if fp64 else ("ds",)):
-                rows.append(one(n, eta, prec, seed))
+                rows.append(one(n, eta, prec, seed, noise=noise if prec == "ds" else 0.0))
                 print(json.dumps(rows[-1]), flush=True)
     return rows
 
@@ -74,11 +75,13 @@ def main(argv=None):
     e.add_argument("--n", type=int, nargs="+", default=[32768, 131072])
     e.add_argument("--fp64", action="store_true")
     e.add_argument("--etas", type=float, nargs="+", default=list(ETAS))
+    e.add_argument("--noise", type=float, default=0.0,
+                   help="DS runs: relative force error the time-step choice allows for")
     a = ap.parse_args(argv)
     if a.what == "scaling":
         rows = scaling(a.nmin, a.nmax, a.fp64_max)
     else:
-        rows = eta_sweep(a.n, a.fp64, etas=a.etas)
+        rows = eta_sweep(a.n, a.fp64, etas=a.etas, noise=a.noise)
     print(json.dumps({"summary": a.what, "runs": len(rows)}))
     return 0
 

@@ -53,6 +53,7 @@ EXPORTS = [
     "g6x_launch_count", "g6x_set_wait_limit", "g6x_probe_wait_timeout", "g6x_set_timing", "g6x_get_timing", "g6h_correct_block", "g6h_create", "g6h_run", "g6h_get_state", "g6h_energy",
     "g6h_stats", "g6h_profile", "g6h_destroy", "g6h_checkpoint", "g6h_restore",
     "g6h_set_neighbour_radius", "g6h_neighbour_stats", "g6h_run_blocks",
+    "g6h_correct_block_ex", "g6h_set_force_noise", "g6hb_set_force_noise",
     "g6x_batch_create", "g6x_batch_destroy", "g6x_batch_irecs", "g6x_batch_results",
     "g6x_batch_set_j", "g6x_batch_set_j_many", "g6x_batch_calc", "g6x_batch_launch_count",
     "g6x_batch_set_schedule", "g6x_batch_get_schedule", "g6x_batch_autotune", "g6hb_autotune",
@@ -111,6 +112,9 @@ def lib():
             "g6x_set_timing": (I, [I, I]),
             "g6x_get_timing": (I, [I, P, P]),
             "g6h_correct_block": (I, [I, D, P, P, D, D, D, P, P, P, P, P, P, P]),
+            "g6h_correct_block_ex": (I, [I, D, P, P, D, D, D, P, P, P, P, P, P, P, D]),
+            "g6h_set_force_noise": (I, [P, D]),
+            "g6hb_set_force_noise": (I, [P, D]),
             "g6h_create": (P, [I, I, P, P, P, D, D, D, D, D, P]),
             "g6h_run": (I, [P, D]),
             "g6h_run_blocks": (C.c_longlong, [P, D, C.c_longlong]),
@@ -407,9 +411,11 @@ def g6x_use_cuda_allocator():
 
 # --------------------------------------------------------- Hermite driver --
 
-def g6h_correct_block(t_blk, t0, dt, eta, dt_max, dt_min, xp, vp, a0, j0, a1, j1):
+def g6h_correct_block(t_blk, t0, dt, eta, dt_max, dt_min, xp, vp, a0, j0, a1, j1,
+                      force_noise=0.0):
     """Host Hermite corrector + next step for a block (C++).  Returns
-    (x1, v1, dt_new, n_too_small); xp and vp are not modified."""
+    (x1, v1, dt_new, n_too_small); xp and vp are not modified.  force_noise:
+    the relative force error the time-step choice allows for (0: none)."""
     xp = _d(xp).reshape(-1, 3).copy()
     vp = _d(vp).reshape(-1, 3).copy()
     n = xp.shape[0]
@@ -417,10 +423,11 @@ def g6h_correct_block(t_blk, t0, dt, eta, dt_max, dt_min, xp, vp, a0, j0, a1, j1
     dt = _d(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
     a0, j0, a1, j1 = (_d(q, (n, 3)) for q in (a0, j0, a1, j1))
     dt_new = np.empty(n)
-    rc = _check(lib().g6h_correct_block(n, float(t_blk), _p(t0), _p(dt), float(eta),
-                                        float(dt_max), float(dt_min), _p(xp), _p(vp), _p(a0),
-                                        _p(j0), _p(a1), _p(j1), _p(dt_new)),
-                "g6h_correct_block")
+    rc = _check(lib().g6h_correct_block_ex(n, float(t_blk), _p(t0), _p(dt), float(eta),
+                                           float(dt_max), float(dt_min), _p(xp), _p(vp),
+                                           _p(a0), _p(j0), _p(a1), _p(j1), _p(dt_new),
+                                           float(force_noise)),
+                "g6h_correct_block_ex")
     return xp, vp, dt_new, rc
 
 
@@ -442,6 +449,9 @@ class G6HSim:
 
     def run(self, t_end):
         return _check(lib().g6h_run(self.h, float(t_end)), "g6h_run")
+
+    def set_force_noise(self, rel):
+        return _check(lib().g6h_set_force_noise(self.h, float(rel)), "g6h_set_force_noise")
 
     def set_neighbour_radius(self, h2):
         return _check(lib().g6h_set_neighbour_radius(self.h, float(h2)),
@@ -644,6 +654,9 @@ class G6HBatchSim:
 
     def set_mode(self, mode):
         return _check(lib().g6hb_set_mode(self.h, int(mode)), "g6hb_set_mode")
+
+    def set_force_noise(self, rel):
+        return _check(lib().g6hb_set_force_noise(self.h, float(rel)), "g6hb_set_force_noise")
 
     def autotune(self, reps=2):
         s = np.zeros(5, dtype=np.int32)

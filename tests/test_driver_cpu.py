@@ -44,6 +44,103 @@ def test_correct_block_flags_steps_below_minimum():
     assert small == 1 and dtn[0] == -1.0
 
 
+def _circular(t):
+    """Acceleration and jerk on the unit circular orbit of unit angular
+    frequency: a = -(cos t, sin t, 0), j = (sin t, -cos t, 0); every
+    derivative has magnitude 1, so Aarseth's request is sqrt(eta)."""
+    a = -np.array([[np.cos(t), np.sin(t), 0.0]])
+    j = np.array([[np.sin(t), -np.cos(t), 0.0]])
+    return a, j
+
+
+def test_noise_aware_step_with_zero_noise_is_the_plain_criterion():
+    build.build()
+    rng = np.random.default_rng(11)
+    n = 300
+    dt = np.ldexp(1.0, -rng.integers(3, 12, n))
+    t_blk = 0.5
+    xp, vp = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    a0, j0 = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    a1 = a0 + j0 * dt[:, None] + rng.normal(size=(n, 3)) * dt[:, None] ** 2
+    j1 = j0 + rng.normal(size=(n, 3)) * dt[:, None]
+    args = (t_blk, t_blk - dt, dt, 0.02, 0.5, 2.0 ** -40, xp, vp, a0, j0, a1, j1)
+    # the wrapper calls g6h_correct_block_ex; call g6h_correct_block itself too
+    x1, v1, dtn, small = g6gb.g6h_correct_block(*args, force_noise=0.0)
+    xr, vr, dtr = xp.copy(), vp.copy(), np.empty(n)
+    p = g6gb._p
+    nsmall = g6gb.lib().g6h_correct_block(n, t_blk, p(np.ascontiguousarray(t_blk - dt)), p(dt),
+                                          0.02, 0.5, 2.0 ** -40, p(xr), p(vr), p(a0), p(j0),
+                                          p(a1), p(j1), p(dtr))
+    assert nsmall == small == 0
+    assert np.array_equal(x1, xr) and np.array_equal(v1, vr) and np.array_equal(dtn, dtr)
+    with np.testing.assert_raises(g6gb.G6Error):
+        g6gb.g6h_correct_block(*args, force_noise=-1e-7)
+
+
+def test_noise_aware_step_does_not_collapse_on_force_noise():
+    """Sect. 3.1: with low-precision forces the step sizes of a small eta
+    shrink further.  On a smooth orbit whose forces carry a relative error of
+    1e-7, the plain criterion reads the noise as a large third derivative and halves a
+    step that the orbit itself allows; allowing for that error keeps it."""
+    build.build()
+    eta, h, t_blk = 1e-4, 2.0 ** -10, 1.0
+    a0, j0 = _circular(t_blk - h)
+    a1, j1 = _circular(t_blk)
+    z = np.zeros((1, 3))
+    rng = np.random.default_rng(5)
+    worst = []
+    for _ in range(20):
+        na = a1 * (1 + 1e-7 * rng.choice([-1.0, 1.0], size=(1, 3)))
+        nj = j1 * (1 + 1e-7 * rng.choice([-1.0, 1.0], size=(1, 3)))
+        args = (t_blk, [t_blk - h], [h], eta, 2.0 ** -3, 2.0 ** -40, z, z, a0, j0, na, nj)
+        _, _, plain, _ = g6gb.g6h_correct_block(*args)
+        _, _, aware, _ = g6gb.g6h_correct_block(*args, force_noise=1e-7)
+        worst.append(plain[0])
+        assert aware[0] >= h
+    assert min(worst) < h                  # the plain criterion does shrink the step
+    # without noise both keep the step (the orbit allows sqrt(eta) = 0.01)
+    args = (t_blk, [t_blk - h], [h], eta, 2.0 ** -3, 2.0 ** -40, z, z, a0, j0, a1, j1)
+    assert g6gb.g6h_correct_block(*args)[2][0] >= h
+    assert g6gb.g6h_correct_block(*args, force_noise=1e-7)[2][0] >= h
+
+
+def test_noise_aware_step_never_shortens_a_step():
+    """The allowance takes the larger of the plain and the reduced request:
+    on random states (including near-zero jerks, where a reduced second
+    derivative of 0 alone would collapse the request) no step comes out
+    shorter than the plain criterion gives."""
+    build.build()
+    rng = np.random.default_rng(13)
+    n = 4000
+    dt = np.ldexp(1.0, -rng.integers(2, 30, n))
+    t_blk = 1.0
+    z = np.zeros((n, 3))
+    a0 = rng.normal(size=(n, 3))
+    j0 = rng.normal(size=(n, 3)) * np.where(rng.random(n) < 0.3, 1e-9, 1.0)[:, None]
+    a1 = a0 * (1 + 1e-6 * rng.normal(size=(n, 3))) + j0 * dt[:, None]
+    j1 = j0 * (1 + 1e-3 * rng.normal(size=(n, 3)))
+    args = (t_blk, t_blk - dt, dt, 1e-3, 0.5, 2.0 ** -60, z, z, a0, j0, a1, j1)
+    plain = g6gb.g6h_correct_block(*args)[2]
+    for noise in (1e-9, 1e-7, 1e-5, 0.5):
+        aware = g6gb.g6h_correct_block(*args, force_noise=noise)[2]
+        assert np.all(aware >= plain), noise
+    assert np.any(g6gb.g6h_correct_block(*args, force_noise=1e-7)[2] > plain)
+
+
+def test_noise_aware_step_still_shrinks_on_real_structure():
+    """A step too long for the orbit (eta = 0.01 allows 0.1) is halved with and
+    without the noise allowance: at h = 1/4 the allowance is ~1e-5 of the third derivative."""
+    build.build()
+    eta, h, t_blk = 0.01, 0.25, 1.0
+    a0, j0 = _circular(t_blk - h)
+    a1, j1 = _circular(t_blk)
+    z = np.zeros((1, 3))
+    args = (t_blk, [t_blk - h], [h], eta, 0.5, 2.0 ** -40, z, z, a0, j0, a1, j1)
+    plain = g6gb.g6h_correct_block(*args)[2][0]
+    aware = g6gb.g6h_correct_block(*args, force_noise=1e-7)[2][0]
+    assert plain == aware == 0.0625
+
+
 # ------------------------------------------------ checkpoint file parser
 # The layout written by g6h_checkpoint (host byte order, little-endian):
 # magic, int64 n, nbuckets, nblocks, nactive, hist[64], 6 doubles of

@@ -289,3 +289,23 @@ def test_batch_driver_256_clusters_drift_vs_stored_oracle(orc):
     guard = 10 * np.maximum(d_orc, np.median(d_orc))
     assert np.all(d_gpu <= guard), np.nonzero(d_gpu > guard)
     assert abs(stats["nactive"] / sum(r[6] for r in rows) - 1) < 0.02
+
+
+def test_batch_driver_force_noise_allowance():
+    # Three clusters to t = 1/16 with eta = 1e-3: with the noise-aware step
+    # choice the batch driver takes fewer batch steps and still synchronises.
+    cls = ics.cluster_batch(3, 13, nmin=256, nmax=512)
+    steps = {}
+    for noise in (0.0, 1e-6):
+        sim = g6.G6HBatchSim([(c["m"], c["x"], c["v"]) for c in cls],
+                             [c["eps2"] for c in cls], 1e-3)
+        try:
+            with pytest.raises(g6.G6Error):
+                sim.set_force_noise(1.5)
+            sim.set_force_noise(noise)
+            sim.run(1.0 / 16)
+            assert np.all(sim.state()["t"] == 1.0 / 16)
+            steps[noise] = sim.stats()["nsteps"]
+        finally:
+            sim.close()
+    assert steps[1e-6] < steps[0.0], steps

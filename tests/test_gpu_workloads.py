@@ -365,3 +365,34 @@ def test_config2_force_errors_at_natural_block_steps(orc):
     print("\nconfig2 block errors (t, m, acc med, acc max, jerk med, jerk max, pot med, nn):")
     for r in rows:
         print("%.6f %6d %.2e %.2e %.2e %.2e %.2e %.4f" % r)
+
+
+def test_hermite_driver_noise_allowance_takes_fewer_blocks(open_ctx, orc):
+    # Plummer N = 4096, eps = 4/N, eta = 1e-3 to t = 1/16: the DS driver with
+    # the noise-aware step choice (relative force error 1e-6) takes fewer
+    # blocks than with the plain criterion, and its energy error stays within
+    # 3x the larger of the plain DS and the FP64 runs' (plus 1e-10 absolute).
+    n, t_end, eta = 4096, 0.0625, 1e-3
+    eps2 = (4.0 / n) ** 2
+    m, x, v = ics.plummer(n, 1)
+    E0 = orc.energy(m, x, v, eps2)
+    cid = open_ctx(n, n)
+    out = {}
+    for name, prec, noise in (("plain", g6.G6X_PREC_DS, 0.0), ("aware", g6.G6X_PREC_DS, 1e-6),
+                              ("fp64", g6.G6X_PREC_FP64, 0.0)):
+        g6.g6x_set_precision(cid, prec)
+        sim = g6.G6HSim(cid, m, x, v, eps2, eta)
+        try:
+            for bad in (-1e-7, 1.0, float("nan")):
+                with pytest.raises(g6.G6Error):
+                    sim.set_force_noise(bad)
+            sim.set_force_noise(noise)
+            sim.run(t_end)
+            st = sim.state()
+            assert np.all(st["t"] == t_end)
+            out[name] = (sim.stats()["nblocks"],
+                         abs(orc.energy(m, st["x"], st["v"], eps2) / E0 - 1))
+        finally:
+            sim.close()
+    assert out["aware"][0] < out["plain"][0], out
+    assert out["aware"][1] <= 3 * max(out["plain"][1], out["fp64"][1]) + 1e-10, out
