@@ -367,6 +367,9 @@ def main():
     fmax = float(peaks.get("sm_max_mhz") or 2070.0)
     peak = sms * FP32_LANES_PER_SM * 2 * fmax * 1e6 / 1e12
     out_main = d_out.cpu().numpy().view(g6.OUT)
+    # measured packed-FP32 FMA rate (outside the timed region), beside the
+    # derived peak the fraction is taken against
+    probe_tf, probe_ms = g6.g6x_fp32_probe(10000)
 
     # all-FP64 kernel on a subset of the block (its rate is flat in m)
     m64 = min(args.fp64_m, m)
@@ -515,7 +518,12 @@ def main():
                                        % (sms, FP32_LANES_PER_SM, fmax),
                          "frac_at_sampled_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 *
                                                    clocks["sm_mhz"] * 1e6 / 1e12)
-                                                   if clocks.get("sm_mhz") else None)},
+                                                   if clocks.get("sm_mhz") else None),
+                         "fp32_probe": {"tflops": probe_tf, "ms": probe_ms,
+                                        "of_derived_peak": probe_tf / peak,
+                                        "force_frac_of_probe": achieved / probe_tf,
+                                        "how": "g6x_fp32_probe: packed FP32x2 FMA chains, "
+                                               "8 CTAs x 256 threads per SM"}},
             "fp64": {"m": m64, "force_interactions_per_s": rate64,
                      "gflops_60": rate64 * FLOPS_PER_PAIR / 1e9,
                      "ds_force_interactions_per_s_same_m": rateds,

@@ -335,6 +335,18 @@ int g6x_set_wait_limit(double seconds);
  * was reported as the force kernels report it (0 would mean it did not). */
 int g6x_probe_wait_timeout(int clusterid);
 
+/* Measure the FP32 rate the force kernel's roofline is taken against: on
+ * the current device, every SM runs 8 CTAs of 256 threads, each thread 8
+ * independent chains of packed FP32x2 fused multiply-adds, iters x 16 per
+ * chain; the launch is timed with CUDA events after one short warm-up
+ * launch.  *tflops = 4 flop x 16 x 8 x iters x threads / time (TFLOP/s);
+ * *ms (may be NULL) = the timed launch.  Not in the paper: the roofline
+ * check of the FP32-bound force (Sect. 3.1 counts 60 flop per pair).
+ * Allocates and frees its own small buffer, stream and events.  Returns 0,
+ * G6_EINVAL (iters outside 1 .. 2^24, tflops NULL), G6_ENODEV, G6_ENOMEM or
+ * G6_EIO. */
+int g6x_fp32_probe(int iters, double *tflops, double *ms);
+
 /* Number of kernels launched on the context's stream since g6_open. */
 long long g6x_launch_count(int clusterid);
 

@@ -54,6 +54,7 @@ EXPORTS = [
     "g6h_stats", "g6h_profile", "g6h_destroy", "g6h_checkpoint", "g6h_restore",
     "g6h_set_neighbour_radius", "g6h_neighbour_stats", "g6h_run_blocks",
     "g6h_correct_block_ex", "g6h_set_force_noise", "g6hb_set_force_noise",
+    "g6x_fp32_probe",
     "g6x_batch_create", "g6x_batch_destroy", "g6x_batch_irecs", "g6x_batch_results",
     "g6x_batch_set_j", "g6x_batch_set_j_many", "g6x_batch_calc", "g6x_batch_launch_count",
     "g6x_batch_set_schedule", "g6x_batch_get_schedule", "g6x_batch_autotune", "g6hb_autotune",
@@ -115,6 +116,7 @@ def lib():
             "g6h_correct_block_ex": (I, [I, D, P, P, D, D, D, P, P, P, P, P, P, P, D]),
             "g6h_set_force_noise": (I, [P, D]),
             "g6hb_set_force_noise": (I, [P, D]),
+            "g6x_fp32_probe": (I, [I, P, P]),
             "g6h_create": (P, [I, I, P, P, P, D, D, D, D, D, P]),
             "g6h_run": (I, [P, D]),
             "g6h_run_blocks": (C.c_longlong, [P, D, C.c_longlong]),
@@ -366,6 +368,14 @@ def g6x_probe_wait_timeout(cid):
     """Code reported by one bounded wait that nothing completes (G6_ETIMEDOUT
     when the timeout path works)."""
     return lib().g6x_probe_wait_timeout(cid)
+
+
+def g6x_fp32_probe(iters=10000):
+    """Measured packed-FP32 FMA rate of the current device: (TFLOP/s, ms of
+    the timed launch)."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(lib().g6x_fp32_probe(int(iters), C.byref(tf), C.byref(ms)), "g6x_fp32_probe")
+    return tf.value, ms.value
 
 
 def g6x_set_timing(cid, enable=True):
