@@ -1841,17 +1841,31 @@ ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
         gmul = ni > 2048 ? 2 : 1;
     } else if (list) {
         v = ni <= 32 ? 6 : 5;
-    } else if (ni <= 32) {
-        v = 4;                       // 16 x 16 threads, one i each
-    } else if (ni <= 128) {
-        v = 14;                      // 16 x 16 threads, two i each
-    } else if (ni <= 256) {
-        v = 15;                      // 32 x 8 threads, two i each
-    } else if (ni <= 2048) {
-        v = 16;                      // 64 x 4 threads, two i each
     } else {
-        v = 0;                       // 128 threads, two i each, whole j-tiles
-        gmul = 2;
+        // The widest i-tile the block size allows, narrowed while the work
+        // line would hold too few (i-tile, j-tile) units for the SMs: wide
+        // tiles need many j-tiles to keep every CTA busy, so small j-sets
+        // take narrower tiles at the same m.
+        struct Shape {
+            int v, itile, max_ni;
+            long long min_units;
+        };
+        static constexpr Shape shapes[] = {
+            {0, 256, INT_MAX, 16384},  // 128 threads, two i each, whole j-tiles
+            {16, 128, 2048, 4096},     // 64 x 4 threads, two i each
+            {15, 64, 256, 2048},       // 32 x 8 threads, two i each
+            {14, 32, 128, 2048},       // 16 x 16 threads, two i each
+            {4, 16, 32, 0},            // 16 x 16 threads, one i each
+        };
+        const long long jtl = nj_pad / JT;
+        int k = 0;
+        while (shapes[k].min_units > 0
+               && (ni <= shapes[k + 1].max_ni
+                   || (long long)((ni + shapes[k].itile - 1) / shapes[k].itile) * jtl
+                          < shapes[k].min_units))
+            ++k;
+        v = shapes[k].v;
+        gmul = v == 0 ? 2 : 1;
     }
     // a fused-prediction shape only where the caller can use it (DS
     // predictor, the j-store current); otherwise its separate twin

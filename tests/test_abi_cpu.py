@@ -160,3 +160,21 @@ def test_c_client_builds_against_the_header_and_library(lib, tmp_path):
                        capture_output=True, text=True)
     if not os.path.exists("/dev/nvidia0"):
         assert r.returncode == -g6gb.G6_ENODEV          # no GPU here
+
+
+def test_block_latency_tool_builds_and_refuses_bad_arguments(lib, tmp_path):
+    """The per-call latency tool (a plain C program against the header and
+    the library) compiles warning-free; bad arguments end it before any
+    library call, and without a GPU its first call fails cleanly."""
+    import subprocess
+    libdir = os.path.join(ROOT, "paper_0902_4463_gb300")
+    exe = str(tmp_path / "block_latency")
+    cmd = ["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-O1",
+           os.path.join(libdir, "block_latency.c"), "-I", os.path.join(ROOT, "include"),
+           "-L", libdir, "-lg6gb", "-Wl,-rpath," + libdir, "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert subprocess.run([exe, "100", "10"]).returncode == 2
+    if not os.path.exists("/dev/nvidia0"):
+        r = subprocess.run([exe, "8192", "1"], capture_output=True, text=True)
+        assert r.returncode == 1 and "setup failed" in r.stderr
