@@ -4,8 +4,10 @@
  * block time (g6_set_ti, so the j-particles are predicted again), starts
  * the force (g6calc_firsthalf) and waits for it (g6calc_lasthalf2).  Prints
  * one JSON line per m: the host wall time of each call (microseconds, mean
- * over the repetitions after 20 warm-up ones), the device time of each
- * phase from the library's CUDA-event timing, and the launch configuration.
+ * over the repetitions after 20 warm-up ones), then, from a second pass of
+ * the same repetitions with the library's CUDA-event timing on (which also
+ * launches every kernel on its own, without programmatic dependent launch),
+ * the device time of each phase, and the launch configuration.
  * Arguments: n, repetitions, and "tune" to run the autotuner first.
  * Particles are uniform in a unit cube (the cost does not depend on their
  * positions); eps2 = 1e-4. */
@@ -72,8 +74,8 @@ int main(int argc, char **argv)
         const int mm = ms[mi];
         double tset = 0, tti = 0, tfh = 0, tlh = 0;
         int off = 0;
-        for (int r = 0; r < reps + 20; ++r) {
-            if (r == 20)
+        for (int r = 0; r < 2 * reps + 20; ++r) {
+            if (r == reps + 20)
                 g6x_set_timing(0, 1);
             t += 1.0 / 1048576.0;
             for (int k = 0; k < mm; ++k)
@@ -97,7 +99,7 @@ int main(int argc, char **argv)
                 fprintf(stderr, "m = %d: error %d\n", mm, rc);
                 return 1;
             }
-            if (r >= 20) {
+            if (r >= 20 && r < reps + 20) {
                 tset += t1 - t0;
                 tti += t2 - t1;
                 tfh += t3 - t2;

@@ -702,6 +702,11 @@ int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_
             return rc;
     }
     cudaError_t e;
+    // Programmatic dependent launch of the force kernel and the reduction
+    // (each starts behind its predecessor and waits for it on the device),
+    // except under per-phase event timing, whose events must bracket whole
+    // kernels.
+    const bool pdl = !c.timing;
     const long long seg_per_tile = (long long)cfg.grid / cfg.n_itile + 1;
     if (!cfg.list && cfg.prec == G6X_PREC_DS && seg_per_tile <= 4) {
         // one launch: the last CTA of each i-tile reduces it (K3 fused into
@@ -726,18 +731,18 @@ int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_
         }
         PhaseTimer pt(c, PH_FORCE);
         e = g6::launch_force_fused(cfg, c.pred, d_irec, ni, eps2, c.d_part, c.d_err, d_out,
-                                   c.js.idx, c.d_tcnt, c.stream, fpp);
+                                   c.js.idx, c.d_tcnt, c.stream, fpp, pdl);
         c.launches += 1;
     } else {
         {
             PhaseTimer pt(c, PH_FORCE);
             e = g6::launch_force(cfg, c.pred, d_irec, ni, eps2, c.d_part, c.d_nbl_part,
-                                 c.d_nbc_part, c.d_err, c.stream, fpp);
+                                 c.d_nbc_part, c.d_err, c.stream, fpp, pdl);
         }
         if (e == cudaSuccess) {
             PhaseTimer pt(c, PH_REDUCE);
             e = g6::launch_reduce(cfg, c.d_part, c.d_nbl_part, c.d_nbc_part, c.js.idx, ni,
-                                  d_out, c.d_nbl, c.d_nblen, c.stream);
+                                  d_out, c.d_nbl, c.d_nblen, c.stream, pdl);
         }
         c.launches += 2;
     }

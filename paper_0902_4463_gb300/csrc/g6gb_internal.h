@@ -206,17 +206,21 @@ cudaError_t launch_update_predict(int kind, JStore js, Pred p, int nj, int nj_pa
 cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
                          const g6x_irec *d_irec, int ni, double eps2,
                          void *part, int *nbl_part, int *nbc_part,
-                         int *d_err, cudaStream_t s, const FusedPred *fp = nullptr);
+                         int *d_err, cudaStream_t s, const FusedPred *fp = nullptr,
+                         bool pdl = false);
 // DS force with the reduction fused in (no neighbour lists): the last CTA
 // to finish an i-tile writes its results to out.  tcnt holds one counter per
 // i-tile, zero before the launch and left zero by a launch that completes.
 cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
                                const g6x_irec *d_irec, int ni, double eps2, void *part,
                                int *d_err, g6x_out *out, const int *jidx, unsigned *tcnt,
-                               cudaStream_t s, const FusedPred *fp = nullptr);
+                               cudaStream_t s, const FusedPred *fp = nullptr,
+                               bool pdl = false);
 cudaError_t launch_reduce(const ForceConfig &cfg, const void *part,
                           const int *nbl_part, const int *nbc_part,
                           const int *jidx, int ni, g6x_out *d_out,
-                          int *d_nbl, int *d_nblen, cudaStream_t s);
+                          int *d_nbl, int *d_nblen, cudaStream_t s, bool pdl = false);
+// pdl: launch with programmatic stream serialization (the kernel may start
+// behind its predecessor in s and waits for it before reading anything).
 
 }  // namespace g6

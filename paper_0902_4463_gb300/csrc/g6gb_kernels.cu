@@ -129,6 +129,22 @@ __device__ __forceinline__ void fence_proxy_async_global()
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor in the stream still runs;
+// grid_dep_wait() blocks until every prerequisite grid has completed and its
+// memory operations are visible (a no-op without such a predecessor), and
+// grid_dep_launch() lets the dependent grid be scheduled once every CTA of
+// this grid has issued it or exited.
+__device__ __forceinline__ void grid_dep_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void grid_dep_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Knuth's TwoSum: s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
@@ -395,6 +411,7 @@ __global__ void __launch_bounds__(JT) k_predict(JStore js, Pred p, int nj, int n
                                                 double t, const g6x_jrec *__restrict__ rec,
                                                 const int *__restrict__ toff, int ntiles_all)
 {
+    grid_dep_launch();              // the force kernel may be scheduled behind this one
     __shared__ int s_lo[JT / 32], s_hi[JT / 32];
     const int ntiles_pred = nj_pad / JT;
     const int ntiles = UPD ? ntiles_all : ntiles_pred;
@@ -558,6 +575,10 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     constexpr int NS = FP ? FP_NSTAGE : NSTAGE;         // stages in the ring
     static_assert(!LIST || TJ == 1, "neighbour lists need whole j-tiles per thread");
     static_assert(JT % (2 * TJ) == 0, "j-tile must split into j-pairs evenly");
+    // nothing is read before the predecessor (prediction, or an earlier
+    // reduction of the same partial buffers) has completed
+    grid_dep_wait();
+    grid_dep_launch();
 
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     float *stage_buf = reinterpret_cast<float *>(dyn_smem);
@@ -1244,6 +1265,8 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
 template <bool LIST>
 __global__ void __launch_bounds__(128) k_force_64(const ForceArgs a)
 {
+    grid_dep_wait();                // the FP64 prediction (see k_force_ds)
+    grid_dep_launch();
     constexpr int TI = 128;
     __shared__ double4_32a sp[JT], sv[JT];
     const int tid = threadIdx.x;
@@ -1474,6 +1497,7 @@ __device__ __forceinline__ g6x_out result_of(const PS &acc, const int *jidx)
 template <class PT>
 __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a)
 {
+    grid_dep_wait();                // the partials of the force kernel
     const int lane = threadIdx.x & 31;
     const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= a.ni)
@@ -1527,6 +1551,7 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a)
 template <class PT>
 __global__ void __launch_bounds__(256) k_reduce_wide(const ReduceArgs a)
 {
+    grid_dep_wait();                // the partials of the force kernel
     const long long i = blockIdx.x;
     if (i >= a.ni)
         return;
@@ -1978,10 +2003,33 @@ static bool set_fused_pred(ForceArgs &a, const ForceConfig &cfg, const FusedPred
     return fp->rec == nullptr || (cfg.n_itile == 1 && fp->toff != nullptr);
 }
 
+// Launch fn, with programmatic stream serialization when pdl is set (the
+// kernel then starts behind its predecessor and waits in grid_dep_wait).
+template <class... Args>
+cudaError_t launch_maybe_pdl(void (*fn)(Args...), int grid, int threads, int smem,
+                             cudaStream_t s, bool pdl, Args... args)
+{
+    if (!pdl) {
+        fn<<<grid, threads, smem, s>>>(args...);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)grid);
+    lc.blockDim = dim3((unsigned)threads);
+    lc.dynamicSmemBytes = (size_t)smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, fn, args...);
+}
+
 cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
                          const g6x_irec *d_irec, int ni, double eps2,
                          void *part, int *nbl_part, int *nbc_part,
-                         int *d_err, cudaStream_t s, const FusedPred *fp)
+                         int *d_err, cudaStream_t s, const FusedPred *fp, bool pdl)
 {
     if (cfg.work <= 0)
         return cudaSuccess;
@@ -2006,14 +2054,13 @@ cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
     if (!set_fused_pred(a, cfg, fp))
         return cudaErrorInvalidValue;
     const Variant &v = kVariants[cfg.variant];
-    v.fn<<<cfg.grid, v.threads, v.smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_maybe_pdl(v.fn, cfg.grid, v.threads, v.smem, s, pdl, a);
 }
 
 cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
                                const g6x_irec *d_irec, int ni, double eps2, void *part,
                                int *d_err, g6x_out *out, const int *jidx, unsigned *tcnt,
-                               cudaStream_t s, const FusedPred *fp)
+                               cudaStream_t s, const FusedPred *fp, bool pdl)
 {
     if (cfg.work <= 0)
         return cudaSuccess;
@@ -2042,14 +2089,13 @@ cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
     if (!set_fused_pred(a, cfg, fp))
         return cudaErrorInvalidValue;
     const Variant &v = kVariants[cfg.variant];
-    v.fn<<<cfg.grid, v.threads, v.smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_maybe_pdl(v.fn, cfg.grid, v.threads, v.smem, s, pdl, a);
 }
 
 cudaError_t launch_reduce(const ForceConfig &cfg, const void *part,
                           const int *nbl_part, const int *nbc_part,
                           const int *jidx, int ni, g6x_out *d_out, int *d_nbl,
-                          int *d_nblen, cudaStream_t s)
+                          int *d_nblen, cudaStream_t s, bool pdl)
 {
     if (ni <= 0)
         return cudaSuccess;
@@ -2075,21 +2121,17 @@ cudaError_t launch_reduce(const ForceConfig &cfg, const void *part,
     if (cfg.prec == G6X_PREC_FP64) {
         if (wide) {
             pin_carveout(k_reduce_wide<Partial64>);
-            k_reduce_wide<Partial64><<<blocks, 256, 0, s>>>(a);
-        } else {
-            pin_carveout(k_reduce<Partial64>);
-            k_reduce<Partial64><<<blocks, 256, 0, s>>>(a);
+            return launch_maybe_pdl(k_reduce_wide<Partial64>, blocks, 256, 0, s, pdl, a);
         }
-    } else {
-        if (wide) {
-            pin_carveout(k_reduce_wide<PartialDS>);
-            k_reduce_wide<PartialDS><<<blocks, 256, 0, s>>>(a);
-        } else {
-            pin_carveout(k_reduce<PartialDS>);
-            k_reduce<PartialDS><<<blocks, 256, 0, s>>>(a);
-        }
+        pin_carveout(k_reduce<Partial64>);
+        return launch_maybe_pdl(k_reduce<Partial64>, blocks, 256, 0, s, pdl, a);
     }
-    return cudaGetLastError();
+    if (wide) {
+        pin_carveout(k_reduce_wide<PartialDS>);
+        return launch_maybe_pdl(k_reduce_wide<PartialDS>, blocks, 256, 0, s, pdl, a);
+    }
+    pin_carveout(k_reduce<PartialDS>);
+    return launch_maybe_pdl(k_reduce<PartialDS>, blocks, 256, 0, s, pdl, a);
 }
 
 // ---------------------------------------------------------------- batch ---
