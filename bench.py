@@ -314,7 +314,7 @@ def main():
         g6.g6x_set_j_dev(CID, mm, d_j.data_ptr())
         g6.g6x_calc_dev(CID, T_BLK, n, mm, d_i.data_ptr(), EPS2, 0, d_o.data_ptr())
 
-    def timed(mm, d_j, d_i, d_o, steps, warmup, sampler=None):
+    def timed(mm, d_j, d_i, d_o, steps, warmup, sampler=None, median=False):
         for _ in range(warmup):
             step(mm, d_j, d_i, d_o)
         g6.g6x_sync(CID)
@@ -323,7 +323,7 @@ def main():
         torch.cuda.synchronize()
         g6.g6x_set_timing(CID, True)
         l0 = g6.g6x_launch_count(CID)
-        total = 0.0
+        times = []
         ctx = sampler if sampler is not None else _Null()
         with ctx:
             for _ in range(steps):
@@ -334,7 +334,7 @@ def main():
                 step(mm, d_j, d_i, d_o)
                 e1.record(stream)
                 e1.synchronize()
-                total += e0.elapsed_time(e1)
+                times.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
@@ -342,7 +342,8 @@ def main():
         ms_ph, cnt = g6.g6x_get_timing(CID)
         g6.g6x_set_timing(CID, False)
         g6.g6x_sync(CID)
-        return total / steps, ms_ph, cnt, launches
+        step_ms = float(np.median(times)) if median else sum(times) / steps
+        return step_ms, ms_ph, cnt, launches
 
     uuid = None
     try:
@@ -397,8 +398,9 @@ def main():
             d_is = to_dev(irec[:mm])
             d_js = to_dev(jrec_act[:mm])
             d_os = torch.empty(mm * g6.OUT.itemsize, dtype=torch.uint8, device=dev)
-            reps = 5 if mm < (1 << 17) else 2
-            mss, phs, cs, _ = timed(mm, d_js, d_is, d_os, reps, 2)
+            # the median of 10 CUDA-event timed steps after 3 warm-up steps;
+            # the phase times are means over the same 10 steps
+            mss, phs, cs, _ = timed(mm, d_js, d_is, d_os, 10, 3, median=True)
             c = g6.g6x_last_config(CID)
             fms = phs[2] / max(1, cs[2])
             sweep.append({"m": mm, "ms_step": round(mss, 5),

@@ -396,3 +396,38 @@ def test_hermite_driver_noise_allowance_takes_fewer_blocks(open_ctx, orc):
             sim.close()
     assert out["aware"][0] < out["plain"][0], out
     assert out["aware"][1] <= 3 * max(out["plain"][1], out["fp64"][1]) + 1e-10, out
+
+
+@pytest.mark.parametrize("variant", [-1, 17])
+def test_config3_block_sizes_sampled_at_full_size(open_ctx, orc, variant):
+    # N = 2^20 (j predicted from t_j = 0 to 2^-10), active sets = the first m
+    # entries of the seeded permutation for m = 16 ... 65536, in the launch
+    # configuration the built-in heuristic picks (variant -1) and, for the
+    # small sizes, in the 16 x 16 x 1 shape that predicts its own j-tiles
+    # (variant 17): up to 128 sampled i per size against the oracle.
+    n, eps2, t_blk = 1 << 20, 1e-6, 2.0 ** -10
+    st = ics.taylor_state(n, 3, t_blk, dt_levels=None)
+    cid = open_ctx(n, 65536)
+    load_j(cid, st["x0"], st["v0"], st["m"], st["a0"], st["j0"], st["tj"])
+    idx = np.arange(n)
+    perm = ics.permutation(n, 7)
+    xp, vp = orc.predict(st["x0"], st["v0"], st["a0"], st["j0"], st["tj"], t_blk)
+    sizes = (16, 64) if variant == 17 else (16, 128, 1024, 8192, 65536)
+    g6.g6x_set_variant(cid, variant)
+    try:
+        for m in sizes:
+            act = perm[:m]
+            acc, jerk, pot, nnb = sweep(cid, n, st["x0"][act], st["v0"][act], act, eps2, t_blk)
+            if variant >= 0:
+                assert g6.g6x_last_config(cid)["variant"] == variant
+            s = np.linspace(0, m - 1, min(m, 128)).astype(int)
+            oa, oj, op, onn, onr = orc.force(st["x0"][act[s]], st["v0"][act[s]], act[s], xp, vp,
+                                             st["m"], idx, eps2)
+            ea, ej = rel_err_vec(acc[s], oa), rel_err_vec(jerk[s], oj)
+            ep = np.abs(pot[s] - op) / np.abs(op)
+            assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5, (m, np.median(ea), ea.max())
+            assert np.median(ej) <= 1e-6 and ej.max() <= 1e-4, (m, np.median(ej), ej.max())
+            assert np.median(ep) <= 1e-6 and ep.max() <= 1e-5, (m, np.median(ep), ep.max())
+            check_nn(onn, onr, nnb[s], st["x0"][act[s]], xp, idx)
+    finally:
+        g6.g6x_set_variant(cid, -1)
