@@ -314,6 +314,19 @@ int g6x_load_tuning(const char *path);
 /* Forget every tuned entry (back to the built-in choice).  Returns 0. */
 int g6x_clear_tuning(void);
 
+/* The launch a calculation of ni i-particles against nj j-particles would
+ * get in precision mode `mode` (G6X_PREC_*), with neighbour lists if list
+ * != 0, on a GPU of sm_count SMs, from the autotuner's table when it has an
+ * entry for this block size and from the built-in choice otherwise; nothing
+ * is launched.  out[0..5] = kernel variant, threads along i, threads along
+ * j, i-particles per thread, grid size, j-tiles.  The grid counts the
+ * resident CTAs per SM of the current device; a host without one gets one
+ * CTA per SM.  Not in the paper (it places one block per multiprocessor,
+ * Sect. 2.3).  Returns 0 or G6_EINVAL (unknown mode, nj or ni outside
+ * 1 .. 2^30, sm_count outside 1 .. 4096, out NULL, lists with
+ * G6X_PREC_DS_DSSUB). */
+int g6x_plan_launch(int mode, int nj, int ni, int list, int sm_count, int out[6]);
+
 /* Launch statistics of the last calculation: kernel variant id, threads
  * along i and j, i-particles per thread, grid size and j-tiles.  Any pointer
  * may be NULL. */

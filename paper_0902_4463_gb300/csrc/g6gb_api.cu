@@ -1713,6 +1713,28 @@ int g6x_get_timing(int cid, double ms[4], long long count[4])
     return 0;
 }
 
+int g6x_plan_launch(int mode, int nj, int ni, int list, int sm_count, int out[6])
+{
+    if ((mode != G6X_PREC_DS && mode != G6X_PREC_FP64 && mode != G6X_PREC_DS_X64
+         && mode != G6X_PREC_DS_DSSUB)
+        || nj < 1 || nj > (1 << 30) || ni < 1 || ni > (1 << 30) || sm_count < 1
+        || sm_count > 4096 || !out || (list && mode == G6X_PREC_DS_DSSUB))
+        return G6_EINVAL;
+    const int prec = mode == G6X_PREC_FP64 || mode == G6X_PREC_DS_DSSUB ? mode : G6X_PREC_DS;
+    const int nj_pad = round_up(nj, JT);
+    const ForceConfig f = g6::choose_config(prec, ni, nj_pad, list ? 1 : 0, sm_count, -1, 0,
+                                            mode == G6X_PREC_DS && !list);
+    // without a device the occupancy query fails: clear its error
+    cudaGetLastError();
+    out[0] = f.variant;
+    out[1] = f.ti;
+    out[2] = f.tj;
+    out[3] = f.nper;
+    out[4] = f.grid;
+    out[5] = f.jtiles;
+    return 0;
+}
+
 int g6x_last_config(int cid, int *variant, int *ti, int *tj, int *ni_per, int *grid,
                     int *jtiles)
 {

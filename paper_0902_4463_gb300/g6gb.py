@@ -54,7 +54,7 @@ EXPORTS = [
     "g6h_stats", "g6h_profile", "g6h_destroy", "g6h_checkpoint", "g6h_restore",
     "g6h_set_neighbour_radius", "g6h_neighbour_stats", "g6h_run_blocks",
     "g6h_correct_block_ex", "g6h_set_force_noise", "g6hb_set_force_noise",
-    "g6x_fp32_probe",
+    "g6x_fp32_probe", "g6x_plan_launch",
     "g6x_batch_create", "g6x_batch_destroy", "g6x_batch_irecs", "g6x_batch_results",
     "g6x_batch_set_j", "g6x_batch_set_j_many", "g6x_batch_calc", "g6x_batch_launch_count",
     "g6x_batch_set_schedule", "g6x_batch_get_schedule", "g6x_batch_autotune", "g6hb_autotune",
@@ -117,6 +117,7 @@ def lib():
             "g6h_set_force_noise": (I, [P, D]),
             "g6hb_set_force_noise": (I, [P, D]),
             "g6x_fp32_probe": (I, [I, P, P]),
+            "g6x_plan_launch": (I, [I, I, I, I, I, P]),
             "g6h_create": (P, [I, I, P, P, P, D, D, D, D, D, P]),
             "g6h_run": (I, [P, D]),
             "g6h_run_blocks": (C.c_longlong, [P, D, C.c_longlong]),
@@ -368,6 +369,15 @@ def g6x_probe_wait_timeout(cid):
     """Code reported by one bounded wait that nothing completes (G6_ETIMEDOUT
     when the timeout path works)."""
     return lib().g6x_probe_wait_timeout(cid)
+
+
+def g6x_plan_launch(mode, nj, ni, list_=False, sm_count=152):
+    """The launch a calculation would get (no GPU needed): dict with variant,
+    ti, tj, ni_per, grid, jtiles."""
+    out = np.zeros(6, dtype=np.int32)
+    _check(lib().g6x_plan_launch(int(mode), int(nj), int(ni), int(bool(list_)), int(sm_count),
+                                 out.ctypes.data_as(C.c_void_p)), "g6x_plan_launch")
+    return dict(zip(("variant", "ti", "tj", "ni_per", "grid", "jtiles"), (int(v) for v in out)))
 
 
 def g6x_fp32_probe(iters=10000):

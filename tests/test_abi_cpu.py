@@ -178,3 +178,47 @@ def test_block_latency_tool_builds_and_refuses_bad_arguments(lib, tmp_path):
     if not os.path.exists("/dev/nvidia0"):
         r = subprocess.run([exe, "8192", "1"], capture_output=True, text=True)
         assert r.returncode == 1 and "setup failed" in r.stderr
+
+
+def test_launch_plan_heuristic_without_a_gpu(lib):
+    """The built-in launch choice (g6x_plan_launch, no GPU needed): the
+    widest i-tile that the block size allows, narrowed while the work line
+    holds too few (i-tile, j-tile) units -- the shapes the autotuner measured
+    best at N = 2^20 and at N = 32768."""
+    g6gb.g6x_clear_tuning()
+    ds = g6gb.G6X_PREC_DS
+
+    def shape(nj, ni, mode=ds, list_=False):
+        p = g6gb.g6x_plan_launch(mode, nj, ni, list_)
+        assert p["jtiles"] == (nj + 255) // 256
+        assert 1 <= p["grid"] <= -(-ni // (p["ti"] * p["ni_per"])) * p["jtiles"]
+        return p["ti"], p["tj"], p["ni_per"]
+
+    big, small = 1 << 20, 32768
+    assert shape(big, 16) == (16, 16, 1)
+    assert shape(big, 128) == (16, 16, 2)
+    assert shape(big, 256) == (32, 8, 2)
+    assert shape(big, 2048) == (64, 4, 2)
+    assert shape(big, 4096) == (128, 1, 2)
+    assert shape(big, big) == (128, 1, 2)
+    assert shape(small, 256) == (16, 16, 1)
+    assert shape(small, 1024) == (32, 8, 2)
+    assert shape(small, 4096) == (64, 4, 2)
+    assert shape(small, small) == (128, 1, 2)
+    # a smaller j-set never gets a wider i-tile at the same block size
+    for ni in (16, 64, 200, 1000, 3000, 20000):
+        widths = [np.prod(shape(nj, ni)[::2]) for nj in (4096, 32768, 131072, 1 << 20)]
+        assert widths == sorted(widths), (ni, widths)
+    # other modes keep their own kernels
+    assert g6gb.g6x_plan_launch(g6gb.G6X_PREC_FP64, big, 4096)["variant"] == 7
+    assert g6gb.g6x_plan_launch(g6gb.G6X_PREC_FP64, big, 4096, True)["variant"] == 8
+    assert g6gb.g6x_plan_launch(ds, big, 4096, True)["variant"] == 5
+    assert g6gb.g6x_plan_launch(ds, big, 16, True)["variant"] == 6
+    assert g6gb.g6x_plan_launch(g6gb.G6X_PREC_DS_DSSUB, big, 16)["variant"] == 22
+    assert g6gb.g6x_plan_launch(g6gb.G6X_PREC_DS_DSSUB, big, 4096)["variant"] == 21
+    out = np.zeros(6, dtype=np.int32)
+    p = out.ctypes.data_as(ctypes.c_void_p)
+    for args in ((9, big, 16, 0, 152), (ds, 0, 16, 0, 152), (ds, big, 0, 0, 152),
+                 (ds, big, 16, 0, 0), (g6gb.G6X_PREC_DS_DSSUB, big, 16, 1, 152)):
+        assert lib.g6x_plan_launch(*args, p) == g6gb.G6_EINVAL
+    assert lib.g6x_plan_launch(ds, big, 16, 0, 152, None) == g6gb.G6_EINVAL

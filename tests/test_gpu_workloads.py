@@ -431,3 +431,22 @@ def test_config3_block_sizes_sampled_at_full_size(open_ctx, orc, variant):
             check_nn(onn, onr, nnb[s], st["x0"][act[s]], xp, idx)
     finally:
         g6.g6x_set_variant(cid, -1)
+
+
+def test_launch_plan_matches_the_launch(open_ctx):
+    # g6x_plan_launch names the variant and grid that a calculation of the
+    # same size then uses (built-in choice, no tuning table)
+    import torch
+    g6.g6x_clear_tuning()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 32768
+    m, x, v = ics.plummer(n, 2)
+    cid = open_ctx(n, n)
+    load_j(cid, x, v, m)
+    for ni in (1, 16, 256, 1024, 4096, n):
+        sel = np.arange(ni)
+        sweep(cid, n, x[sel], v[sel], sel, 1e-5, 0.0)
+        got = g6.g6x_last_config(cid)
+        plan = g6.g6x_plan_launch(g6.G6X_PREC_DS, n, ni, False, sms)
+        assert (got["variant"], got["grid"], got["jtiles"]) == \
+            (plan["variant"], plan["grid"], plan["jtiles"]), (ni, got, plan)
