@@ -212,3 +212,21 @@ def test_checkpoint_parser_rejects_damage(tmp_path):
     assert _restore(tmp_path, _ckpt_bytes(buckets=[(0.125, [0, 0]), (0.25, [1])])) == g6gb.G6_EINVAL
     assert _restore(tmp_path, _ckpt_bytes(buckets=[(0.125, [0, 2])])) == g6gb.G6_EINVAL
     assert _restore(tmp_path, _ckpt_bytes(dt=(0.125, 0.0, 0.125))) == g6gb.G6_EINVAL
+
+
+# ------------------------------------------------ host thread pool
+def test_host_thread_pool(tmp_path):
+    """The library's host pool (g6gb_pool.h) in a standalone C++ test: every
+    index once, back-to-back runs, sleeping workers, nested and concurrent
+    callers (a deadlock would trip the timeout)."""
+    import os
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    exe = str(tmp_path / "pool_test")
+    r = subprocess.run(["g++", "-std=c++17", "-O2", "-Wall", "-Wextra", "-Werror", "-pthread",
+                        "-I", os.path.join(root, "paper_0902_4463_gb300", "csrc"),
+                        os.path.join(root, "tests", "cpp", "pool_test.cpp"), "-o", exe],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "pool ok" in r.stdout, r.stderr
