@@ -308,7 +308,9 @@ int g6x_get_timing(int clusterid, double ms[4], long long count[4]);
 int g6x_autotune(int clusterid, int nj, int m_max, const char *path);
 
 /* Load a table written by g6x_autotune (g6_open loads the file named by
- * env G6GB_TUNE_FILE once).  Returns entries read or G6_EINVAL. */
+ * env G6GB_TUNE_FILE once): lines "precision log2(m) variant grid_multiplier"
+ * ('#' starts a comment line).  The whole file is checked first; on any bad
+ * line nothing changes.  Returns entries read or G6_EINVAL. */
 int g6x_load_tuning(const char *path);
 
 /* Forget every tuned entry (back to the built-in choice).  Returns 0. */

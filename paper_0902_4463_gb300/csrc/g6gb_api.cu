@@ -20,6 +20,7 @@
 #include <sstream>
 #include <string>
 #include <utility>
+#include <array>
 #include <vector>
 
 namespace {
@@ -1551,8 +1552,9 @@ extern "C" int g6x_load_tuning(const char *path)
     std::ifstream f(path);
     if (!f)
         return G6_EINVAL;
+    // the whole file is checked before any entry takes effect
     std::string line;
-    int n = 0;
+    std::vector<std::array<int, 4>> rows;
     while (std::getline(f, line)) {
         if (line.empty() || line[0] == '#')
             continue;
@@ -1564,10 +1566,11 @@ extern "C" int g6x_load_tuning(const char *path)
             || v >= g6::variant_count() || g < 1 || g > 8
             || g6::variant_info(v).prec != prec || g6::variant_info(v).list)
             return G6_EINVAL;
-        g6::tune_set(prec, b, v, g);
-        ++n;
+        rows.push_back({prec, b, v, g});
     }
-    return n;
+    for (const auto &r : rows)
+        g6::tune_set(r[0], r[1], r[2], r[3]);
+    return (int)rows.size();
 }
 
 extern "C" int g6x_clear_tuning(void)

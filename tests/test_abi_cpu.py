@@ -222,3 +222,35 @@ def test_launch_plan_heuristic_without_a_gpu(lib):
                  (ds, big, 16, 0, 0), (g6gb.G6X_PREC_DS_DSSUB, big, 16, 1, 152)):
         assert lib.g6x_plan_launch(*args, p) == g6gb.G6_EINVAL
     assert lib.g6x_plan_launch(ds, big, 16, 0, 152, None) == g6gb.G6_EINVAL
+
+
+def test_tuning_table_is_consulted_and_loads_all_or_nothing(lib, tmp_path):
+    """A table in the autotuner's format ("precision log2(m) variant
+    grid_multiplier") overrides the built-in launch choice for its block-size
+    buckets (larger buckets reuse the largest tuned one); the fused-prediction
+    shapes only where the predictor allows them; a file with one bad line
+    changes nothing; clearing restores the built-in choice."""
+    ds, x64 = g6gb.G6X_PREC_DS, g6gb.G6X_PREC_DS_X64
+    big = 1 << 20
+    g6gb.g6x_clear_tuning()
+    assert g6gb.g6x_plan_launch(ds, big, 16)["variant"] == 4
+    good = tmp_path / "good.txt"
+    good.write_text("# comment\n0 4 17 1\n0 5 14 2\n1 4 7 1\n")
+    assert g6gb.g6x_load_tuning(str(good)) == 3
+    assert g6gb.g6x_plan_launch(ds, big, 16)["variant"] == 17
+    assert g6gb.g6x_plan_launch(x64, big, 16)["variant"] == 4      # its separate twin
+    p32 = g6gb.g6x_plan_launch(ds, big, 32)
+    assert p32["variant"] == 14
+    assert g6gb.g6x_plan_launch(ds, big, 4096)["variant"] == 14    # largest bucket reused
+    assert g6gb.g6x_plan_launch(g6gb.G6X_PREC_FP64, big, 16)["variant"] == 7
+    for bad in ("0 4 99 1\n", "0 4 7 1\n", "0 4 5 1\n", "0 4 4 9\n", "2 4 4 1\n", "0 4\n"):
+        f = tmp_path / "bad.txt"
+        f.write_text("0 6 16 1\n" + bad)
+        with np.testing.assert_raises(g6gb.G6Error):
+            g6gb.g6x_load_tuning(str(f))
+        assert g6gb.g6x_plan_launch(ds, big, 64)["variant"] == 14, bad   # nothing applied
+    with np.testing.assert_raises(g6gb.G6Error):
+        g6gb.g6x_load_tuning(str(tmp_path / "missing.txt"))
+    g6gb.g6x_clear_tuning()
+    assert g6gb.g6x_plan_launch(ds, big, 16)["variant"] == 4
+    assert g6gb.g6x_plan_launch(ds, big, 4096)["variant"] == 0
