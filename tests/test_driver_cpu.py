@@ -214,6 +214,32 @@ def test_checkpoint_parser_rejects_damage(tmp_path):
     assert _restore(tmp_path, _ckpt_bytes(dt=(0.125, 0.0, 0.125))) == g6gb.G6_EINVAL
 
 
+def test_large_blocks_on_host_threads_match_the_serial_corrector():
+    """Blocks of 8192 and more particles are corrected on the host thread
+    pool; the results equal those of the same particles corrected in serial
+    pieces, bit for bit (steps below the minimum counted the same way)."""
+    build.build()
+    rng = np.random.default_rng(21)
+    n = 30000
+    dt = np.ldexp(1.0, -rng.integers(3, 20, n))
+    t_blk = 0.75
+    xp, vp = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    a0, j0 = rng.normal(size=(n, 3)), rng.normal(size=(n, 3)) * 3
+    a1 = a0 + j0 * dt[:, None] + rng.normal(size=(n, 3)) * dt[:, None] ** 2
+    j1 = j0 + rng.normal(size=(n, 3)) * dt[:, None] * 50
+    args = (t_blk, t_blk - dt, dt, 0.01, 0.5, 2.0 ** -12, xp, vp, a0, j0, a1, j1)
+    x1, v1, dtn, small = g6gb.g6h_correct_block(*args)
+    assert small > 0                         # some steps fall below the floor
+    xs, vs, ds, ss = [], [], [], 0
+    for k0 in range(0, n, 5000):
+        sl = slice(k0, k0 + 5000)
+        part = g6gb.g6h_correct_block(t_blk, (t_blk - dt)[sl], dt[sl], 0.01, 0.5, 2.0 ** -12,
+                                      xp[sl], vp[sl], a0[sl], j0[sl], a1[sl], j1[sl])
+        xs.append(part[0]); vs.append(part[1]); ds.append(part[2]); ss += part[3]
+    assert np.array_equal(x1, np.concatenate(xs)) and np.array_equal(v1, np.concatenate(vs))
+    assert np.array_equal(dtn, np.concatenate(ds)) and small == ss
+
+
 # ------------------------------------------------ host thread pool
 def test_host_thread_pool(tmp_path):
     """The library's host pool (g6gb_pool.h) in a standalone C++ test: every
