@@ -706,8 +706,9 @@ int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_
     // Programmatic dependent launch of the force kernel and the reduction
     // (each starts behind its predecessor and waits for it on the device),
     // except under per-phase event timing, whose events must bracket whole
-    // kernels.
-    const bool pdl = !c.timing;
+    // kernels, and on the all-FP64 path, whose block steps it made about 2x
+    // slower.
+    const bool pdl = !c.timing && cfg.prec != G6X_PREC_FP64;
     const long long seg_per_tile = (long long)cfg.grid / cfg.n_itile + 1;
     if (!cfg.list && cfg.prec == G6X_PREC_DS && seg_per_tile <= 4) {
         // one launch: the last CTA of each i-tile reduces it (K3 fused into
