@@ -21,6 +21,64 @@ def _unit(v):
 # ------------------------------------------------------------------ forces --
 # Sect. 2.3 (calculation step): softened acceleration, jerk and potential.
 
+@pytest.mark.parametrize("eps2", [0.0, 1e-3])
+def test_summed_forces_match_high_precision_brute_force(orc, eps2):
+    """Eight particles, every i against every j (self excluded by index),
+    evaluated independently in 50-digit decimal arithmetic from the same
+    binary64 inputs: the summed softened acceleration, jerk and potential of
+    the oracle agree to a few ulps of the largest term, and its nearest
+    neighbour is the one the exact squared distances (rational arithmetic)
+    give."""
+    import decimal
+    from fractions import Fraction
+    rng = np.random.default_rng(17)
+    n = 8
+    x = rng.normal(size=(n, 3))
+    v = rng.normal(size=(n, 3))
+    m = rng.uniform(0.1, 1.0, n)
+    idx = np.arange(n)
+    acc, jerk, pot, nnb, nnr2 = orc.force(x, v, idx, x, v, m, idx, eps2)
+    ctx = decimal.Context(prec=50)
+    D = lambda f: ctx.create_decimal(float(f))          # exact binary64 -> decimal
+    e2 = D(eps2)
+    for i in range(n):
+        a = [decimal.Decimal(0)] * 3
+        jk = [decimal.Decimal(0)] * 3
+        p = decimal.Decimal(0)
+        scale_a = scale_j = scale_p = 0.0
+        best, best_j = None, -1
+        for j in range(n):
+            if j == i:
+                continue
+            r = [ctx.subtract(D(x[j, d]), D(x[i, d])) for d in range(3)]
+            u = [ctx.subtract(D(v[j, d]), D(v[i, d])) for d in range(3)]
+            r2 = ctx.add(ctx.add(ctx.multiply(r[0], r[0]), ctx.multiply(r[1], r[1])),
+                         ctx.multiply(r[2], r[2]))
+            s2 = ctx.add(r2, e2)
+            s = ctx.sqrt(s2)
+            inv3 = ctx.divide(1, ctx.multiply(s2, s))
+            rv = sum((ctx.multiply(r[d], u[d]) for d in range(3)), decimal.Decimal(0))
+            mj = D(m[j])
+            for d in range(3):
+                a[d] = ctx.add(a[d], ctx.multiply(ctx.multiply(mj, inv3), r[d]))
+                t = ctx.subtract(u[d], ctx.divide(ctx.multiply(3 * rv, r[d]), s2))
+                jk[d] = ctx.add(jk[d], ctx.multiply(ctx.multiply(mj, inv3), t))
+            p = ctx.subtract(p, ctx.divide(mj, s))
+            scale_a = max(scale_a, float(mj * ctx.divide(1, s2)))
+            scale_j = max(scale_j, float(mj * inv3 * (abs(rv) * 3 / s + sum(abs(q) for q in u))))
+            scale_p = max(scale_p, float(ctx.divide(mj, s)))
+            exact = sum((Fraction(float(x[j, d])) - Fraction(float(x[i, d]))) ** 2
+                        for d in range(3))
+            if best is None or exact < best:
+                best, best_j = exact, j
+        for d in range(3):
+            assert abs(acc[i, d] - float(a[d])) <= 64 * 2.0 ** -52 * scale_a * n, (i, d)
+            assert abs(jerk[i, d] - float(jk[d])) <= 64 * 2.0 ** -52 * scale_j * n, (i, d)
+        assert abs(pot[i] - float(p)) <= 64 * 2.0 ** -52 * scale_p * n, i
+        assert nnb[i] == best_j
+        assert nnr2[i] == pytest.approx(float(best), rel=1e-14)
+
+
 @pytest.mark.parametrize("eps2", [0.0, 0.04])
 def test_two_body_closed_form(orc, eps2):
     e = _unit([0.3, -0.7, 0.2])
