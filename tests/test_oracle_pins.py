@@ -290,6 +290,32 @@ def test_predictor_truncation_error_on_circular_motion(orc):
         assert xp[0, 2] == 0.0 and vp[0, 2] == 0.0
 
 
+def test_predictor_exact_for_constant_jerk(orc):
+    """Motion with constant jerk is a cubic in time, which Eq. 1 and Eq. 2
+    reproduce exactly: the prediction equals the exact rational evaluation
+    of x0 + v0 dt + a0 dt^2/2 + j dt^3/6 (and its derivative) to within the
+    rounding of the FP64 sums, for many particles, each predicted over its
+    own time since t_j (dt = t_blk - t_j)."""
+    from fractions import Fraction as F
+    rng = np.random.default_rng(29)
+    n = 64
+    x0, v0 = rng.normal(size=(n, 3)) * 10, rng.normal(size=(n, 3))
+    a0, j0 = rng.normal(size=(n, 3)), rng.normal(size=(n, 3)) * 5
+    tj = 0.5 - np.ldexp(1.0, -rng.integers(1, 12, n))
+    t_blk = 0.5
+    xp, vp = orc.predict(x0, v0, a0, j0, tj, t_blk)
+    for i in range(n):
+        dt = F(t_blk) - F(float(tj[i]))
+        for d in range(3):
+            ex = (F(float(x0[i, d])) + F(float(v0[i, d])) * dt + F(float(a0[i, d])) * dt ** 2 / 2
+                  + F(float(j0[i, d])) * dt ** 3 / 6)
+            ev = F(float(v0[i, d])) + F(float(a0[i, d])) * dt + F(float(j0[i, d])) * dt ** 2 / 2
+            sx = abs(x0[i, d]) + abs(v0[i, d] * float(dt)) + abs(a0[i, d]) + abs(j0[i, d])
+            sv = abs(v0[i, d]) + abs(a0[i, d]) + abs(j0[i, d])
+            assert abs(xp[i, d] - float(ex)) <= 8 * 2.0 ** -52 * sx, (i, d)
+            assert abs(vp[i, d] - float(ev)) <= 8 * 2.0 ** -52 * sv, (i, d)
+
+
 # -------------------------------------------------------------- integrator --
 # Sect. 2: 4th-order Hermite predictor-corrector with block time steps.
 
