@@ -254,3 +254,17 @@ def test_tuning_table_is_consulted_and_loads_all_or_nothing(lib, tmp_path):
     g6gb.g6x_clear_tuning()
     assert g6gb.g6x_plan_launch(ds, big, 16)["variant"] == 4
     assert g6gb.g6x_plan_launch(ds, big, 4096)["variant"] == 0
+
+
+def test_driver_setters_refuse_bad_arguments_without_a_gpu(lib):
+    """The drivers' option setters validate before touching any state: a NULL
+    driver handle is refused, as is a force-noise allowance outside [0, 1)
+    in the stand-alone corrector."""
+    assert lib.g6h_set_force_noise(None, 0.1) == g6gb.G6_EINVAL
+    assert lib.g6hb_set_force_noise(None, 0.1) == g6gb.G6_EINVAL
+    assert lib.g6h_set_neighbour_radius(None, 1e-4) == g6gb.G6_EINVAL
+    z = np.zeros((1, 3))
+    for bad in (-1e-9, float("nan")):
+        with pytest.raises(g6gb.G6Error):
+            g6gb.g6h_correct_block(0.5, [0.25], [0.25], 0.01, 0.5, 2.0 ** -40, z, z, z, z, z, z,
+                                   force_noise=bad)
