@@ -12,7 +12,9 @@ Metric: interactions/s = m * N / step time, and Gflop/s at 60 flop per pair
 of the active block (its rate is flat in m) for the DS-over-FP64 speed-up.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--n N] [--sweep] [--fp64-m M] [--no-cpu-baseline]
+                  [--n N] [--m M] [--sweep] [--fp64-m M] [--no-cpu-baseline]
+  python bench.py --latency --n N [--reps R]        per-call cost of small block steps
+  python bench.py --experiment scaling|eta [...]     paper-style Hermite runs (Sect. 3)
 """
 import argparse
 import hashlib
@@ -60,6 +62,21 @@ def parse():
                     help="DS predictor: the paper's DS + SP add (ds) or an FP64 add (ds_x64)")
     ap.add_argument("--variant", type=int, default=-1)
     ap.add_argument("--grid", type=int, default=0)
+    ap.add_argument("--latency", action="store_true",
+                    help="per-call cost of small block steps through the GRAPE calls at --n")
+    ap.add_argument("--reps", type=int, default=200, help="--latency: repetitions per size")
+    ap.add_argument("--experiment", choices=["scaling", "eta"], default=None,
+                    help="paper-style Hermite runs (Sect. 3): wall clock, Gflop/s and mean "
+                         "block size against N, or dE/E against eta")
+    ap.add_argument("--nmin", type=int, default=1024)
+    ap.add_argument("--nmax", type=int, default=262144)
+    ap.add_argument("--fp64-max", type=int, default=0)
+    ap.add_argument("--ns", type=int, nargs="+", default=[32768, 131072])
+    ap.add_argument("--etas", type=float, nargs="+",
+                    default=[1e-4, 3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 0.1, 0.3])
+    ap.add_argument("--fp64", action="store_true", help="--experiment eta: also all-FP64 runs")
+    ap.add_argument("--noise", type=float, default=0.0,
+                    help="--experiment eta: relative force error the DS step choice allows for")
     return ap.parse_args()
 
 
@@ -258,10 +275,132 @@ def run_reference(args):
     return 0
 
 
+def run_latency(args):
+    """Per-call cost of one block step through the GRAPE calling sequence
+    (Sect. 2.1, 2.5): for block sizes m = 1 .. 4096 against n j-particles
+    (uniform in a unit cube, eps2 = 1e-4), each repetition updates the m
+    j-records (g6x_set_j_particles), sets a new block time (g6_set_ti, so the
+    j-particles are predicted again), starts the force (g6calc_firsthalf) and
+    waits for it (g6calc_lasthalf2).  One JSON line per m: the host wall time
+    of each call (microseconds, mean over the repetitions after 20 warm-up
+    ones; the calls go through ctypes, which adds about a microsecond each),
+    then, from a second pass with the library's CUDA-event timing on (every
+    kernel then launched on its own), the device time of each phase, and the
+    launch configuration."""
+    from paper_0902_4463_gb300 import build as gbuild
+    gbuild.build()
+    from paper_0902_4463_gb300 import g6gb as g6
+    n, reps = args.n, args.reps
+    rng = np.random.default_rng(12345)
+    x = rng.uniform(size=(n, 3))
+    v = rng.uniform(-0.5, 0.5, size=(n, 3))
+    m = np.full(n, 1.0 / n)
+    z = np.zeros((n, 3))
+    idx = np.arange(n, dtype=np.int32)
+    lib = g6.lib()
+    P = g6._p
+    g6.g6x_open_ex(CID, n, 4096)
+    try:
+        g6.g6x_set_j_particles(CID, idx, idx, 0.0, m, z, z, v, x)
+        acc, jerk, pot = np.empty((4096, 3)), np.empty((4096, 3)), np.empty(4096)
+        nnb = np.empty(4096, dtype=np.int32)
+        t = 0.0
+        for mm in (1, 16, 64, 256, 1024, 4096):
+            sel = np.ascontiguousarray(idx[:mm])
+            tj = np.zeros(mm)
+            mj = np.ascontiguousarray(m[:mm])
+            xs, vs = np.ascontiguousarray(x[:mm]), np.ascontiguousarray(v[:mm])
+            zs = np.ascontiguousarray(z[:mm])
+
+            def one():
+                nonlocal t
+                t += 2.0 ** -20
+                tj[:] = t - 2.0 ** -20
+                t0 = time.perf_counter()
+                lib.g6x_set_j_particles(CID, mm, P(sel), P(sel), P(tj), P(mj), P(zs), P(zs),
+                                        P(vs), P(xs))
+                t1 = time.perf_counter()
+                lib.g6_set_ti(CID, t)
+                lib.g6calc_firsthalf(CID, n, mm, P(sel), P(xs), P(vs), None, None, None, 1e-4,
+                                     None)
+                t2 = time.perf_counter()
+                rc = lib.g6calc_lasthalf2(CID, n, mm, None, None, None, 1e-4, None, P(acc),
+                                          P(jerk), P(pot), P(nnb))
+                t3 = time.perf_counter()
+                if rc < 0:
+                    raise g6.G6Error(rc, "g6calc_lasthalf2")
+                return t1 - t0, t2 - t1, t3 - t2
+
+            for _ in range(20):
+                one()
+            tot = np.zeros(3)
+            for _ in range(reps):
+                tot += one()
+            host = tot / reps * 1e6
+            g6.g6x_set_timing(CID, True)
+            for _ in range(reps):
+                one()
+            ms, cnt = g6.g6x_get_timing(CID)
+            g6.g6x_set_timing(CID, False)
+            cfg = g6.g6x_last_config(CID)
+            dev = [ms[k] / max(1, cnt[k]) * 1e3 for k in range(4)]
+            print(json.dumps({"n": n, "m": mm, "set_j_us": host[0], "firsthalf_us": host[1],
+                              "lasthalf_us": host[2], "total_us": float(host.sum()),
+                              "device_us": {"store_predict": dev[0] + dev[1], "force": dev[2],
+                                            "reduce": dev[3]},
+                              "launches_per_step": sum(int(c) for c in cnt) / reps,
+                              "config": cfg}), flush=True)
+    finally:
+        g6.g6_close(CID)
+    return 0
+
+
+def run_experiment(args):
+    """Paper-style experiments on one GPU (Sect. 3) with the library's Hermite
+    block-time-step driver on equal-mass Plummer spheres, to t = 1/4:
+    `scaling` -- wall clock, Gflop/s and mean block size against N (powers of
+    two from --nmin to --nmax, eta = 0.01; all-FP64 runs up to --fp64-max);
+    `eta` -- dE/E against the accuracy parameter at each N of --ns (with
+    --fp64 also the all-FP64 path; --noise R lets the DS step choice allow for
+    a relative force error R).  The paper does not state its softening; these
+    runs use eps = 4/N.  Energies come from one all-FP64 force sweep.  One JSON
+    line per run."""
+    from paper_0902_4463_gb300 import hermite_run
+
+    def one(n, eta, prec, noise=0.0):
+        r = hermite_run.run(n, 1, (4.0 / n) ** 2, eta, 0.25, prec, noise=noise)
+        keep = ("n", "eta", "prec", "eps2", "t_end", "wall_s", "nblocks", "nactive",
+                "mean_block", "interactions_per_s", "gflops_60", "dE_over_E", "synchronised",
+                "force_noise")
+        out = {k: r[k] for k in keep}
+        out["force_s"] = r["profile"]["force_s"]
+        out["host_s"] = r["profile"]["sched_s"] + r["profile"]["correct_s"]
+        print(json.dumps(out), flush=True)
+
+    if args.experiment == "scaling":
+        n = args.nmin
+        while n <= args.nmax:
+            one(n, 0.01, "ds")
+            if n <= args.fp64_max:
+                one(n, 0.01, "fp64")
+            n *= 2
+    else:
+        for n in args.ns:
+            for eta in args.etas:
+                one(n, eta, "ds", args.noise)
+                if args.fp64:
+                    one(n, eta, "fp64")
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.latency:
+        return run_latency(args)
+    if args.experiment:
+        return run_experiment(args)
     ws, rank, local = dist_env()
     import torch
     if ws > 1:

@@ -265,7 +265,8 @@ int g6x_get_predicted(int clusterid, int nj, float *hi, float *lo, float *vel,
  *   - ni > G6X_NOALLOC_NI_MAX, or a launch whose partial sums cannot fit the
  *     array even on a smaller grid, returns G6_EINVAL before any work.
  *   - The first call on each device looks up the array's device address;
- *     make that first call during set-up, before any stream capture.
+ *     make that first call during set-up, before any stream capture.  The
+ *     caller's current device must be the context's (G6_EINVAL otherwise).
  *   - All calls in the process share the array and it keeps the last call's
  *     contents; each call writes every record it reads, so nothing needs
  *     clearing.  Calls that overlap on the GPU (other streams or contexts)
@@ -329,6 +330,21 @@ int g6x_clear_tuning(void);
  * G6X_PREC_DS_DSSUB). */
 int g6x_plan_launch(int mode, int nj, int ni, int list, int sm_count, int out[6]);
 
+/* The compiled force-kernel variants (the numbers g6x_set_variant, the
+ * tuning table and g6x_last_config use).  g6x_variant_info(v, out) fills
+ * out[0..7] = threads along i, thread groups along j, i-particles per
+ * thread, builds neighbour lists (0/1), precision mode (G6X_PREC_*),
+ * predicts its own j-tiles (Eq. 1, Eq. 2 inside the force kernel; 0/1), the
+ * variant of the same shape that reads separately predicted tiles (-1 if
+ * none), and 1 for the warp-specialised small-block kernel (the whole block
+ * is one i-tile of at most threads-along-i x i-per-thread particles; j-store
+ * update, prediction, force and reduction in one launch).  Returns the
+ * number of variants; g6x_variant_info(-1, NULL) returns it alone.  Needs no
+ * GPU.  G6_EINVAL for v outside -1 .. count-1, or out NULL with v >= 0.
+ * Not in the paper: these are this library's shapes of the work split of
+ * Sect. 2.3. */
+int g6x_variant_info(int variant, int out[8]);
+
 /* Launch statistics of the last calculation: kernel variant id, threads
  * along i and j, i-particles per thread, grid size and j-tiles.  Any pointer
  * may be NULL. */
@@ -361,6 +377,15 @@ int g6x_probe_wait_timeout(int clusterid);
  * G6_EINVAL (iters outside 1 .. 2^24, tflops NULL), G6_ENODEV, G6_ENOMEM or
  * G6_EIO. */
 int g6x_fp32_probe(int iters, double *tflops, double *ms);
+
+/* The FP64 counterpart, the roofline denominator of the all-FP64 force
+ * kernel (the comparison kernel of the precision argument, Sect. 2.3): the
+ * same launch shape, each thread 8 independent chains of FP64 fused
+ * multiply-adds, iters x 16 per chain.  *tflops = 2 flop x 16 x 8 x iters x
+ * threads / time.  GB300's FP64 pipe is a small fraction of its FP32 rate,
+ * so a few hundred iters already take milliseconds.  Same ownership and
+ * returns as g6x_fp32_probe. */
+int g6x_fp64_probe(int iters, double *tflops, double *ms);
 
 /* Number of kernels launched on the context's stream since g6_open. */
 long long g6x_launch_count(int clusterid);

@@ -300,8 +300,7 @@ void free_ctx(Ctx &c)
     g6::JStore &js = c.js;
     // d_jst, d_irec, d_out and d_err are device aliases of mapped host
     // buffers, freed with them below
-    void *dptrs[] = {js.x0, js.xds, js.xds2, js.t0, js.v0m, js.a2f, js.j6f, js.v64, js.a264,
-                     js.j664, js.idx, c.pred.pt, c.pred.trange, c.pred.p64, c.pred.v64,
+    void *dptrs[] = {js.x0, js.raw, js.v64, js.a264, js.j664, js.idx, c.pred.pt, c.pred.trange, c.pred.p64, c.pred.v64,
                      c.d_part, c.d_tcnt, c.d_nbl_part, c.d_nbc_part, c.d_nbl, c.d_nblen};
     for (void *p : dptrs)
         dev_free(p);
@@ -667,6 +666,28 @@ int predict_and_force(Ctx &c, int nj, int ni, const g6x_irec *d_irec, double eps
     return rc;
 }
 
+// At least n zeroed arrival counters for the reductions inside the force
+// launch (zeroed again after a launch that may have stopped mid-count).
+int ensure_counters(Ctx &c, size_t n)
+{
+    if (n > c.tcnt_cap) {
+        size_t cap = n + n / 4 + 64;
+        unsigned *q = (unsigned *)dev_alloc(cap * sizeof(*q));
+        if (!q)
+            return G6_ENOMEM;
+        dev_free(c.d_tcnt);
+        c.d_tcnt = q;
+        c.tcnt_cap = cap;
+        c.tcnt_dirty = true;
+    }
+    if (c.tcnt_dirty) {
+        if (cudaMemsetAsync(c.d_tcnt, 0, c.tcnt_cap * sizeof(unsigned), c.stream) != cudaSuccess)
+            return cuda_err(cudaGetLastError());
+        c.tcnt_dirty = false;
+    }
+    return 0;
+}
+
 int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_irec,
               double eps2, g6x_out *d_out, bool folded)
 {
@@ -710,27 +731,23 @@ int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_
     // slower.
     const bool pdl = !c.timing && cfg.prec != G6X_PREC_FP64;
     const long long seg_per_tile = (long long)cfg.grid / cfg.n_itile + 1;
-    if (!cfg.list && cfg.prec == G6X_PREC_DS && seg_per_tile <= 4) {
+    if (cfg.ws) {
+        // small block: store, prediction, force and reduction in one launch
+        rc = ensure_counters(c, g6::counter_slots(cfg));
+        if (rc)
+            return rc;
+        PhaseTimer pt(c, PH_FORCE);
+        e = g6::launch_force_ws(cfg, d_irec, ni, eps2, nj, c.d_part, c.d_tcnt, d_out, c.js.idx,
+                                c.d_err, fpa, c.stream, pdl);
+        c.launches += 1;
+    } else if (!cfg.list && cfg.prec == G6X_PREC_DS && seg_per_tile <= 4) {
         // one launch: the last CTA of each i-tile reduces it (K3 fused into
         // K2) when every tile has only a few partials (large blocks); with
         // many partials per tile that serial tail costs more than the
         // separate K3, which spreads the sums over many CTAs
-        if ((size_t)cfg.n_itile > c.tcnt_cap) {
-            size_t n = (size_t)cfg.n_itile + cfg.n_itile / 4 + 64;
-            unsigned *q = (unsigned *)dev_alloc(n * sizeof(*q));
-            if (!q)
-                return G6_ENOMEM;
-            dev_free(c.d_tcnt);
-            c.d_tcnt = q;
-            c.tcnt_cap = n;
-            c.tcnt_dirty = true;
-        }
-        if (c.tcnt_dirty) {
-            if (cudaMemsetAsync(c.d_tcnt, 0, c.tcnt_cap * sizeof(unsigned), c.stream)
-                != cudaSuccess)
-                return cuda_err(cudaGetLastError());
-            c.tcnt_dirty = false;
-        }
+        rc = ensure_counters(c, g6::counter_slots(cfg));
+        if (rc)
+            return rc;
         PhaseTimer pt(c, PH_FORCE);
         e = g6::launch_force_fused(cfg, c.pred, d_irec, ni, eps2, c.d_part, c.d_err, d_out,
                                    c.js.idx, c.d_tcnt, c.stream, fpp, pdl);
@@ -823,12 +840,7 @@ int g6x_open_ex(int cid, int nj_max, int ni_max)
     g6::JStore &js = c.js;
     js.cap = c.cap;
     js.x0 = (double *)dev_alloc(3 * n * sizeof(double));
-    js.xds = (float4 *)dev_alloc(n * sizeof(float4));
-    js.xds2 = (float2 *)dev_alloc(n * sizeof(float2));
-    js.t0 = (double *)dev_alloc(n * sizeof(double));
-    js.v0m = (float4 *)dev_alloc(n * sizeof(float4));
-    js.a2f = (float4 *)dev_alloc(n * sizeof(float4));
-    js.j6f = (float4 *)dev_alloc(n * sizeof(float4));
+    js.raw = (unsigned char *)dev_alloc((n / JT) * g6::RAW_TILE_BYTES);
     js.v64 = (double4_32a *)dev_alloc(n * sizeof(double4_32a));
     js.a264 = (double4_32a *)dev_alloc(n * sizeof(double4_32a));
     js.j664 = (double4_32a *)dev_alloc(n * sizeof(double4_32a));
@@ -842,7 +854,7 @@ int g6x_open_ex(int cid, int nj_max, int ni_max)
         c.h_err = (int *)host_alloc_mapped(sizeof(int), &de);
         c.d_err = (int *)de;
     }
-    if (!js.x0 || !js.xds || !js.xds2 || !js.t0 || !js.v0m || !js.a2f || !js.j6f || !js.v64 || !js.a264
+    if (!js.x0 || !js.raw || !js.v64 || !js.a264
         || !js.j664 || !js.idx || !c.pred.pt || !c.pred.trange || !c.pred.p64
         || !c.pred.v64 || !c.d_err || !c.h_err)
         rc = G6_ENOMEM;
@@ -1320,19 +1332,26 @@ static __device__ __align__(256) unsigned char g6x_noalloc_scratch[G6X_NOALLOC_S
 namespace {
 
 constexpr size_t kNoallocSlots = G6X_NOALLOC_SCRATCH_BYTES / sizeof(g6::Partial);
+// the header states the array as 147456 records of 72 bytes
+static_assert(sizeof(g6::Partial) == 72, "partial slot size the header documents");
+static_assert(kNoallocSlots == 147456, "partial slot count the header documents");
 static_assert(G6X_NOALLOC_SCRATCH_BYTES % sizeof(g6::Partial) == 0,
               "scratch holds a whole number of partial records");
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[kMaxDevices];
 
-// Device address of the scratch array on the current device.
-int noalloc_scratch(void **out)
+// Device address of the scratch array on the context's device `dev`, which
+// must be the caller's current device (the kernels go to the context's
+// stream on that device).
+int noalloc_scratch(int dev, void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
     if (e != cudaSuccess)
         return cuda_err(e);
+    if (cur != dev)
+        return G6_EINVAL;
     if (dev < 0 || dev >= kMaxDevices)
         return G6_ENODEV;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -1377,7 +1396,7 @@ extern "C" int g6x_calc_dev_noalloc(int cid, double ti, int nj, int ni,
             return G6_EINVAL;
     }
     void *scratch = nullptr;
-    int rc = noalloc_scratch(&scratch);
+    int rc = noalloc_scratch(c->dev, &scratch);
     if (rc)
         return rc;
     c->t_set = ti;
@@ -1389,11 +1408,17 @@ extern "C" int g6x_calc_dev_noalloc(int cid, double ti, int nj, int ni,
     // Every record the reduction reads is written by the force kernel of
     // this same call, so nothing left by an earlier call needs clearing.
     g6::Partial *part = static_cast<g6::Partial *>(scratch);
-    cudaError_t e = g6::launch_force(cfg, c->pred, d_irec, ni, eps2, part, nullptr, nullptr,
-                                     c->d_err, c->stream);
-    if (e == cudaSuccess)
+    cudaError_t e;
+    {
+        PhaseTimer pt(*c, PH_FORCE);
+        e = g6::launch_force(cfg, c->pred, d_irec, ni, eps2, part, nullptr, nullptr, c->d_err,
+                             c->stream);
+    }
+    if (e == cudaSuccess) {
+        PhaseTimer pt(*c, PH_REDUCE);
         e = g6::launch_reduce(cfg, part, nullptr, nullptr, c->js.idx, ni, d_out, nullptr,
                               nullptr, c->stream);
+    }
     if (e != cudaSuccess)
         return cuda_err(e);
     c->launches += 2;
@@ -1473,7 +1498,7 @@ extern "C" int g6x_autotune(int cid, int nj, int m_max, const char *path)
         for (int v = 0; v < g6::variant_count() && e == cudaSuccess; ++v) {
             const g6::VariantInfo vi = g6::variant_info(v);
             if (vi.prec != c->prec || vi.list || vi.ti * vi.nper > 16 * m
-                || (vi.fpred && c->pmode != G6X_PREC_DS))
+                || (vi.fpred && c->pmode != G6X_PREC_DS) || (vi.ws && vi.ti * vi.nper < m))
                 continue;
             int occ = g6::variant_occupancy(v);
             if (occ < 1)
@@ -1485,7 +1510,8 @@ extern "C" int g6x_autotune(int cid, int nj, int m_max, const char *path)
                 if (cfg.grid == last_grid)
                     continue;
                 last_grid = cfg.grid;
-                if (grow_dev(c->d_part, c->part_cap, g6::partial_slots(cfg))) {
+                if (grow_dev(c->d_part, c->part_cap, g6::partial_slots(cfg))
+                    || (vi.ws && ensure_counters(*c, g6::counter_slots(cfg)))) {
                     lost_work = true;
                     continue;
                 }
@@ -1500,13 +1526,18 @@ extern "C" int g6x_autotune(int cid, int nj, int m_max, const char *path)
                     if (e == cudaSuccess && !vi.fpred)
                         e = g6::launch_predict(pkind, c->js, c->pred, nj, nj_pad, c->t_set,
                                                c->sm_count, c->stream);
-                    if (e == cudaSuccess)
-                        e = g6::launch_force(cfg, c->pred, d_i, m, 1e-6, c->d_part, nullptr,
-                                             nullptr, c->d_err, c->stream,
-                                             vi.fpred ? &fpa : nullptr);
-                    if (e == cudaSuccess)
-                        e = g6::launch_reduce(cfg, c->d_part, nullptr, nullptr, c->js.idx, m,
-                                              d_o, nullptr, nullptr, c->stream);
+                    if (e == cudaSuccess && vi.ws) {
+                        e = g6::launch_force_ws(cfg, d_i, m, 1e-6, nj, c->d_part, c->d_tcnt, d_o,
+                                                c->js.idx, c->d_err, fpa, c->stream, false);
+                    } else {
+                        if (e == cudaSuccess)
+                            e = g6::launch_force(cfg, c->pred, d_i, m, 1e-6, c->d_part, nullptr,
+                                                 nullptr, c->d_err, c->stream,
+                                                 vi.fpred ? &fpa : nullptr);
+                        if (e == cudaSuccess)
+                            e = g6::launch_reduce(cfg, c->d_part, nullptr, nullptr, c->js.idx,
+                                                  m, d_o, nullptr, nullptr, c->stream);
+                    }
                     if (e == cudaSuccess)
                         e = cudaEventRecord(e1, c->stream);
                     if (e == cudaSuccess)
@@ -1737,6 +1768,25 @@ int g6x_plan_launch(int mode, int nj, int ni, int list, int sm_count, int out[6]
     out[4] = f.grid;
     out[5] = f.jtiles;
     return 0;
+}
+
+int g6x_variant_info(int variant, int out[8])
+{
+    const int n = g6::variant_count();
+    if (variant == -1 && !out)
+        return n;
+    if (variant < 0 || variant >= n || !out)
+        return G6_EINVAL;
+    const g6::VariantInfo v = g6::variant_info(variant);
+    out[0] = v.ti;
+    out[1] = v.tj;
+    out[2] = v.nper;
+    out[3] = v.list;
+    out[4] = v.prec;
+    out[5] = v.fpred;
+    out[6] = v.twin;
+    out[7] = v.ws;
+    return n;
 }
 
 int g6x_last_config(int cid, int *variant, int *ti, int *tj, int *ni_per, int *grid,

@@ -160,7 +160,7 @@ void free_batch(g6x_batch *b)
         cudaStreamSynchronize(b->stream2);
     drop_graph(b);
     g6::JStore &js = b->js;
-    void *dp[] = {js.x0, js.xds, js.xds2, js.t0, js.v0m, js.a2f, js.j6f, js.v64, js.a264,
+    void *dp[] = {js.x0, js.raw, js.v64, js.a264,
                   js.j664, js.idx, b->pred.pt, b->pred.trange, b->pred.p64, b->pred.v64,
                   b->d_tile_cluster, b->d_cl_jtile, b->d_cl_nj};
     for (void *p : dp)
@@ -618,12 +618,7 @@ g6x_batch *g6x_batch_create(int ncl, const int nj[], int precision, int variant,
     g6::JStore &js = b->js;
     js.cap = b->total_slots;
     js.x0 = dalloc<double>(3 * n);
-    js.xds = dalloc<float4>(n);
-    js.xds2 = dalloc<float2>(n);
-    js.t0 = dalloc<double>(n);
-    js.v0m = dalloc<float4>(n);
-    js.a2f = dalloc<float4>(n);
-    js.j6f = dalloc<float4>(n);
+    js.raw = dalloc<unsigned char>((n / JT) * g6::RAW_TILE_BYTES);
     js.v64 = dalloc<double4_32a>(n);
     js.a264 = dalloc<double4_32a>(n);
     js.j664 = dalloc<double4_32a>(n);
@@ -637,7 +632,7 @@ g6x_batch *g6x_batch_create(int ncl, const int nj[], int precision, int variant,
     b->h_out = halloc<g6x_out>(slots_i, &b->d_out);
     b->h_jsort = halloc<g6x_jrec>(slots_i, &b->d_jsort);
     b->h_err = halloc<int>(1, &b->d_err);
-    if (!js.x0 || !js.xds || !js.xds2 || !js.t0 || !js.v0m || !js.a2f || !js.j6f || !js.v64
+    if (!js.x0 || !js.raw || !js.v64
         || !js.a264 || !js.j664 || !js.idx || !b->pred.pt || !b->pred.trange
         || !b->d_tile_cluster || !b->d_cl_jtile || !b->d_cl_nj || !b->h_irec || !b->h_out
         || !b->h_jsort || !b->h_err)

@@ -40,19 +40,31 @@ constexpr size_t PARTIAL_BYTES = sizeof(Partial64) > sizeof(PartialDS) ? sizeof(
                                                                          : sizeof(PartialDS);
 using Partial = Partial64;   // slot-sized unit of partial buffers
 
-// j-memory (the j-store), structure of arrays, capacity `cap` (multiple of JT).
+// One tile of JT j-slots of the raw j-store as one contiguous block, so that
+// a kernel stages a tile with one bulk copy (one stream per tile keeps HBM at
+// full rate; one stream per array would halve it): the planes, each JT
+// entries and 16-byte aligned, are t0 (double), (v, m), a/2, j/6 (float4),
+// (x_hi, y_hi, z_hi, x_lo) (float4), (y_lo, z_lo) (float2), index (int) --
+// 84 B per slot, 21504 B per tile.
+constexpr unsigned RAW_T0 = 0;
+constexpr unsigned RAW_V = RAW_T0 + JT * 8;
+constexpr unsigned RAW_A = RAW_V + JT * 16;
+constexpr unsigned RAW_J = RAW_A + JT * 16;
+constexpr unsigned RAW_XA = RAW_J + JT * 16;
+constexpr unsigned RAW_XB = RAW_XA + JT * 16;
+constexpr unsigned RAW_ID = RAW_XB + JT * 8;
+constexpr unsigned RAW_TILE_BYTES = RAW_ID + JT * 4;
+
+// j-memory (the j-store), capacity `cap` (multiple of JT).
 struct JStore {
-    double *x0;        // 3 planes of cap doubles: x, y, z at t0
-    float4 *xds;       // the same position as double-single: (x_hi, y_hi, z_hi, x_lo)
-    float2 *xds2;      //                                     (y_lo, z_lo)
-    double *t0;        // time of the stored state
-    float4 *v0m;       // (vx, vy, vz, m)              FP32 copy
-    float4 *a2f;       // (ax/2, ay/2, az/2, 0)         FP32 copy
-    float4 *j6f;       // (jx/6, jy/6, jz/6, 0)         FP32 copy
+    double *x0;        // 3 planes of cap doubles: x, y, z at t0 (FP64)
+    unsigned char *raw;    // cap / JT tiles in the layout above: t0, FP32 copies of
+                           // (v, m), a/2, j/6, the position as double-single, index
     double4_32a *v64;      // (vx, vy, vz, m)              FP64 copy
     double4_32a *a264;     // (ax/2, ay/2, az/2, 0)
     double4_32a *j664;     // (jx/6, jy/6, jz/6, 0)
-    int *idx;          // particle index (-1: empty slot)
+    int *idx;          // particle index (-1: empty slot), flat: the same values as
+                       // the tiles' index plane, for the reductions and the FP64 path
     int cap;
 };
 
@@ -90,6 +102,7 @@ struct ForceConfig {
     int smem;          // dynamic shared memory bytes
     int list;          // builds neighbour lists
     int prec;          // G6X_PREC_*
+    int ws;            // warp-specialised small-block kernel (launch_force_ws)
 };
 
 // Shape of one compiled force-kernel variant.
@@ -97,6 +110,9 @@ struct VariantInfo {
     int ti, tj, nper, list, prec;
     int fpred = 0;     // predicts the j-tiles itself (Eq. 1, Eq. 2) from the raw j-store
     int twin = -1;     // for fpred shapes: the same shape reading predicted tiles
+    int ws = 0;        // warp-specialised small-block kernel: the whole block is one
+                       // i-tile, j-tiles streamed by a producer warp, the partials
+                       // reduced inside the launch (two levels)
 };
 
 // What a fused-prediction force kernel needs: the raw j-store, the block
@@ -167,16 +183,31 @@ cudaError_t launch_reduce_batch(int v, int grid, const void *part, const int *ji
                                 g6x_out *d_out, const BatchTables &bt, int blocks,
                                 cudaStream_t s);
 
+// The warp-specialised small-block variants (g6gb_small.cu) follow the
+// others in one numbering: variant_count() covers both tables.
 int variant_count();
 VariantInfo variant_info(int v);
+int ws_variant_count();
+VariantInfo ws_variant_info(int k);
+int ws_variant_smem(int k);
+int ws_variant_occupancy(int k);
+// CTAs per first-level group of the small-block kernel's partial reduction
+int ws_group_size(int grid);
+// partial records (level 0 and level 1) a small-block launch writes
+size_t ws_partial_slots(int grid, int itile);
+
 // Resident CTAs per SM of variant v (0 on error).
 int variant_occupancy(int v);
 // Pick a variant and grid for ni i-particles against nj_pad j-particles.
 // allow_fpred: a fused-prediction shape may be chosen (otherwise its twin).
 ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
                           int force_variant, int force_grid, bool allow_fpred = false);
+// Whether the built-in choice takes the small-block kernel (where allowed).
+extern bool g_ws_default;
 // Number of Partial slots a launch with this configuration writes.
 size_t partial_slots(const ForceConfig &cfg);
+// Arrival counters a launch with this configuration needs (zero before it).
+size_t counter_slots(const ForceConfig &cfg);
 
 // Autotuning table (see g6x_autotune): per precision and power-of-two
 // bucket of ni, the force variant and grid multiplier to use.
@@ -216,6 +247,13 @@ cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
                                int *d_err, g6x_out *out, const int *jidx, unsigned *tcnt,
                                cudaStream_t s, const FusedPred *fp = nullptr,
                                bool pdl = false);
+// One small-block launch (cfg.ws; cfg.grid <= cfg.jtiles, ni <= cfg.itile):
+// the j-store update of fp.rec (if any), prediction, force and reduction
+// into out; part holds partial_slots(cfg) records, cnt counter_slots(cfg)
+// counters, zero before the launch and left zero by a launch that completes.
+cudaError_t launch_force_ws(const ForceConfig &cfg, const g6x_irec *d_irec, int ni, double eps2,
+                            int nj, void *part, unsigned *cnt, g6x_out *out, const int *jidx,
+                            int *d_err, const FusedPred &fp, cudaStream_t s, bool pdl);
 cudaError_t launch_reduce(const ForceConfig &cfg, const void *part,
                           const int *nbl_part, const int *nbc_part,
                           const int *jidx, int ni, g6x_out *d_out,

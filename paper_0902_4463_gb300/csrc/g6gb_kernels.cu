@@ -25,7 +25,7 @@
 // NSTAGE-deep ring, so the loads of later tiles overlap the pair loop.  Every
 // mbarrier wait is bounded; on expiry the kernel records G6_ETIMEDOUT in the
 // error word, waits (bounded) for its own copies in flight and returns.
-#include "g6gb_internal.h"
+#include "g6gb_device.cuh"
 
 #include <climits>
 #include <cmath>
@@ -37,148 +37,6 @@ namespace {
 
 constexpr int NSTAGE = 3;
 constexpr int FP_NSTAGE = 2;        // raw-tile stages of the fused-prediction kernels
-constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s per mbarrier wait
-
-// One j-tile of the raw j-store arrays as staged by the force kernel with
-// fused prediction: t0, (v, m), a/2, j/6, (x_hi, y_hi, z_hi, x_lo),
-// (y_lo, z_lo), index -- 84 B per particle, every part 16-byte aligned.
-constexpr unsigned RAW_T0 = 0;
-constexpr unsigned RAW_V = RAW_T0 + JT * 8;
-constexpr unsigned RAW_A = RAW_V + JT * 16;
-constexpr unsigned RAW_J = RAW_A + JT * 16;
-constexpr unsigned RAW_XA = RAW_J + JT * 16;
-constexpr unsigned RAW_XB = RAW_XA + JT * 16;
-constexpr unsigned RAW_ID = RAW_XB + JT * 8;
-constexpr unsigned RAW_TILE_BYTES = RAW_ID + JT * 4;
-
-__device__ __forceinline__ float rsqrt_approx(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
-                 :: "r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for phase `parity` of an mbarrier for at most limit_ns.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
-                                                  unsigned long long limit_ns)
-{
-    if (mbar_try_wait(bar, parity))
-        return true;
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        for (int k = 0; k < 32; ++k)
-            if (mbar_try_wait(bar, parity))
-                return true;
-        if (global_ns() - t0 > limit_ns)
-            return false;
-    }
-}
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src,
-                                         uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes"
-                 " [%0], [%1], %2, [%3];"
-                 :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void fence_barrier_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// Order this thread's earlier global stores before later bulk asynchronous
-// copies (the async proxy) that read them.
-__device__ __forceinline__ void fence_proxy_async_global()
-{
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
-// Programmatic dependent launch: a kernel launched with programmatic stream
-// serialization may start while its predecessor in the stream still runs;
-// grid_dep_wait() blocks until every prerequisite grid has completed and its
-// memory operations are visible (a no-op without such a predecessor), and
-// grid_dep_launch() lets the dependent grid be scheduled once every CTA of
-// this grid has issued it or exited.
-__device__ __forceinline__ void grid_dep_wait()
-{
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
-__device__ __forceinline__ void grid_dep_launch()
-{
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-// Knuth's TwoSum: s + e == a + b exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// (ah, al) += (bh, bl) in compensated FP32: TwoSum of the high parts, the
-// low parts added to the error, renormalised (Fast2Sum).
-__device__ __forceinline__ void ds_acc(float &ah, float &al, float bh, float bl)
-{
-    float s, e;
-    two_sum(ah, bh, s, e);
-    e = __fadd_rn(e, __fadd_rn(al, bl));
-    ah = __fadd_rn(s, e);
-    al = __fsub_rn(e, __fsub_rn(ah, s));
-}
-
-// Work line helpers: CTA c owns [begin(c), begin(c+1)).
-__device__ __forceinline__ long long work_begin(long long c, long long W, long long G)
-{
-    return c * W / G;
-}
-
-// Largest c with work_begin(c) <= p, i.e. the CTA that owns position p.
-__device__ __forceinline__ long long work_owner(long long p, long long W, long long G)
-{
-    return ((p + 1) * G - 1) / W;
-}
-
-// Far-away massless stand-in for padding and empty j-slots: every pair term
-// it produces is exactly zero (r^2 overflows to +inf, rsqrt(+inf) = 0).
-constexpr double FAR = 1e30;
 
 }  // namespace
 
@@ -191,43 +49,20 @@ __global__ void k_init_store(JStore js)
         js.x0[k] = FAR;
         js.x0[js.cap + k] = FAR;
         js.x0[2 * js.cap + k] = FAR;
-        js.xds[k] = make_float4((float)FAR, (float)FAR, (float)FAR, 0.f);
-        js.xds2[k] = make_float2(0.f, 0.f);
-        js.t0[k] = 0.0;
-        js.v0m[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        js.a2f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        js.j6f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        js_xds(js, k) = make_float4((float)FAR, (float)FAR, (float)FAR, 0.f);
+        js_xds2(js, k) = make_float2(0.f, 0.f);
+        js_t0(js, k) = 0.0;
+        js_v0m(js, k) = make_float4(0.f, 0.f, 0.f, 0.f);
+        js_a2f(js, k) = make_float4(0.f, 0.f, 0.f, 0.f);
+        js_j6f(js, k) = make_float4(0.f, 0.f, 0.f, 0.f);
         js.v64[k] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
         js.a264[k] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
         js.j664[k] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
         js.idx[k] = -1;
+        js_idx(js, k) = -1;
     }
 }
 
-// Store one j-particle record in its j-memory slot (the j-store update of
-// Sect. 2.1: only corrected particles travel to the GPU each step).
-__device__ __forceinline__ void store_record(const g6x_jrec &r, const JStore &js)
-{
-    const int a = r.address;
-    if (a < 0 || a >= js.cap)
-        return;
-    js.x0[a] = r.x[0];
-    js.x0[js.cap + a] = r.x[1];
-    js.x0[2 * js.cap + a] = r.x[2];
-    const float hx = __double2float_rn(r.x[0]), hy = __double2float_rn(r.x[1]),
-                hz = __double2float_rn(r.x[2]);
-    js.xds[a] = make_float4(hx, hy, hz, __double2float_rn(r.x[0] - (double)hx));
-    js.xds2[a] = make_float2(__double2float_rn(r.x[1] - (double)hy),
-                             __double2float_rn(r.x[2] - (double)hz));
-    js.t0[a] = r.tj;
-    js.v0m[a] = make_float4((float)r.v[0], (float)r.v[1], (float)r.v[2], (float)r.mass);
-    js.a2f[a] = make_float4((float)r.a2[0], (float)r.a2[1], (float)r.a2[2], 0.f);
-    js.j6f[a] = make_float4((float)r.j6[0], (float)r.j6[1], (float)r.j6[2], 0.f);
-    js.v64[a] = make_double4_32a(r.v[0], r.v[1], r.v[2], r.mass);
-    js.a264[a] = make_double4_32a(r.a2[0], r.a2[1], r.a2[2], 0.0);
-    js.j664[a] = make_double4_32a(r.j6[0], r.j6[1], r.j6[2], 0.0);
-    js.idx[a] = r.index;
-}
 
 // K0: one thread per record; addresses within one launch are distinct (the
 // host staging keeps one record per address).
@@ -260,17 +95,6 @@ __global__ void k_irec_from_store(JStore js, g6x_irec *out, int m)
 
 // ----------------------------------------------------------------- K1 ---
 
-// DS + SP addition of Sect. 2.2: (hi, lo) + d with the FP32 operations of a
-// TwoSum of hi and d, the low part added in, and a final renormalisation
-// (Fast2Sum) -- ten FP32 operations.
-__device__ __forceinline__ void ds_add_f(float hi, float lo, float d, float &rh, float &rl)
-{
-    float s, e;
-    two_sum(hi, d, s, e);
-    e = __fadd_rn(e, lo);
-    rh = __fadd_rn(s, e);
-    rl = __fsub_rn(e, __fsub_rn(rh, s));
-}
 
 // Records one tile's range of particle indices (empty slots excluded);
 // called by all JT threads of the CTA with their own slot's index.
@@ -298,43 +122,13 @@ __device__ __forceinline__ void tile_index_range(int *s_lo, int *s_hi, int id, b
     __syncthreads();
 }
 
-// Eq. 1 and Eq. 2 for one j-slot k < nj, written as the tiled DS layout:
-// the paper's form (Sect. 2.2) -- Taylor increment dt (v + dt (a/2 + dt j/6))
-// in FP32, added to the double-single x0 by the DS + SP addition, velocity in
-// FP32; only dt = t - t0 is formed in FP64 (block times are exact there).
-// The DS position part of Eq. 1 (hi, lo per component).
-__device__ __forceinline__ void predict_ds_pos(float h, float4 xa, float2 xb, float4 v,
-                                               float4 a, float4 j, float *hi, float *lo)
-{
-    ds_add_f(xa.x, xa.w, h * fmaf(h, fmaf(h, j.x, a.x), v.x), hi[0], lo[0]);
-    ds_add_f(xa.y, xb.x, h * fmaf(h, fmaf(h, j.y, a.y), v.y), hi[1], lo[1]);
-    ds_add_f(xa.z, xb.y, h * fmaf(h, fmaf(h, j.z, a.z), v.z), hi[2], lo[2]);
-}
-
-__device__ __forceinline__ void predict_ds_vals(float h, float4 xa, float2 xb, float4 v,
-                                                float4 a, float4 j, int id, float *o)
-{
-    float hi[3], lo[3];
-    predict_ds_pos(h, xa, xb, v, a, j, hi, lo);
-    const float h3 = 3.0f * h;
-    o[W_XH * JT] = hi[0];
-    o[W_YH * JT] = hi[1];
-    o[W_ZH * JT] = hi[2];
-    o[W_M * JT] = v.w;
-    o[W_XL * JT] = lo[0];
-    o[W_YL * JT] = lo[1];
-    o[W_ZL * JT] = lo[2];
-    o[W_VX * JT] = fmaf(h, fmaf(h3, j.x, 2.0f * a.x), v.x);
-    o[W_VY * JT] = fmaf(h, fmaf(h3, j.y, 2.0f * a.y), v.y);
-    o[W_VZ * JT] = fmaf(h, fmaf(h3, j.z, 2.0f * a.z), v.z);
-    o[W_ID * JT] = __int_as_float(id);
-}
-
+// Eq. 1 and Eq. 2 for one j-slot k < nj in the paper's DS + SP form
+// (predict_ds_vals), written to the tiled DS layout.
 __device__ __forceinline__ void predict_slot_ds(const JStore &js, int k, double t, float *o,
                                                 int id)
 {
-    predict_ds_vals((float)(t - js.t0[k]), js.xds[k], js.xds2[k], js.v0m[k], js.a2f[k],
-                    js.j6f[k], id, o);
+    predict_ds_vals((float)(t - js_t0(js, k)), js_xds(js, k), js_xds2(js, k), js_v0m(js, k),
+                    js_a2f(js, k), js_j6f(js, k), id, o);
 }
 
 // The same with the DS position formed through FP64: the FP32 increment is
@@ -342,9 +136,9 @@ __device__ __forceinline__ void predict_slot_ds(const JStore &js, int k, double 
 __device__ __forceinline__ void predict_slot_ds_x64(const JStore &js, int k, double t, float *o,
                                                     int id)
 {
-    const double dt = t - js.t0[k];
+    const double dt = t - js_t0(js, k);
     const float h = (float)dt;
-    const float4 v = js.v0m[k], a = js.a2f[k], j = js.j6f[k];
+    const float4 v = js_v0m(js, k), a = js_a2f(js, k), j = js_j6f(js, k);
     const double px = js.x0[k] + (double)(h * fmaf(h, fmaf(h, j.x, a.x), v.x));
     const double py = js.x0[js.cap + k] + (double)(h * fmaf(h, fmaf(h, j.y, a.y), v.y));
     const double pz = js.x0[2 * js.cap + k] + (double)(h * fmaf(h, fmaf(h, j.z, a.z), v.z));
@@ -364,26 +158,11 @@ __device__ __forceinline__ void predict_slot_ds_x64(const JStore &js, int k, dou
     o[W_ID * JT] = __int_as_float(id);
 }
 
-__device__ __forceinline__ void far_slot_ds(float *o)
-{
-    o[W_XH * JT] = (float)FAR;
-    o[W_YH * JT] = (float)FAR;
-    o[W_ZH * JT] = (float)FAR;
-    o[W_M * JT] = 0.f;
-    o[W_XL * JT] = 0.f;
-    o[W_YL * JT] = 0.f;
-    o[W_ZL * JT] = 0.f;
-    o[W_VX * JT] = 0.f;
-    o[W_VY * JT] = 0.f;
-    o[W_VZ * JT] = 0.f;
-    o[W_ID * JT] = __int_as_float(-1);
-}
-
 // Eq. 1 and Eq. 2 entirely in FP64, for the FP64 force kernel.
 __device__ __forceinline__ void predict_slot_64(const JStore &js, Pred &p, int k, int nj, double t)
 {
     if (k < nj) {
-        const double h = t - js.t0[k];
+        const double h = t - js_t0(js, k);
         const double4_32a v = js.v64[k], a = js.a264[k], j = js.j664[k];
         const double px = js.x0[k] + h * fma(h, fma(h, j.x, a.x), v.x);
         const double py = js.x0[js.cap + k] + h * fma(h, fma(h, j.y, a.y), v.y);
@@ -428,7 +207,7 @@ __global__ void __launch_bounds__(JT) k_predict(JStore js, Pred p, int nj, int n
             predict_slot_64(js, p, k, nj, t);
         } else {
             float *o = p.pt + (size_t)tile * (JW * JT) + threadIdx.x;
-            const int id = k < nj ? js.idx[k] : -1;
+            const int id = k < nj ? js_idx(js, k) : -1;
             tile_index_range(s_lo, s_hi, id, k < nj && id >= 0, &p.trange[tile]);
             if (k >= nj)
                 far_slot_ds(o);
@@ -466,7 +245,7 @@ __global__ void __launch_bounds__(JT) k_predict_batch(JStore js, Pred p, BatchPr
             predict_slot_64(js, p, slot, valid ? slot + 1 : slot, t);
         } else {
             float *o = p.pt + (size_t)tile * (JW * JT) + threadIdx.x;
-            const int id = valid ? js.idx[slot] : -1;
+            const int id = valid ? js_idx(js, slot) : -1;
             tile_index_range(s_lo, s_hi, id, valid && id >= 0, &p.trange[tile]);
             if (!valid)
                 far_slot_ds(o);
@@ -502,36 +281,6 @@ __device__ __forceinline__ float2 ds_sep2(float2 h, float2 l, float2 nh, float2 
 
 // ----------------------------------------------------------------- K2 ---
 
-struct ForceArgs {
-    const float *pt;                  // DS predicted j, tiled layout
-    const int2 *trange;               // DS per-tile index range
-    const double4_32a *p64, *v64;         // FP64 predicted j
-    const g6x_irec *irec;
-    void *part;                       // PartialDS (DS kernels) or Partial64 (FP64)
-    int *nbl;                         // list entries  [slot][maxnb]
-    int *nbc;                         // list counts   [slot]
-    int *err;
-    long long W;
-    int J;
-    int ni;
-    double eps2;
-    // fused reduction: the last CTA to finish an i-tile reduces it into out
-    g6x_out *out;
-    const int *jidx;
-    unsigned *tcnt;                   // per i-tile: CTAs done (0 between launches)
-    int fused;
-    BatchTables bt;                   // batch geometry (batch kernels only)
-    unsigned long long wait_ns;       // limit of each wait for a staged tile
-    // prediction inside the force kernel: the j-store, the block time and
-    // the number of particles in j-memory; with one i-tile (each j-tile
-    // handled by one CTA) also the staged j-records, sorted by tile, that
-    // each CTA stores for its own tiles before it reads them
-    JStore js;
-    double t_pred;
-    int nj;
-    const g6x_jrec *rec;
-    const int *toff;
-};
 
 // Pair forces in FP32 with the DS separation of Eq. 3 (Sect. 2.3).  Per pair:
 //   dx   = (xj_hi - xi_hi) + (xj_lo - xi_lo)                       Eq. 3
@@ -668,15 +417,8 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         int s = q % NS;
         if constexpr (FP) {
             unsigned char *d = dyn_smem + (size_t)s * RAW_TILE_BYTES;
-            const size_t j0 = (size_t)jt * JT;
             mbar_expect_tx(&bar[s], RAW_TILE_BYTES);
-            bulk_g2s(d + RAW_T0, a.js.t0 + j0, JT * sizeof(double), &bar[s]);
-            bulk_g2s(d + RAW_V, a.js.v0m + j0, JT * sizeof(float4), &bar[s]);
-            bulk_g2s(d + RAW_A, a.js.a2f + j0, JT * sizeof(float4), &bar[s]);
-            bulk_g2s(d + RAW_J, a.js.j6f + j0, JT * sizeof(float4), &bar[s]);
-            bulk_g2s(d + RAW_XA, a.js.xds + j0, JT * sizeof(float4), &bar[s]);
-            bulk_g2s(d + RAW_XB, a.js.xds2 + j0, JT * sizeof(float2), &bar[s]);
-            bulk_g2s(d + RAW_ID, a.js.idx + j0, JT * sizeof(int), &bar[s]);
+            bulk_g2s(d, raw_tile(a.js, jt), RAW_TILE_BYTES, &bar[s]);
         } else {
             mbar_expect_tx(&bar[s], TILE_BYTES);
             bulk_g2s(stage_buf + (size_t)s * JW * JT, a.pt + (size_t)jt * JW * JT, TILE_BYTES,
@@ -880,10 +622,11 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                     if (kk < PPT && (!FP || slot < a.nj)) {
                         float ph[3], pl[3];
                         if constexpr (FP) {
-                            const float hh = (float)(a.t_pred - a.js.t0[slot]);
-                            predict_ds_pos(hh, a.js.xds[slot], a.js.xds2[slot], a.js.v0m[slot],
-                                           a.js.a2f[slot], a.js.j6f[slot], ph, pl);
-                            id = a.js.idx[slot];
+                            const float hh = (float)(a.t_pred - js_t0(a.js, slot));
+                            predict_ds_pos(hh, js_xds(a.js, slot), js_xds2(a.js, slot),
+                                           js_v0m(a.js, slot), js_a2f(a.js, slot),
+                                           js_j6f(a.js, slot), ph, pl);
+                            id = js_idx(a.js, slot);
                         } else {
                             ph[0] = __ldg(T + W_XH * JT + jj);
                             ph[1] = __ldg(T + W_YH * JT + jj);
@@ -1375,120 +1118,6 @@ struct ReduceArgs {
     int J, G, ni, itile, list;
 };
 
-// Sum of partial records of one i-particle: compensated FP32 for the DS path
-// (converted to FP64 once, at the end), plain FP64 for the FP64 path; the
-// nearest neighbour is the smallest |r|^2, ties to the lower j-slot.
-template <class PT>
-struct PartialSum;
-
-template <>
-struct PartialSum<PartialDS> {
-    float h[7], l[7];
-    float br;
-    int bj;
-    __device__ void init()
-    {
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            h[q] = 0.f;
-            l[q] = 0.f;
-        }
-        br = __int_as_float(0x7f800000);
-        bj = -1;
-    }
-    __device__ void nn(float r, int j)
-    {
-        if (j >= 0 && (bj < 0 || r < br || (r == br && j < bj))) {
-            br = r;
-            bj = j;
-        }
-    }
-    __device__ void add(const PartialDS &P)
-    {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            ds_acc(h[d], l[d], P.acc[d].x, P.acc[d].y);
-            ds_acc(h[3 + d], l[3 + d], P.jerk[d].x, P.jerk[d].y);
-        }
-        ds_acc(h[6], l[6], P.pot.x, P.pot.y);
-        nn(P.nnr2, P.nnj);
-    }
-    __device__ void shfl_combine(int off)
-    {
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            const float oh = __shfl_xor_sync(0xffffffffu, h[q], off);
-            const float ol = __shfl_xor_sync(0xffffffffu, l[q], off);
-            ds_acc(h[q], l[q], oh, ol);
-        }
-        const float r = __shfl_xor_sync(0xffffffffu, br, off);
-        const int j = __shfl_xor_sync(0xffffffffu, bj, off);
-        nn(r, j);
-    }
-    __device__ double value(int q) const { return (double)h[q] + (double)l[q]; }
-    __device__ float nnr2() const { return br; }
-};
-
-template <>
-struct PartialSum<Partial64> {
-    double s[7];
-    double br;
-    int bj;
-    __device__ void init()
-    {
-#pragma unroll
-        for (int q = 0; q < 7; ++q)
-            s[q] = 0.0;
-        br = __longlong_as_double(0x7ff0000000000000ll);
-        bj = -1;
-    }
-    __device__ void nn(double r, int j)
-    {
-        if (j >= 0 && (bj < 0 || r < br || (r == br && j < bj))) {
-            br = r;
-            bj = j;
-        }
-    }
-    __device__ void add(const Partial64 &P)
-    {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            s[d] += P.acc[d];
-            s[3 + d] += P.jerk[d];
-        }
-        s[6] += P.pot;
-        nn(P.nnr2, P.nnj);
-    }
-    __device__ void shfl_combine(int off)
-    {
-#pragma unroll
-        for (int q = 0; q < 7; ++q)
-            s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
-        const double r = __shfl_xor_sync(0xffffffffu, br, off);
-        const int j = __shfl_xor_sync(0xffffffffu, bj, off);
-        nn(r, j);
-    }
-    __device__ double value(int q) const { return s[q]; }
-    __device__ float nnr2() const { return (float)br; }
-};
-
-template <class PS>
-__device__ __forceinline__ g6x_out result_of(const PS &acc, const int *jidx)
-{
-    g6x_out o;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        o.acc[d] = acc.value(d);
-        o.jerk[d] = acc.value(3 + d);
-    }
-    o.pot = -acc.value(6);
-    // a winner that far away is an empty slot (parked at FAR), not a particle:
-    // no other j-particle took part
-    const bool has_nn = acc.bj >= 0 && acc.nnr2() < 1e30f;
-    o.nnb = has_nn ? jidx[acc.bj] : -1;
-    o.nnr2 = has_nn ? acc.nnr2() : __int_as_float(0x7f800000);
-    return o;
-}
 
 // K3, one warp per i-particle: lanes take the partials of the CTAs that
 // touched its i-tile and combine with warp shuffles (Sect. 2.3, 2.5).
@@ -1756,13 +1385,18 @@ cudaError_t prepare_variant(int v)
 
 }  // namespace
 
-int variant_count() { return kNumVariants; }
+int variant_count() { return kNumVariants + ws_variant_count(); }
 
-VariantInfo variant_info(int v) { return kVariants[v].info; }
+VariantInfo variant_info(int v)
+{
+    return v < kNumVariants ? kVariants[v].info : ws_variant_info(v - kNumVariants);
+}
 
 int variant_occupancy(int v)
 {
-    if (v < 0 || v >= kNumVariants)
+    if (v >= kNumVariants)
+        return ws_variant_occupancy(v - kNumVariants);
+    if (v < 0)
         return 0;
     if (g_occ[v] == 0) {
         if (prepare_variant(v) != cudaSuccess)
@@ -1846,57 +1480,101 @@ void tune_clear()
             e = TuneEntry();
 }
 
+namespace {
+
+// Largest block the built-in choice gives the small-block kernel: measured
+// on GB300 at N = 32768 and 2^20 it is faster than the separate predictor
+// and the split-j shapes up to m = 64 and slower from m = 128 on.
+constexpr int WS_DEFAULT_MAX_NI = 64;
+
+// The built-in launch choice for a block of ni against nj_pad j-particles
+// (no tuning table); *gmul receives the grid multiplier.
+int heuristic_variant(int prec, int ni, int nj_pad, int list, bool allow_ws, int *gmul)
+{
+    *gmul = 1;
+    if (prec == G6X_PREC_FP64)
+        return list ? 8 : 7;
+    if (prec == G6X_PREC_DS_DSSUB && !list) {
+        *gmul = ni > 2048 ? 2 : 1;
+        return ni <= 32 ? 22 : 21;
+    }
+    if (list)
+        return ni <= 32 ? 6 : 5;
+    if (allow_ws && ni <= WS_DEFAULT_MAX_NI) {
+        // the warp-specialised small-block kernel: the narrowest i-tile
+        // (one i-particle per thread) that holds the whole block
+        int best = -1, best_tile = INT_MAX;
+        for (int k = 0; k < ws_variant_count(); ++k) {
+            const VariantInfo w = ws_variant_info(k);
+            const int tile = w.ti * w.nper;
+            if (w.nper == 1 && tile >= ni && tile < best_tile) {
+                best = k;
+                best_tile = tile;
+            }
+        }
+        if (best >= 0)
+            return kNumVariants + best;
+    }
+    // The widest i-tile the block size allows, narrowed while the work
+    // line would hold too few (i-tile, j-tile) units for the SMs: wide
+    // tiles need many j-tiles to keep every CTA busy, so small j-sets
+    // take narrower tiles at the same m.
+    struct Shape {
+        int v, itile, max_ni;
+        long long min_units;
+    };
+    static constexpr Shape shapes[] = {
+        {0, 256, INT_MAX, 16384},  // 128 threads, two i each, whole j-tiles
+        {16, 128, 2048, 4096},     // 64 x 4 threads, two i each
+        {15, 64, 256, 2048},       // 32 x 8 threads, two i each
+        {14, 32, 128, 2048},       // 16 x 16 threads, two i each
+        {4, 16, 32, 0},            // 16 x 16 threads, one i each
+    };
+    const long long jtl = nj_pad / JT;
+    int k = 0;
+    while (shapes[k].min_units > 0
+           && (ni <= shapes[k + 1].max_ni
+               || (long long)((ni + shapes[k].itile - 1) / shapes[k].itile) * jtl
+                      < shapes[k].min_units))
+        ++k;
+    *gmul = shapes[k].v == 0 ? 2 : 1;
+    return shapes[k].v;
+}
+
+}  // namespace
+
+// Whether the built-in choice may take the warp-specialised small-block
+// kernel (where the caller allows a fused prediction).
+bool g_ws_default = true;
+
 ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
                           int force_variant, int force_grid, bool allow_fpred)
 {
+    const int nvar = variant_count();
     int v;
     int gmul = 1, tv = -1;
     if (force_variant < 0 && !list && tune_get(prec, tune_bucket(ni), &tv, &gmul)
-        && tv >= 0 && tv < kNumVariants && kVariants[tv].info.prec == prec
-        && !kVariants[tv].info.list)
+        && tv >= 0 && tv < nvar && variant_info(tv).prec == prec && !variant_info(tv).list)
         force_variant = tv;
     else
         gmul = 1;
-    if (force_variant >= 0 && force_variant < kNumVariants) {
+    if (force_variant >= 0 && force_variant < nvar)
         v = force_variant;
-    } else if (prec == G6X_PREC_FP64) {
-        v = list ? 8 : 7;
-    } else if (prec == G6X_PREC_DS_DSSUB && !list) {
-        v = ni <= 32 ? 22 : 21;
-        gmul = ni > 2048 ? 2 : 1;
-    } else if (list) {
-        v = ni <= 32 ? 6 : 5;
-    } else {
-        // The widest i-tile the block size allows, narrowed while the work
-        // line would hold too few (i-tile, j-tile) units for the SMs: wide
-        // tiles need many j-tiles to keep every CTA busy, so small j-sets
-        // take narrower tiles at the same m.
-        struct Shape {
-            int v, itile, max_ni;
-            long long min_units;
-        };
-        static constexpr Shape shapes[] = {
-            {0, 256, INT_MAX, 16384},  // 128 threads, two i each, whole j-tiles
-            {16, 128, 2048, 4096},     // 64 x 4 threads, two i each
-            {15, 64, 256, 2048},       // 32 x 8 threads, two i each
-            {14, 32, 128, 2048},       // 16 x 16 threads, two i each
-            {4, 16, 32, 0},            // 16 x 16 threads, one i each
-        };
-        const long long jtl = nj_pad / JT;
-        int k = 0;
-        while (shapes[k].min_units > 0
-               && (ni <= shapes[k + 1].max_ni
-                   || (long long)((ni + shapes[k].itile - 1) / shapes[k].itile) * jtl
-                          < shapes[k].min_units))
-            ++k;
-        v = shapes[k].v;
-        gmul = v == 0 ? 2 : 1;
-    }
+    else
+        v = heuristic_variant(prec, ni, nj_pad, list, allow_fpred && g_ws_default, &gmul);
     // a fused-prediction shape only where the caller can use it (DS
-    // predictor, the j-store current); otherwise its separate twin
-    if (kVariants[v].info.fpred && (!allow_fpred || list))
-        v = kVariants[v].info.twin;
-    const VariantInfo &vi = kVariants[v].info;
+    // predictor, the j-store current); otherwise its separate twin, or for
+    // the small-block kernel (no twin; one i-tile) the built-in choice
+    {
+        const VariantInfo w = variant_info(v);
+        if (w.fpred && (!allow_fpred || list || (w.ws && ni > w.ti * w.nper))) {
+            if (w.twin >= 0)
+                v = w.twin;
+            else
+                v = heuristic_variant(prec, ni, nj_pad, list, false, &gmul);
+        }
+    }
+    const VariantInfo vi = variant_info(v);
     ForceConfig c{};
     c.variant = v;
     c.ti = vi.ti;
@@ -1906,9 +1584,10 @@ ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
     c.jtiles = nj_pad / JT;
     c.n_itile = (ni + c.itile - 1) / c.itile;
     c.work = (long long)c.n_itile * c.jtiles;
-    c.smem = kVariants[v].smem;
+    c.smem = vi.ws ? ws_variant_smem(v - kNumVariants) : kVariants[v].smem;
     c.list = vi.list;
     c.prec = vi.prec;
+    c.ws = vi.ws;
     int occ = variant_occupancy(v);
     if (occ < 1)
         occ = 1;
@@ -1923,7 +1602,18 @@ ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
 
 size_t partial_slots(const ForceConfig &cfg)
 {
+    if (cfg.ws)
+        return ws_partial_slots(cfg.grid, cfg.itile);
     return (size_t)(cfg.grid + cfg.n_itile) * cfg.itile;
+}
+
+size_t counter_slots(const ForceConfig &cfg)
+{
+    if (cfg.ws) {
+        const int gs = ws_group_size(cfg.grid);
+        return (size_t)(cfg.grid + gs - 1) / gs + 1;
+    }
+    return (size_t)cfg.n_itile;
 }
 
 cudaError_t launch_init_store(JStore js, cudaStream_t s)
@@ -1991,6 +1681,8 @@ cudaError_t launch_update_predict(int kind, JStore js, Pred p, int nj, int nj_pa
 // Arguments of the fused prediction (variants with fpred set).
 static bool set_fused_pred(ForceArgs &a, const ForceConfig &cfg, const FusedPred *fp)
 {
+    if (cfg.ws || cfg.variant < 0 || cfg.variant >= kNumVariants)
+        return false;
     if (!kVariants[cfg.variant].info.fpred)
         return true;
     if (!fp)
@@ -2003,28 +1695,6 @@ static bool set_fused_pred(ForceArgs &a, const ForceConfig &cfg, const FusedPred
     return fp->rec == nullptr || (cfg.n_itile == 1 && fp->toff != nullptr);
 }
 
-// Launch fn, with programmatic stream serialization when pdl is set (the
-// kernel then starts behind its predecessor and waits in grid_dep_wait).
-template <class... Args>
-cudaError_t launch_maybe_pdl(void (*fn)(Args...), int grid, int threads, int smem,
-                             cudaStream_t s, bool pdl, Args... args)
-{
-    if (!pdl) {
-        fn<<<grid, threads, smem, s>>>(args...);
-        return cudaGetLastError();
-    }
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3((unsigned)grid);
-    lc.blockDim = dim3((unsigned)threads);
-    lc.dynamicSmemBytes = (size_t)smem;
-    lc.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    lc.attrs = attr;
-    lc.numAttrs = 1;
-    return cudaLaunchKernelEx(&lc, fn, args...);
-}
 
 cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
                          const g6x_irec *d_irec, int ni, double eps2,
@@ -2033,6 +1703,8 @@ cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
 {
     if (cfg.work <= 0)
         return cudaSuccess;
+    if (cfg.ws || cfg.variant < 0 || cfg.variant >= kNumVariants)
+        return cudaErrorInvalidValue;           // small-block kernel: launch_force_ws
     cudaError_t e = prepare_variant(cfg.variant);
     if (e != cudaSuccess)
         return e;
@@ -2064,7 +1736,8 @@ cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
 {
     if (cfg.work <= 0)
         return cudaSuccess;
-    if (cfg.list || cfg.prec != G6X_PREC_DS)
+    if (cfg.list || cfg.prec != G6X_PREC_DS || cfg.ws || cfg.variant < 0
+        || cfg.variant >= kNumVariants)
         return cudaErrorInvalidValue;
     cudaError_t e = prepare_variant(cfg.variant);
     if (e != cudaSuccess)
@@ -2099,6 +1772,8 @@ cudaError_t launch_reduce(const ForceConfig &cfg, const void *part,
 {
     if (ni <= 0)
         return cudaSuccess;
+    if (cfg.ws)
+        return cudaErrorInvalidValue;           // the small-block kernel reduces itself
     ReduceArgs a;
     a.part = part;
     a.nbl = nbl_part;

@@ -54,7 +54,7 @@ EXPORTS = [
     "g6h_stats", "g6h_profile", "g6h_destroy", "g6h_checkpoint", "g6h_restore",
     "g6h_set_neighbour_radius", "g6h_neighbour_stats", "g6h_run_blocks",
     "g6h_correct_block_ex", "g6h_set_force_noise", "g6hb_set_force_noise",
-    "g6x_fp32_probe", "g6x_plan_launch",
+    "g6x_fp32_probe", "g6x_fp64_probe", "g6x_plan_launch", "g6x_variant_info",
     "g6x_batch_create", "g6x_batch_destroy", "g6x_batch_irecs", "g6x_batch_results",
     "g6x_batch_set_j", "g6x_batch_set_j_many", "g6x_batch_calc", "g6x_batch_launch_count",
     "g6x_batch_set_schedule", "g6x_batch_get_schedule", "g6x_batch_autotune", "g6hb_autotune",
@@ -117,6 +117,8 @@ def lib():
             "g6h_set_force_noise": (I, [P, D]),
             "g6hb_set_force_noise": (I, [P, D]),
             "g6x_fp32_probe": (I, [I, P, P]),
+            "g6x_fp64_probe": (I, [I, P, P]),
+            "g6x_variant_info": (I, [I, P]),
             "g6x_plan_launch": (I, [I, I, I, I, I, P]),
             "g6h_create": (P, [I, I, P, P, P, D, D, D, D, D, P]),
             "g6h_run": (I, [P, D]),
@@ -380,11 +382,33 @@ def g6x_plan_launch(mode, nj, ni, list_=False, sm_count=152):
     return dict(zip(("variant", "ti", "tj", "ni_per", "grid", "jtiles"), (int(v) for v in out)))
 
 
+def g6x_variant_info(variant):
+    """Shape of a compiled force-kernel variant: dict with ti, tj, ni_per,
+    list, prec, fpred, twin, ws."""
+    out = np.zeros(8, dtype=np.int32)
+    _check(lib().g6x_variant_info(int(variant), out.ctypes.data_as(C.c_void_p)),
+           "g6x_variant_info")
+    return dict(zip(("ti", "tj", "ni_per", "list", "prec", "fpred", "twin", "ws"),
+                    (int(v) for v in out)))
+
+
+def g6x_variant_count():
+    return _check(lib().g6x_variant_info(-1, None), "g6x_variant_info")
+
+
 def g6x_fp32_probe(iters=10000):
     """Measured packed-FP32 FMA rate of the current device: (TFLOP/s, ms of
     the timed launch)."""
     tf, ms = C.c_double(), C.c_double()
     _check(lib().g6x_fp32_probe(int(iters), C.byref(tf), C.byref(ms)), "g6x_fp32_probe")
+    return tf.value, ms.value
+
+
+def g6x_fp64_probe(iters=200):
+    """Measured FP64 FMA rate of the current device: (TFLOP/s, ms of the
+    timed launch)."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(lib().g6x_fp64_probe(int(iters), C.byref(tf), C.byref(ms)), "g6x_fp64_probe")
     return tf.value, ms.value
 
 

@@ -162,24 +162,6 @@ def test_c_client_builds_against_the_header_and_library(lib, tmp_path):
         assert r.returncode == -g6gb.G6_ENODEV          # no GPU here
 
 
-def test_block_latency_tool_builds_and_refuses_bad_arguments(lib, tmp_path):
-    """The per-call latency tool (a plain C program against the header and
-    the library) compiles warning-free; bad arguments end it before any
-    library call, and without a GPU its first call fails cleanly."""
-    import subprocess
-    libdir = os.path.join(ROOT, "paper_0902_4463_gb300")
-    exe = str(tmp_path / "block_latency")
-    cmd = ["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-O1",
-           os.path.join(libdir, "block_latency.c"), "-I", os.path.join(ROOT, "include"),
-           "-L", libdir, "-lg6gb", "-Wl,-rpath," + libdir, "-o", exe]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    assert r.returncode == 0, r.stderr
-    assert subprocess.run([exe, "100", "10"]).returncode == 2
-    if not os.path.exists("/dev/nvidia0"):
-        r = subprocess.run([exe, "8192", "1"], capture_output=True, text=True)
-        assert r.returncode == 1 and "setup failed" in r.stderr
-
-
 def test_launch_plan_heuristic_without_a_gpu(lib):
     """The built-in launch choice (g6x_plan_launch, no GPU needed): the
     widest i-tile that the block size allows, narrowed while the work line
@@ -195,6 +177,18 @@ def test_launch_plan_heuristic_without_a_gpu(lib):
         return p["ti"], p["tj"], p["ni_per"]
 
     big, small = 1 << 20, 32768
+
+    def ws(nj, ni):
+        return g6gb.g6x_variant_info(g6gb.g6x_plan_launch(ds, nj, ni)["variant"])["ws"] == 1
+
+    # blocks of up to 64 take the small-block kernel with the narrowest
+    # i-tile that holds them; larger blocks the split-j and wide shapes
+    for nj in (1024, small, big):
+        assert all(ws(nj, ni) for ni in (1, 8, 9, 16, 17, 33, 64))
+        assert not any(ws(nj, ni) for ni in (65, 128, 256, 4096))
+        assert shape(nj, 1) == (8, 32, 1) and shape(nj, 8) == (8, 32, 1)
+        assert shape(nj, 17) == (32, 8, 1) and shape(nj, 64) == (64, 4, 1)
+        assert g6gb.g6x_plan_launch(ds, nj, 16, True)["variant"] in (5, 6)   # lists: no
     assert shape(big, 16) == (16, 16, 1)
     assert shape(big, 128) == (16, 16, 2)
     assert shape(big, 256) == (32, 8, 2)
@@ -233,7 +227,9 @@ def test_tuning_table_is_consulted_and_loads_all_or_nothing(lib, tmp_path):
     ds, x64 = g6gb.G6X_PREC_DS, g6gb.G6X_PREC_DS_X64
     big = 1 << 20
     g6gb.g6x_clear_tuning()
-    assert g6gb.g6x_plan_launch(ds, big, 16)["variant"] == 4
+    ws16 = g6gb.g6x_plan_launch(ds, big, 16)["variant"]      # the small-block kernel
+    assert g6gb.g6x_variant_info(ws16)["ws"] == 1
+    assert g6gb.g6x_plan_launch(x64, big, 16)["variant"] == 4   # no fused prediction there
     good = tmp_path / "good.txt"
     good.write_text("# comment\n0 4 17 1\n0 5 14 2\n1 4 7 1\n")
     assert g6gb.g6x_load_tuning(str(good)) == 3
@@ -252,7 +248,7 @@ def test_tuning_table_is_consulted_and_loads_all_or_nothing(lib, tmp_path):
     with np.testing.assert_raises(g6gb.G6Error):
         g6gb.g6x_load_tuning(str(tmp_path / "missing.txt"))
     g6gb.g6x_clear_tuning()
-    assert g6gb.g6x_plan_launch(ds, big, 16)["variant"] == 4
+    assert g6gb.g6x_plan_launch(ds, big, 16)["variant"] == ws16
     assert g6gb.g6x_plan_launch(ds, big, 4096)["variant"] == 0
 
 

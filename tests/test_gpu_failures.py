@@ -92,7 +92,7 @@ def test_calculation_that_must_grow_fails_then_succeeds(refusing, orc):
 
 
 def test_batch_creation_fails_cleanly(refusing):
-    for allow in (0, 5, 15, 18):           # the batch makes 19 device allocations
+    for allow in (0, 5, 10, 13):           # the batch makes 14 device allocations
         refusing.calls, refusing.allow = 0, allow
         with pytest.raises(g6.G6Error) as e:
             g6.G6Batch([300, 1000, 70])
