@@ -507,9 +507,11 @@ def main():
     fmax = float(peaks.get("sm_max_mhz") or 2070.0)
     peak = sms * FP32_LANES_PER_SM * 2 * fmax * 1e6 / 1e12
     out_main = d_out.cpu().numpy().view(g6.OUT)
-    # measured packed-FP32 FMA rate (outside the timed region), beside the
-    # derived peak the fraction is taken against
+    # measured packed-FP32 and FP64 FMA rates (outside the timed region),
+    # beside the derived peak the fraction is taken against and as the
+    # denominator of the all-FP64 kernel's fraction
     probe_tf, probe_ms = g6.g6x_fp32_probe(10000)
+    probe64_tf, probe64_ms = g6.g6x_fp64_probe(400)
 
     # all-FP64 kernel on a subset of the block (its rate is flat in m)
     m64 = min(args.fp64_m, m)
@@ -667,8 +669,16 @@ def main():
                                                "8 CTAs x 256 threads per SM"}},
             "fp64": {"m": m64, "force_interactions_per_s": rate64,
                      "gflops_60": rate64 * FLOPS_PER_PAIR / 1e9,
+                     "peak_tflops": probe64_tf,
+                     "peak_basis": "g6x_fp64_probe: FP64 FMA chains, 8 CTAs x 256 threads per SM "
+                                   "(measured)",
+                     "frac": rate64 * FLOPS_PER_PAIR / 1e12 / probe64_tf,
                      "ds_force_interactions_per_s_same_m": rateds,
-                     "speedup_ds_over_fp64": rateds / rate64},
+                     "speedup_ds_over_fp64": rateds / rate64,
+                     "speedup_ds_over_fp64_at_m_n": (pairs / (force_ms * 1e-3)) / rate64,
+                     "speedup_basis_at_m_n": "DS force rate of the timed m = N step over the "
+                                             "FP64 rate at m = %d (the FP64 kernel is bound by "
+                                             "its pipe, its rate flat in m)" % m64},
             "ablation_full_ds_subtraction": {"m": m64, "force_interactions_per_s": ratess,
                                              "eq3_force_interactions_per_s": rateds,
                                              "eq3_speedup": rateds / ratess},

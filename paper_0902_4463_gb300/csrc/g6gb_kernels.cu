@@ -97,29 +97,29 @@ __global__ void k_irec_from_store(JStore js, g6x_irec *out, int m)
 
 
 // Records one tile's range of particle indices (empty slots excluded);
-// called by all JT threads of the CTA with their own slot's index.
-__device__ __forceinline__ void tile_index_range(int *s_lo, int *s_hi, int id, bool valid,
-                                                 int2 *out)
+// called by all JT threads of the CTA with their own slot's index.  The
+// per-warp ranges go to the half `par` of the double-buffered s_lo / s_hi,
+// so consecutive tiles need only the one barrier here: the next tile writes
+// the other half, and the tile after that passes this tile's barrier after
+// thread 0 has read its half.
+__device__ __forceinline__ void tile_index_range(int (*s_lo)[JT / 32], int (*s_hi)[JT / 32],
+                                                 int par, int id, bool valid, int2 *out)
 {
     int lo_id = valid ? id : INT_MAX, hi_id = valid ? id : -1;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        lo_id = min(lo_id, __shfl_xor_sync(0xffffffffu, lo_id, off));
-        hi_id = max(hi_id, __shfl_xor_sync(0xffffffffu, hi_id, off));
-    }
+    lo_id = __reduce_min_sync(0xffffffffu, lo_id);
+    hi_id = __reduce_max_sync(0xffffffffu, hi_id);
     if ((threadIdx.x & 31) == 0) {
-        s_lo[threadIdx.x >> 5] = lo_id;
-        s_hi[threadIdx.x >> 5] = hi_id;
+        s_lo[par][threadIdx.x >> 5] = lo_id;
+        s_hi[par][threadIdx.x >> 5] = hi_id;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < JT / 32; ++w) {
-            lo_id = min(lo_id, s_lo[w]);
-            hi_id = max(hi_id, s_hi[w]);
+            lo_id = min(lo_id, s_lo[par][w]);
+            hi_id = max(hi_id, s_hi[par][w]);
         }
         *out = make_int2(lo_id, hi_id);
     }
-    __syncthreads();
 }
 
 // Eq. 1 and Eq. 2 for one j-slot k < nj in the paper's DS + SP form
@@ -191,9 +191,10 @@ __global__ void __launch_bounds__(JT) k_predict(JStore js, Pred p, int nj, int n
                                                 const int *__restrict__ toff, int ntiles_all)
 {
     grid_dep_launch();              // the force kernel may be scheduled behind this one
-    __shared__ int s_lo[JT / 32], s_hi[JT / 32];
+    __shared__ int s_lo[2][JT / 32], s_hi[2][JT / 32];
     const int ntiles_pred = nj_pad / JT;
     const int ntiles = UPD ? ntiles_all : ntiles_pred;
+    int par = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         if constexpr (UPD) {
             for (int r = toff[tile] + threadIdx.x; r < toff[tile + 1]; r += JT)
@@ -208,7 +209,8 @@ __global__ void __launch_bounds__(JT) k_predict(JStore js, Pred p, int nj, int n
         } else {
             float *o = p.pt + (size_t)tile * (JW * JT) + threadIdx.x;
             const int id = k < nj ? js_idx(js, k) : -1;
-            tile_index_range(s_lo, s_hi, id, k < nj && id >= 0, &p.trange[tile]);
+            tile_index_range(s_lo, s_hi, par, id, k < nj && id >= 0, &p.trange[tile]);
+            par ^= 1;
             if (k >= nj)
                 far_slot_ds(o);
             else if constexpr (KIND == PRED_DS)
@@ -226,7 +228,8 @@ __global__ void __launch_bounds__(JT) k_predict_batch(JStore js, Pred p, BatchPr
                                                       const int *__restrict__ toff, int tile0,
                                                       int ntiles)
 {
-    __shared__ int s_lo[JT / 32], s_hi[JT / 32];
+    __shared__ int s_lo[2][JT / 32], s_hi[2][JT / 32];
+    int par = 0;
     for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
         const int tile = tile0 + tt;
         if (rec && toff) {
@@ -246,7 +249,8 @@ __global__ void __launch_bounds__(JT) k_predict_batch(JStore js, Pred p, BatchPr
         } else {
             float *o = p.pt + (size_t)tile * (JW * JT) + threadIdx.x;
             const int id = valid ? js_idx(js, slot) : -1;
-            tile_index_range(s_lo, s_hi, id, valid && id >= 0, &p.trange[tile]);
+            tile_index_range(s_lo, s_hi, par, id, valid && id >= 0, &p.trange[tile]);
+            par ^= 1;
             if (!valid)
                 far_slot_ds(o);
             else if constexpr (KIND == PRED_DS)

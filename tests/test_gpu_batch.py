@@ -54,7 +54,7 @@ def _check_cluster(orc, st, t_blk, eps2, sel, res):
     ea, ej = rel_err_vec(res["acc"], oa), rel_err_vec(res["jerk"], oj)
     ep = np.abs(res["pot"] - op) / np.abs(op)
     assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5, (np.median(ea), ea.max())
-    assert np.median(ej) <= 1e-6 and ej.max() <= 1e-4, (np.median(ej), ej.max())
+    assert np.median(ej) <= 1e-6 and ej.max() <= 1e-5, (np.median(ej), ej.max())
     assert np.median(ep) <= 1e-6 and ep.max() <= 1e-5
     assert check_nn(onn, onr, res["nnb"], xp[sel], xp, st["idx"]) > 0.98
 

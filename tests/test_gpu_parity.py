@@ -45,7 +45,7 @@ def test_full_sweep_plummer_1024(ctx, orc, prec):
     ea, ej = rel_err_vec(acc, oa), rel_err_vec(jerk, oj)
     ep = np.abs(pot - op) / np.abs(op)
     assert np.median(ea) <= med and ea.max() <= mx
-    assert np.median(ej) <= med and ej.max() <= 10 * mx
+    assert np.median(ej) <= med and ej.max() <= mx, (np.median(ej), ej.max())
     assert np.median(ep) <= med and ep.max() <= mx
     assert check_nn(onn, onr, nnb, x, x, idx) > 0.99
 
@@ -96,7 +96,7 @@ def test_subset_of_predicted_particles_ragged(ctx, orc, prec):
     ea, ej = rel_err_vec(acc, oa), rel_err_vec(jerk, oj)
     ep = np.abs(pot - op) / np.abs(op)
     assert np.median(ea) <= med and ea.max() <= mx
-    assert np.median(ej) <= 3 * med and ej.max() <= 30 * mx
+    assert np.median(ej) <= med and ej.max() <= mx, (np.median(ej), ej.max())
     assert np.median(ep) <= med and ep.max() <= mx
     check_nn(onn, onr, nnb, xi, xp, idx)
 
