@@ -143,19 +143,40 @@ int g6calc_lasthalf2(int clusterid, int nj, int ni, const int index[],
 
 /* Copy the neighbour lists of the last calculation to the host (Sect. 4):
  * for each i the j-particles with unsoftened |r|^2 < h2[i], excluding
- * itself, in ascending j-slot order, at most G6_MAXNB of them.  Returns 0,
- * G6_EOVERFLOW (1) if some list was longer than G6_MAXNB (it is truncated),
- * or a negative error.  Lists exist only if firsthalf got h2 != NULL. */
+ * itself, in ascending j-slot order, at most the context's list length of
+ * them (G6_MAXNB unless g6x_set_max_neighbours chose another).  Synchronous.
+ * The force kernel keeps each CTA's part of a list in a slot with room for a
+ * few entries, grown as lists grow: when a part had more entries than its
+ * slot held, this call computes that calculation's lists once more with
+ * larger slots (the j-memory must not have changed since: G6_EBUSY), so the
+ * lists returned are always complete.  Returns 0, G6_EOVERFLOW (1) if some
+ * list was longer than the list length (it is truncated), or a negative
+ * error.  Lists exist only if firsthalf got h2 != NULL (or g6x_calc_dev
+ * nl != 0, whose d_irec must then stay unchanged until this call). */
 int g6_read_neighbour_list(int clusterid);
 
 /* Neighbour list of i-particle number ipipe (0 <= ipipe < ni) of the last
  * calculation: *nblen = list length, nbl[0 .. min(*nblen, maxlength)-1] =
  * particle indices.  Returns 0, G6_EOVERFLOW if *nblen > maxlength or the
- * list overflowed G6_MAXNB, or a negative error. */
+ * list overflowed the list length, or a negative error. */
 int g6_get_neighbour_list(int clusterid, int ipipe, int maxlength, int *nblen,
                           int nbl[]);
 
 /* ------------------------------------------------------------ extensions */
+
+/* Neighbour-list length of the context, 1 .. G6X_MAXNB_LIMIT entries per
+ * i-particle (default G6_MAXNB = 256, the paper's choice, Sect. 4; the paper
+ * fixes it at compile time, here it is a setting).  Longer lists cost more
+ * host memory and read-back; the force kernel's cost depends on the number
+ * of entries found, not on this length.  Applies to later calculations;
+ * lists already computed are dropped.  Returns 0 or G6_EINVAL. */
+#define G6X_MAXNB_LIMIT 4096
+int g6x_set_max_neighbours(int clusterid, int maxnb);
+/* The context's list length, or a negative error. */
+int g6x_max_neighbours(int clusterid);
+/* How often g6_read_neighbour_list computed lists again because a list
+ * part outgrew its slot (see there), or a negative error. */
+long long g6x_list_reruns(int clusterid);
 
 #define G6X_PREC_DS     0 /* FP32 force with DS separations (Eq. 3) and the
                              DS + SP predictor of Sect. 2.2 (default)       */
@@ -481,9 +502,9 @@ int g6h_profile(const g6h_sim *s, double *sec_sched, double *sec_force,
  * sweep never builds lists.  Returns 0, G6_EINVAL or G6_ENOMEM. */
 int g6h_set_neighbour_radius(g6h_sim *s, double h2);
 
-/* Lists read back so far, their total length (entries kept, at most
- * G6_MAXNB per list) and how many overflowed G6_MAXNB.  Any pointer may be
- * NULL. */
+/* Lists read back so far, their total length (entries kept, at most the
+ * context's list length per list) and how many overflowed it.  Any pointer
+ * may be NULL. */
 int g6h_neighbour_stats(const g6h_sim *s, long long *lists, long long *entries,
                         long long *overflowed);
 

@@ -138,8 +138,17 @@ struct Ctx {
     bool tcnt_dirty = false;          // a launch may have stopped mid-count
     int *d_nbl_part = nullptr, *d_nbc_part = nullptr;
     size_t nbp_cap = 0;
+    int nbp_seg = 0;                  // entries per list partial of d_nbl_part
     int *d_nbl = nullptr, *d_nblen = nullptr, *h_nbl = nullptr, *h_nblen = nullptr;
     size_t nbo_cap = 0;
+    int nbo_maxnb = 0;                // list length of d_nbl / h_nbl
+    // neighbour lists (Sect. 4): entries kept per i-particle, room per list
+    // partial (grown when a launch needed more), and the largest count a
+    // launch saw (mapped)
+    int maxnb = G6_MAXNB;
+    int nbseg = 16;
+    int *h_nbmax = nullptr, *d_nbmax = nullptr;
+    long long list_reruns = 0;
     int *d_err = nullptr, *h_err = nullptr;
     // prediction bookkeeping per precision mode
     double t_set = 0.0;
@@ -152,6 +161,14 @@ struct Ctx {
     int calc_ni = 0, calc_nj = 0;
     bool lists_ready = false, lists_host = false;
     int list_ni = 0;
+    // what the last list launch computed, to compute its lists again with
+    // more room per partial: its launch, inputs, block time and j-memory version
+    ForceConfig list_cfg{};
+    int list_nj = 0;
+    const g6x_irec *list_irec = nullptr;
+    g6x_out *list_out = nullptr;
+    double list_eps2 = 0.0, list_t = 0.0;
+    long long list_ver = -1;
     cudaEvent_t ev_done = nullptr;
     ForceConfig last_cfg{};
     long long launches = 0;
@@ -305,7 +322,7 @@ void free_ctx(Ctx &c)
     for (void *p : dptrs)
         dev_free(p);
     void *hptrs[] = {c.h_jst, c.h_jsort, c.h_toff, c.h_irec, c.h_out, c.h_nbl, c.h_nblen,
-                     c.h_err};
+                     c.h_err, c.h_nbmax};
     for (void *p : hptrs)
         host_free(p);
     for (int p = 0; p < 4; ++p)
@@ -597,12 +614,12 @@ int update_and_predict(Ctx &c, int nj, bool predict = true, int fold_jtiles = 0,
 // Output neighbour lists for ni i-particles (device and pinned host copies).
 int grow_nb_out(Ctx &c, int ni)
 {
-    if ((size_t)ni <= c.nbo_cap && c.d_nbl)
+    if ((size_t)ni <= c.nbo_cap && c.d_nbl && c.nbo_maxnb == c.maxnb)
         return 0;
     size_t n = (size_t)(ni > 16 ? ni : 16);
-    int *dl = (int *)dev_alloc(n * G6_MAXNB * sizeof(int));
+    int *dl = (int *)dev_alloc(n * c.maxnb * sizeof(int));
     int *dn = (int *)dev_alloc(n * sizeof(int));
-    int *hl = (int *)host_alloc(n * G6_MAXNB * sizeof(int));
+    int *hl = (int *)host_alloc(n * c.maxnb * sizeof(int));
     int *hn = (int *)host_alloc(n * sizeof(int));
     if (!dl || !dn || !hl || !hn) {
         dev_free(dl);
@@ -620,6 +637,7 @@ int grow_nb_out(Ctx &c, int ni)
     c.h_nbl = hl;
     c.h_nblen = hn;
     c.nbo_cap = n;
+    c.nbo_maxnb = c.maxnb;
     return 0;
 }
 
@@ -704,16 +722,22 @@ int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_
     int rc = grow_dev(c.d_part, c.part_cap, slots);
     if (rc)
         return rc;
+    g6::ListArgs la{c.maxnb, c.nbseg < c.maxnb ? c.nbseg : c.maxnb, c.d_nbmax};
     if (cfg.list) {
+        // each list partial (one CTA's segment of one i-particle) has room
+        // for la.nbseg entries, not for a whole list: the partials take
+        // slots x nbseg ints instead of slots x maxnb
         size_t cap_old = c.nbp_cap;
         rc = grow_dev(c.d_nbc_part, c.nbp_cap, slots);
         if (rc)
             return rc;
-        if (c.nbp_cap != cap_old || !c.d_nbl_part) {
+        if (c.nbp_cap != cap_old || !c.d_nbl_part || c.nbp_seg != la.nbseg) {
             dev_free(c.d_nbl_part);
-            c.d_nbl_part = (int *)dev_alloc(c.nbp_cap * G6_MAXNB * sizeof(int));
+            c.d_nbl_part = (int *)dev_alloc(c.nbp_cap * la.nbseg * sizeof(int));
+            c.nbp_seg = la.nbseg;
             if (!c.d_nbl_part) {
                 c.nbp_cap = 0;
+                c.nbp_seg = 0;
                 dev_free(c.d_nbc_part);
                 c.d_nbc_part = nullptr;
                 return G6_ENOMEM;
@@ -722,6 +746,8 @@ int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_
         rc = grow_nb_out(c, ni);
         if (rc)
             return rc;
+        if (cudaMemsetAsync(c.d_nbmax, 0, sizeof(int), c.stream) != cudaSuccess)
+            return cuda_err(cudaGetLastError());
     }
     cudaError_t e;
     // Programmatic dependent launch of the force kernel and the reduction
@@ -756,12 +782,12 @@ int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_
         {
             PhaseTimer pt(c, PH_FORCE);
             e = g6::launch_force(cfg, c.pred, d_irec, ni, eps2, c.d_part, c.d_nbl_part,
-                                 c.d_nbc_part, c.d_err, c.stream, fpp, pdl);
+                                 c.d_nbc_part, c.d_err, c.stream, fpp, pdl, &la);
         }
         if (e == cudaSuccess) {
             PhaseTimer pt(c, PH_REDUCE);
             e = g6::launch_reduce(cfg, c.d_part, c.d_nbl_part, c.d_nbc_part, c.js.idx, ni,
-                                  d_out, c.d_nbl, c.d_nblen, c.stream, pdl);
+                                  d_out, c.d_nbl, c.d_nblen, c.stream, pdl, &la);
         }
         c.launches += 2;
     }
@@ -771,6 +797,15 @@ int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_
     c.lists_ready = cfg.list != 0;
     c.lists_host = false;
     c.list_ni = ni;
+    if (cfg.list) {
+        c.list_cfg = cfg;
+        c.list_nj = nj;
+        c.list_irec = d_irec;
+        c.list_out = d_out;
+        c.list_eps2 = eps2;
+        c.list_t = c.t_set;
+        c.list_ver = c.ver;
+    }
     return 0;
 }
 
@@ -853,10 +888,13 @@ int g6x_open_ex(int cid, int nj_max, int ni_max)
         void *de = nullptr;
         c.h_err = (int *)host_alloc_mapped(sizeof(int), &de);
         c.d_err = (int *)de;
+        void *dm = nullptr;
+        c.h_nbmax = (int *)host_alloc_mapped(sizeof(int), &dm);
+        c.d_nbmax = (int *)dm;
     }
     if (!js.x0 || !js.raw || !js.v64 || !js.a264
         || !js.j664 || !js.idx || !c.pred.pt || !c.pred.trange || !c.pred.p64
-        || !c.pred.v64 || !c.d_err || !c.h_err)
+        || !c.pred.v64 || !c.d_err || !c.h_err || !c.h_nbmax)
         rc = G6_ENOMEM;
     if (!rc)
         rc = ensure_io(c, ni_max < 4096 ? ni_max : 4096);
@@ -1073,6 +1111,7 @@ void g6calc_firsthalf(int cid, int nj, int ni, const int index[],
             if (!rc) {
                 c->lists_ready = true;
                 c->list_ni = ni;
+                c->list_cfg = ForceConfig{};      // nothing to compute again
             }
         }
     }
@@ -1156,10 +1195,45 @@ int g6_read_neighbour_list(int cid)
     if (c->pending || !c->lists_ready)
         return G6_EINVAL;
     int n = c->list_ni;
-    cudaError_t e = cudaMemcpyAsync(c->h_nblen, c->d_nblen, sizeof(int) * n,
-                                    cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return cuda_err(e);
+    if (c->list_cfg.list && *(volatile int *)c->h_nbmax > c->nbp_seg) {
+        // a list partial found more entries than it had room for: compute
+        // the lists of that calculation again with enough room per partial
+        // (the same launch on the same inputs, so the forces it writes
+        // again are identical)
+        if (c->ver != c->list_ver || c->n_jst != 0)
+            return G6_EBUSY;              // j-memory has changed since
+        int need = *(volatile int *)c->h_nbmax;
+        int seg = c->nbseg;
+        while (seg < need)
+            seg *= 2;
+        c->nbseg = seg < c->maxnb ? seg : c->maxnb;
+        const double t_keep = c->t_set;
+        c->t_set = c->list_t;
+        int rc = predict_if_stale(*c, c->list_nj);
+        if (!rc)
+            rc = run_force(*c, c->list_cfg, c->list_nj, n, c->list_irec, c->list_eps2,
+                           c->list_out, false);
+        c->t_set = t_keep;
+        if (rc)
+            return rc;
+        c->list_reruns += 1;
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess)
+            return cuda_err(e);
+        if (*(volatile int *)c->h_err) {
+            int code = *c->h_err;
+            *(volatile int *)c->h_err = 0;
+            c->tcnt_dirty = true;
+            return code < 0 ? code : G6_EIO;
+        }
+    }
+    e = cudaMemcpyAsync(c->h_nblen, c->d_nblen, sizeof(int) * n, cudaMemcpyDeviceToHost,
+                        c->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->h_nbl, c->d_nbl, sizeof(int) * (size_t)n * G6_MAXNB,
+        e = cudaMemcpyAsync(c->h_nbl, c->d_nbl, sizeof(int) * (size_t)n * c->maxnb,
                             cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(c->stream);
@@ -1167,7 +1241,7 @@ int g6_read_neighbour_list(int cid)
         return cuda_err(e);
     c->lists_host = true;
     for (int k = 0; k < n; ++k)
-        if (c->h_nblen[k] > G6_MAXNB)
+        if (c->h_nblen[k] > c->maxnb)
             return G6_EOVERFLOW;
     return 0;
 }
@@ -1182,14 +1256,44 @@ int g6_get_neighbour_list(int cid, int ipipe, int maxlength, int *nblen, int nbl
         return G6_EINVAL;
     int len = c->h_nblen[ipipe];
     *nblen = len;
-    int keep = len < G6_MAXNB ? len : G6_MAXNB;
+    int keep = len < c->maxnb ? len : c->maxnb;
     if (keep > maxlength)
         keep = maxlength;
     if (keep > 0 && !nbl)
         return G6_EINVAL;
     for (int k = 0; k < keep; ++k)
-        nbl[k] = c->h_nbl[(size_t)ipipe * G6_MAXNB + k];
-    return (len > G6_MAXNB || len > maxlength) ? G6_EOVERFLOW : 0;
+        nbl[k] = c->h_nbl[(size_t)ipipe * c->maxnb + k];
+    return (len > c->maxnb || len > maxlength) ? G6_EOVERFLOW : 0;
+}
+
+int g6x_set_max_neighbours(int cid, int maxnb)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    if (!c)
+        return err;
+    if (c->pending || maxnb < 1 || maxnb > G6X_MAXNB_LIMIT)
+        return G6_EINVAL;
+    if (maxnb != c->maxnb) {
+        c->maxnb = maxnb;
+        c->lists_ready = false;
+        c->lists_host = false;
+    }
+    return 0;
+}
+
+int g6x_max_neighbours(int cid)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    return c ? c->maxnb : err;
+}
+
+long long g6x_list_reruns(int cid)
+{
+    int err;
+    Ctx *c = get(cid, &err);
+    return c ? c->list_reruns : (long long)err;
 }
 
 int g6x_set_j_particles(int cid, int n, const int address[], const int index[],

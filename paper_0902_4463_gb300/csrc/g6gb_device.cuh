@@ -259,8 +259,11 @@ struct ForceArgs {
     const double4_32a *p64, *v64;         // FP64 predicted j
     const g6x_irec *irec;
     void *part;                       // PartialDS (DS kernels) or Partial64 (FP64)
-    int *nbl;                         // list entries  [slot][maxnb]
+    int *nbl;                         // list entries  [slot][nbseg]
     int *nbc;                         // list counts   [slot]
+    int maxnb;                        // list length kept per i-particle (Sect. 4)
+    int nbseg;                        // entries a list partial has room for (<= maxnb)
+    int *nbmax;                       // largest min(count, maxnb) of any list partial
     int *err;
     long long W;
     int J;

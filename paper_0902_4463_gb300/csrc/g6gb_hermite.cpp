@@ -99,12 +99,21 @@ int force(g6h_sim &s, int ni, const double *xi, const double *vi, const int *ii,
     rc = g6_read_neighbour_list(s.cid);
     if (rc < 0)
         return rc;
+    const int maxnb = g6x_max_neighbours(s.cid);
+    if (maxnb < 0)
+        return maxnb;
+    try {
+        if ((int)s.nbl.size() < maxnb)
+            s.nbl.resize(maxnb);
+    } catch (...) {
+        return G6_ENOMEM;
+    }
     for (int q = 0; q < ni; ++q) {
         int len = 0;
-        const int r = g6_get_neighbour_list(s.cid, q, G6_MAXNB, &len, s.nbl.data());
+        const int r = g6_get_neighbour_list(s.cid, q, maxnb, &len, s.nbl.data());
         if (r < 0)
             return r;
-        s.nb_entries += std::min(len, G6_MAXNB);
+        s.nb_entries += std::min(len, maxnb);
         s.nb_overflowed += r == G6_EOVERFLOW;
     }
     s.nb_lists += ni;
@@ -545,7 +554,6 @@ int g6h_set_neighbour_radius(g6h_sim *s, double h2)
     if (h2 > 0) {
         try {
             s->h2v.resize(s->n);
-            s->nbl.resize(G6_MAXNB);
         } catch (...) {
             return G6_ENOMEM;
         }

@@ -234,11 +234,19 @@ cudaError_t launch_predict(int kind, JStore js, Pred p, int nj, int nj_pad,
 cudaError_t launch_update_predict(int kind, JStore js, Pred p, int nj, int nj_pad, double t,
                                   const g6x_jrec *rec, const int *toff, int ntiles_all,
                                   int sm_count, cudaStream_t s);
+// Neighbour lists of a launch (Sect. 4): maxnb entries kept per i-particle,
+// room for nbseg of them per list partial (one CTA's segment of one
+// i-particle), and a device int that receives the largest min(count, maxnb)
+// of any partial -- above nbseg the lists of that launch are incomplete.
+struct ListArgs {
+    int maxnb, nbseg;
+    int *nbmax;
+};
 cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
                          const g6x_irec *d_irec, int ni, double eps2,
                          void *part, int *nbl_part, int *nbc_part,
                          int *d_err, cudaStream_t s, const FusedPred *fp = nullptr,
-                         bool pdl = false);
+                         bool pdl = false, const ListArgs *lists = nullptr);
 // DS force with the reduction fused in (no neighbour lists): the last CTA
 // to finish an i-tile writes its results to out.  tcnt holds one counter per
 // i-tile, zero before the launch and left zero by a launch that completes.
@@ -257,7 +265,8 @@ cudaError_t launch_force_ws(const ForceConfig &cfg, const g6x_irec *d_irec, int 
 cudaError_t launch_reduce(const ForceConfig &cfg, const void *part,
                           const int *nbl_part, const int *nbc_part,
                           const int *jidx, int ni, g6x_out *d_out,
-                          int *d_nbl, int *d_nblen, cudaStream_t s, bool pdl = false);
+                          int *d_nbl, int *d_nblen, cudaStream_t s, bool pdl = false,
+                          const ListArgs *lists = nullptr);
 // pdl: launch with programmatic stream serialization (the kernel may start
 // behind its predecessor in s and waits for it before reading anything).
 

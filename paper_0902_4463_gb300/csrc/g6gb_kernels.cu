@@ -777,8 +777,11 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                 P->pot = cslot(k, 6);
                 P->nnr2 = nnr[k];
                 P->nnj = nn_rescan(k);
-                if constexpr (LIST)
+                if constexpr (LIST) {
                     a.nbc[(size_t)seg * ITILE + il] = nbn[k];
+                    if (nbn[k] > 0)
+                        atomicMax(a.nbmax, min(nbn[k], a.maxnb));
+                }
             }
         } else {
             // The TJ j-groups of an i-particle combine in place: every
@@ -897,14 +900,14 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                 if constexpr (LIST) {
                     const int il = k * TI + ti;
                     const int j0 = jt * JT + 2 * jp;
-                    int *dst = a.nbl + ((size_t)(c + t) * ITILE + il) * G6_MAXNB;
+                    int *dst = a.nbl + ((size_t)(c + t) * ITILE + il) * a.nbseg;
                     if (key.x < h2[k]) {
-                        if (nbn[k] < G6_MAXNB)
+                        if (nbn[k] < a.nbseg)
                             dst[nbn[k]] = j0;
                         ++nbn[k];
                     }
                     if (key.y < h2[k]) {
-                        if (nbn[k] < G6_MAXNB)
+                        if (nbn[k] < a.nbseg)
                             dst[nbn[k]] = j0 + 1;
                         ++nbn[k];
                     }
@@ -1039,8 +1042,11 @@ __global__ void __launch_bounds__(128) k_force_64(const ForceArgs a)
         P->pot = s[6];
         P->nnr2 = nnr;
         P->nnj = nnj;
-        if constexpr (LIST)
+        if constexpr (LIST) {
             a.nbc[(size_t)seg * TI + tid] = nbn;
+            if (nbn > 0)
+                atomicMax(a.nbmax, min(nbn, a.maxnb));
+        }
     };
 
     for (long long p = wb; p < we; ++p) {
@@ -1100,8 +1106,8 @@ __global__ void __launch_bounds__(128) k_force_64(const ForceArgs a)
             }
             if constexpr (LIST) {
                 if (key < h2) {
-                    if (nbn < G6_MAXNB)
-                        a.nbl[((size_t)(c + t) * TI + tid) * G6_MAXNB + nbn] = jbase + jj;
+                    if (nbn < a.nbseg)
+                        a.nbl[((size_t)(c + t) * TI + tid) * a.nbseg + nbn] = jbase + jj;
                     ++nbn;
                 }
             }
@@ -1120,13 +1126,14 @@ struct ReduceArgs {
     int *nbl_out, *nblen_out;
     long long W;
     int J, G, ni, itile, list;
+    int maxnb, nbseg;                 // list length kept; entries per list partial
 };
 
 
 // K3, one warp per i-particle: lanes take the partials of the CTAs that
 // touched its i-tile and combine with warp shuffles (Sect. 2.3, 2.5).
 // Neighbour lists are concatenated in segment order, which is ascending j,
-// and truncated at G6_MAXNB (Sect. 4).
+// and truncated at the context's list length (Sect. 4).
 template <class PT>
 __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a)
 {
@@ -1155,7 +1162,7 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a)
     for (long long c0 = clo; c0 <= chi; c0 += 32) {
         long long cc = c0 + lane;
         int cnt = cc <= chi ? a.nbc[(size_t)(cc + t) * a.itile + il] : 0;
-        int kept = min(cnt, G6_MAXNB);
+        int kept = min(cnt, a.nbseg);
         int incl = kept;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -1164,9 +1171,9 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a)
                 incl += v;
         }
         long long pos0 = base + incl - kept;
-        const int *src = a.nbl + ((size_t)(cc + t) * a.itile + il) * G6_MAXNB;
-        for (int e = 0; e < kept && pos0 + e < G6_MAXNB; ++e)
-            a.nbl_out[(size_t)i * G6_MAXNB + pos0 + e] = a.jidx[src[e]];
+        const int *src = a.nbl + ((size_t)(cc + t) * a.itile + il) * a.nbseg;
+        for (int e = 0; e < kept && pos0 + e < a.maxnb; ++e)
+            a.nbl_out[(size_t)i * a.maxnb + pos0 + e] = a.jidx[src[e]];
         long long ctot = cnt;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
@@ -1703,7 +1710,8 @@ static bool set_fused_pred(ForceArgs &a, const ForceConfig &cfg, const FusedPred
 cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
                          const g6x_irec *d_irec, int ni, double eps2,
                          void *part, int *nbl_part, int *nbc_part,
-                         int *d_err, cudaStream_t s, const FusedPred *fp, bool pdl)
+                         int *d_err, cudaStream_t s, const FusedPred *fp, bool pdl,
+                         const ListArgs *lists)
 {
     if (cfg.work <= 0)
         return cudaSuccess;
@@ -1721,6 +1729,13 @@ cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
     a.part = part;
     a.nbl = nbl_part;
     a.nbc = nbc_part;
+    if (lists) {
+        a.maxnb = lists->maxnb;
+        a.nbseg = lists->nbseg;
+        a.nbmax = lists->nbmax;
+    }
+    if (cfg.list && (!lists || !lists->nbmax || lists->nbseg < 1 || lists->nbseg > lists->maxnb))
+        return cudaErrorInvalidValue;
     a.err = d_err;
     a.W = cfg.work;
     a.J = cfg.jtiles;
@@ -1772,7 +1787,7 @@ cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
 cudaError_t launch_reduce(const ForceConfig &cfg, const void *part,
                           const int *nbl_part, const int *nbc_part,
                           const int *jidx, int ni, g6x_out *d_out, int *d_nbl,
-                          int *d_nblen, cudaStream_t s, bool pdl)
+                          int *d_nblen, cudaStream_t s, bool pdl, const ListArgs *lists)
 {
     if (ni <= 0)
         return cudaSuccess;
@@ -1792,6 +1807,10 @@ cudaError_t launch_reduce(const ForceConfig &cfg, const void *part,
     a.ni = ni;
     a.itile = cfg.itile;
     a.list = cfg.list;
+    a.maxnb = lists ? lists->maxnb : 0;
+    a.nbseg = lists ? lists->nbseg : 0;
+    if (cfg.list && !lists)
+        return cudaErrorInvalidValue;
     // many partials per i-particle (small blocks spread over many CTAs):
     // one CTA per i-particle; otherwise one warp per i-particle
     const long long per_i = (long long)cfg.grid / cfg.n_itile + 1;

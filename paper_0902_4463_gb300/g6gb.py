@@ -23,6 +23,7 @@ G6_ETIMEDOUT = -110
 G6_ENODEV = -6
 G6_EOVERFLOW = 1
 G6_MAXNB = 256
+G6X_MAXNB_LIMIT = 4096
 G6_MAX_CLUSTERS = 16
 G6X_PREC_DS = 0
 G6X_PREC_FP64 = 1
@@ -55,6 +56,7 @@ EXPORTS = [
     "g6h_set_neighbour_radius", "g6h_neighbour_stats", "g6h_run_blocks",
     "g6h_correct_block_ex", "g6h_set_force_noise", "g6hb_set_force_noise",
     "g6x_fp32_probe", "g6x_fp64_probe", "g6x_plan_launch", "g6x_variant_info",
+    "g6x_set_max_neighbours", "g6x_max_neighbours", "g6x_list_reruns",
     "g6x_batch_create", "g6x_batch_destroy", "g6x_batch_irecs", "g6x_batch_results",
     "g6x_batch_set_j", "g6x_batch_set_j_many", "g6x_batch_calc", "g6x_batch_launch_count",
     "g6x_batch_set_schedule", "g6x_batch_get_schedule", "g6x_batch_autotune", "g6hb_autotune",
@@ -119,6 +121,9 @@ def lib():
             "g6x_fp32_probe": (I, [I, P, P]),
             "g6x_fp64_probe": (I, [I, P, P]),
             "g6x_variant_info": (I, [I, P]),
+            "g6x_set_max_neighbours": (I, [I, I]),
+            "g6x_max_neighbours": (I, [I]),
+            "g6x_list_reruns": (C.c_longlong, [I]),
             "g6x_plan_launch": (I, [I, I, I, I, I, P]),
             "g6h_create": (P, [I, I, P, P, P, D, D, D, D, D, P]),
             "g6h_run": (I, [P, D]),
@@ -269,17 +274,31 @@ def g6_read_neighbour_list(cid):
     return _check(lib().g6_read_neighbour_list(cid), "g6_read_neighbour_list")
 
 
-def g6_get_neighbour_list(cid, ipipe, maxlength=G6_MAXNB):
-    """Returns (rc, nblen, list) where list holds min(nblen, maxlength, 256) ids."""
+def g6_get_neighbour_list(cid, ipipe, maxlength=None):
+    """Returns (rc, nblen, list) where list holds min(nblen, maxlength, the
+    context's list length) ids; maxlength defaults to that list length."""
+    maxnb = g6x_max_neighbours(cid)
+    maxlength = maxnb if maxlength is None else int(maxlength)
     nbl = np.empty(max(1, maxlength), dtype=np.int32)
     nblen = C.c_int(0)
     rc = _check(lib().g6_get_neighbour_list(cid, int(ipipe), int(maxlength), C.byref(nblen),
                                             _p(nbl)), "g6_get_neighbour_list")
-    n = min(nblen.value, maxlength, G6_MAXNB)
+    n = min(nblen.value, maxlength, maxnb)
     return rc, nblen.value, nbl[:n].copy()
 
 
 # ------------------------------------------------------------- extensions --
+
+def g6x_set_max_neighbours(cid, maxnb):
+    return _check(lib().g6x_set_max_neighbours(cid, int(maxnb)), "g6x_set_max_neighbours")
+
+
+def g6x_max_neighbours(cid):
+    return _check(lib().g6x_max_neighbours(cid), "g6x_max_neighbours")
+
+
+def g6x_list_reruns(cid):
+    return lib().g6x_list_reruns(cid)
 
 def g6x_set_precision(cid, mode):
     return _check(lib().g6x_set_precision(cid, int(mode)), "g6x_set_precision")

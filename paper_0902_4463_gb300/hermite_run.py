@@ -40,7 +40,7 @@ def energy_fp64(cid, sim, mode):
 
 
 def run(n, seed, eps2, eta, t_end, prec="ds", binaries=0.0, dt_max=2.0 ** -4, cid=0,
-        tune=None, h2=0.0, noise=0.0):
+        tune=None, h2=0.0, noise=0.0, maxnb=0):
     """Integrate and return the result dict (the context is opened and closed
     here)."""
     _build.build()
@@ -54,6 +54,8 @@ def run(n, seed, eps2, eta, t_end, prec="ds", binaries=0.0, dt_max=2.0 ** -4, ci
         g6.g6x_set_precision(cid, mode)
         if tune:
             g6.g6x_load_tuning(tune)
+        if maxnb > 0:
+            g6.g6x_set_max_neighbours(cid, maxnb)
         sim = g6.G6HSim(cid, m, x, v, eps2, eta, dt_max=dt_max)
         if h2 > 0:
             sim.set_neighbour_radius(h2)
@@ -79,6 +81,7 @@ def run(n, seed, eps2, eta, t_end, prec="ds", binaries=0.0, dt_max=2.0 ** -4, ci
                 interactions_per_s=inter / wall, gflops_60=60.0 * inter / wall / 1e9,
                 dE_over_E=(e1 - e0) / e0, E0=e0, E1=e1, block_hist_log2=hist,
                 profile=prof, h2=h2, force_noise=noise, neighbour_lists=nbs,
+                max_neighbours=maxnb or g6.G6_MAXNB,
                 synchronised=bool(np.all(state["t"] == t_end)))
 
 
@@ -97,9 +100,11 @@ def main(argv=None):
                     help="neighbour-list radius^2 requested every block step (0: none)")
     ap.add_argument("--noise", type=float, default=0.0,
                     help="relative force error the time-step choice allows for (0: none)")
+    ap.add_argument("--maxnb", type=int, default=0,
+                    help="neighbour-list length (0: the default, 256)")
     a = ap.parse_args(argv)
     r = run(a.n, a.seed, a.eps2, a.eta, a.t_end, a.prec, a.binaries, tune=a.tune, h2=a.h2,
-            noise=a.noise)
+            noise=a.noise, maxnb=a.maxnb)
     print(json.dumps(r))
     return 0
 

@@ -91,36 +91,59 @@ def _list_ok(gpu_ids, orc_pos, idx_j, xi, xj, h2, tol=1e-6):
         assert abs(r2 - h2) <= tol * h2, (k, r2, h2)
 
 
+@pytest.mark.parametrize("maxnb", [64, 256, 1024])
 @pytest.mark.parametrize("prec", [g6.G6X_PREC_DS, g6.G6X_PREC_FP64])
-def test_neighbour_lists_plummer_with_binaries(open_ctx, orc, prec):
+def test_neighbour_lists_plummer_with_binaries(open_ctx, orc, prec, maxnb):
+    # Sect. 4 lists at the list lengths 64, 256 (the paper's) and 1024
+    # against the oracle's lists truncated at the same length: contents,
+    # ascending order, overflow flags.  The list parts start with room for a
+    # few entries, so the first read computes the lists once more with
+    # larger parts; a second calculation of the same block needs no more.
     n, eps2 = 8192, 1e-8
     m, x, v, pairs = ics.plummer_with_binaries(n, 5)
     idx = np.arange(n)
     cid = open_ctx(n, n)
     g6.g6x_set_precision(cid, prec)
+    g6.g6x_set_max_neighbours(cid, maxnb)
+    assert g6.g6x_max_neighbours(cid) == maxnb
     load_j(cid, x, v, m)
     act = np.sort(ics.permutation(n, 5)[:600])
     h2 = np.full(act.size, 1e-4)
     h2[::7] = 0.05 ** 2                       # some long lists
-    h2[::11] = 0.3 ** 2                       # some that overflow 256
-    acc, jerk, pot, nnb = sweep(cid, n, x[act], v[act], act, eps2, 0.0, h2=h2)
-    rc = g6.g6_read_neighbour_list(cid)
-    nblen, nbl, nov = orc.neighbours(x[act], act, x, idx, h2, maxnb=g6.G6_MAXNB)
-    assert rc == (g6.G6_EOVERFLOW if nov else 0) and nov > 0
-    for q in range(act.size):
-        rc_q, ln, ids = g6.g6_get_neighbour_list(cid, q, g6.G6_MAXNB)
-        if nblen[q] <= g6.G6_MAXNB:
-            assert abs(ln - nblen[q]) <= 2
-            _list_ok(ids, nbl[q, :nblen[q]], idx, x[act[q]], x, h2[q])
-            assert list(ids) == sorted(ids)            # ascending j-slot
-        else:
-            assert ln > g6.G6_MAXNB and rc_q == g6.G6_EOVERFLOW
-            assert len(ids) == g6.G6_MAXNB and list(ids) == sorted(ids)
+    h2[::11] = 0.3 ** 2                       # some that overflow 64 and 256
+    h2[::13] = 1.0                            # some that overflow 1024
+    nblen, nbl, nov = orc.neighbours(x[act], act, x, idx, h2, maxnb=maxnb)
+    for rep in range(2):
+        acc, jerk, pot, nnb = sweep(cid, n, x[act], v[act], act, eps2, 0.0, h2=h2)
+        rc = g6.g6_read_neighbour_list(cid)
+        assert g6.g6x_list_reruns(cid) == 1          # only the first read ran again
+        assert rc == (g6.G6_EOVERFLOW if nov else 0) and nov > 0
+        for q in range(act.size):
+            rc_q, ln, ids = g6.g6_get_neighbour_list(cid, q)
+            if nblen[q] <= maxnb:
+                assert abs(ln - nblen[q]) <= 2
+                _list_ok(ids, nbl[q, :nblen[q]], idx, x[act[q]], x, h2[q])
+                assert list(ids) == sorted(ids)            # ascending j-slot
+            else:
+                assert ln > maxnb and rc_q == g6.G6_EOVERFLOW
+                assert len(ids) == maxnb and list(ids) == sorted(ids)
+                # truncation keeps the lowest j-slots: the oracle's first maxnb
+                # up to members within rounding of the radius
+                _list_ok(ids, nbl[q, :maxnb], idx, x[act[q]], x, h2[q])
     # forces are unchanged by list building
     oa, *_ = orc.force(x[act], v[act], act, x, v, m, idx, eps2)
     ea = rel_err_vec(acc, oa)
     lim = (1e-6, 1e-5) if prec == g6.G6X_PREC_DS else (1e-12, 1e-10)
     assert np.median(ea) <= lim[0] and ea.max() <= lim[1]
+
+
+def test_list_length_setting_is_validated(open_ctx):
+    cid = open_ctx(1024, 64)
+    assert g6.g6x_max_neighbours(cid) == g6.G6_MAXNB
+    for bad in (0, -1, g6.G6X_MAXNB_LIMIT + 1):
+        with pytest.raises(g6.G6Error):
+            g6.g6x_set_max_neighbours(cid, bad)
+    assert g6.g6x_max_neighbours(cid) == g6.G6_MAXNB
 
 
 def test_lists_with_all_radii_zero_are_empty(open_ctx):
