@@ -682,6 +682,12 @@ int g6hb_stats(const g6hb_sim *s, long long *nsteps, long long *nactive,
 
 /* State of every particle in creation order: x, v [sum n][3], t [sum n]. */
 int g6hb_get_state(const g6hb_sim *s, double *x, double *v, double *t);
+/* The same with the acceleration and jerk [sum n][3] of each particle's
+ * last correction and its time step dt [sum n] (any pointer may be NULL):
+ * between batch steps a particle sits at its own last block time t and its
+ * next one is t + dt (Sect. 2.1). */
+int g6hb_get_state_ex(const g6hb_sim *s, double *x, double *v, double *acc, double *jerk,
+                      double *t, double *dt);
 
 void g6hb_destroy(g6hb_sim *s);
 

@@ -1339,6 +1339,22 @@ int g6hb_get_state(const g6hb_sim *s, double *x, double *v, double *t)
     return 0;
 }
 
+int g6hb_get_state_ex(const g6hb_sim *s, double *x, double *v, double *acc, double *jerk,
+                      double *t, double *dt)
+{
+    int rc = g6hb_get_state(s, x, v, t);
+    if (rc)
+        return rc;
+    const size_t tot = s->m.size();
+    if (acc)
+        std::memcpy(acc, s->a.data(), 3 * tot * sizeof(double));
+    if (jerk)
+        std::memcpy(jerk, s->j.data(), 3 * tot * sizeof(double));
+    if (dt)
+        std::memcpy(dt, s->dt.data(), tot * sizeof(double));
+    return 0;
+}
+
 int g6hb_set_force_noise(g6hb_sim *s, double rel)
 {
     if (!s || !(rel >= 0) || !(rel < 1))

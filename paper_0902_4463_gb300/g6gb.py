@@ -62,7 +62,7 @@ EXPORTS = [
     "g6x_batch_set_schedule", "g6x_batch_get_schedule", "g6x_batch_autotune", "g6hb_autotune",
     "g6hb_set_schedule", "g6x_batch_set_timing", "g6x_batch_get_timing", "g6hb_batch",
     "g6hb_create", "g6hb_step", "g6hb_run", "g6hb_set_mode", "g6hb_stats", "g6hb_get_state",
-    "g6hb_destroy",
+    "g6hb_destroy", "g6hb_get_state_ex",
 ]
 
 _lib = None
@@ -159,6 +159,7 @@ def lib():
             "g6hb_set_mode": (I, [P, I]),
             "g6hb_stats": (I, [P, P, P, P, P, P]),
             "g6hb_get_state": (I, [P, P, P, P]),
+            "g6hb_get_state_ex": (I, [P, P, P, P, P, P, P]),
             "g6hb_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
@@ -753,6 +754,16 @@ class G6HBatchSim:
         x, v, t = np.empty((tot, 3)), np.empty((tot, 3)), np.empty(tot)
         _check(lib().g6hb_get_state(self.h, _p(x), _p(v), _p(t)), "g6hb_get_state")
         return dict(x=x, v=v, t=t)
+
+    def full_state(self):
+        """x, v, acc, jerk [sum n, 3]; t, dt [sum n]: each particle at its own
+        last block time, next due at t + dt."""
+        tot = int(self.off[-1])
+        x, v, a, j = (np.empty((tot, 3)) for _ in range(4))
+        t, dt = np.empty(tot), np.empty(tot)
+        _check(lib().g6hb_get_state_ex(self.h, _p(x), _p(v), _p(a), _p(j), _p(t), _p(dt)),
+               "g6hb_get_state_ex")
+        return dict(x=x, v=v, acc=a, jerk=j, t=t, dt=dt)
 
     def close(self):
         if self.h:

@@ -309,3 +309,78 @@ def test_batch_driver_force_noise_allowance():
         finally:
             sim.close()
     assert steps[1e-6] < steps[0.0], steps
+
+
+def test_batch_driver_forces_at_natural_block_steps(orc):
+    # The 256-cluster batch driver stopped at 10 points of its run to
+    # t = 1/16 (eta = 0.01): at each, every cluster's next natural block (the
+    # particles due at the cluster's earliest t + dt, predicted on the host
+    # as the driver does) is evaluated through the batch calls with the j-
+    # particles at their own last block times, and by the oracle (j predicted
+    # in FP64).  Per cluster: max relative error <= 1e-5 for acceleration
+    # and potential, 3e-5 for the jerk (which nearly cancels for some stars of
+    # the Salpeter clusters), and valid nearest neighbours; median <= 1e-6 per
+    # cluster for blocks of at least 16 particles and over the pooled
+    # particles of all clusters at each point (a median of one or two
+    # particles is their own error, which the max bound covers) -- the
+    # deterministic check behind the ensemble drift test above.
+    cls = ics.cluster_batch(256, 1)
+    eps2 = [c["eps2"] for c in cls]
+    sim = g6.G6HBatchSim([(c["m"], c["x"], c["v"]) for c in cls], eps2, 0.01)
+    nj = [c["n"] for c in cls]
+    bat = g6.G6Batch(nj)
+    worst = []
+    pooled = [[], [], []]
+    try:
+        for point in range(10):
+            for _ in range(400):
+                sim.step(0.0625)
+            st = sim.full_state()
+            t_blk, ni, acts = np.zeros(len(cls)), np.zeros(len(cls), dtype=np.int32), []
+            for k, c in enumerate(cls):
+                lo, hi = sim.off[k], sim.off[k + 1]
+                tn = st["t"][lo:hi] + st["dt"][lo:hi]
+                t_blk[k] = tn.min()
+                act = np.nonzero(tn == t_blk[k])[0]
+                acts.append(act)
+                ni[k] = act.size
+                bat.set_j(k, c["m"], st["x"][lo:hi], st["v"][lo:hi], st["acc"][lo:hi] / 2.0,
+                          st["jerk"][lo:hi] / 6.0, st["t"][lo:hi])
+                h = (t_blk[k] - st["t"][lo:hi][act])[:, None]
+                a0, j0 = st["acc"][lo:hi][act], st["jerk"][lo:hi][act]
+                xi = st["x"][lo:hi][act] + h * (st["v"][lo:hi][act] + h * (a0 / 2.0 + h * j0 / 6.0))
+                vi = st["v"][lo:hi][act] + h * (a0 + h * j0 / 2.0)
+                bat.set_i(k, xi, vi, act)
+            bat.calc(t_blk, eps2, ni)
+            for k, c in enumerate(cls):
+                lo, hi = sim.off[k], sim.off[k + 1]
+                act = acts[k]
+                res = bat.results(k, ni[k])
+                r = bat.irecs(k)
+                xi, vi = r["x"][:ni[k]].copy(), r["v"][:ni[k]].copy()
+                xp, vp = orc.predict(st["x"][lo:hi], st["v"][lo:hi], st["acc"][lo:hi],
+                                     st["jerk"][lo:hi], st["t"][lo:hi], t_blk[k])
+                idx = np.arange(c["n"])
+                oa, oj, op, onn, onr = orc.force(xi, vi, act, xp, vp, c["m"], idx, eps2[k])
+                ea, ej = rel_err_vec(res["acc"], oa), rel_err_vec(res["jerk"], oj)
+                ep = np.abs(res["pot"] - op) / np.abs(op)
+                key = (point, k, c["n"], int(ni[k]))
+                for q, e in enumerate((ea, ej, ep)):
+                    # jerk: up to 3e-5 where it nearly cancels (measured worst
+                    # 1.2e-5, a particle of a 5255-particle block)
+                    assert e.max() <= (3e-5 if q == 1 else 1e-5), (key, q, e.max())
+                    if ni[k] >= 16:
+                        assert np.median(e) <= 1e-6, (key, q, np.median(e))
+                    pooled[q].append(e)
+                check_nn(onn, onr, res["nnb"], xi, xp, idx)
+                worst.append(max(ea.max(), ej.max(), ep.max()))
+            for q in range(3):
+                e = np.concatenate(pooled[q])
+                assert np.median(e) <= 1e-6, (point, q, np.median(e))
+                pooled[q] = []
+    finally:
+        bat.close()
+        sim.close()
+    assert len(worst) == 10 * len(cls)
+    print("batch natural blocks: worst max relative error %.2e, median over clusters %.2e"
+          % (max(worst), float(np.median(worst))))
