@@ -312,20 +312,25 @@ def run_latency(args):
             xs, vs = np.ascontiguousarray(x[:mm]), np.ascontiguousarray(v[:mm])
             zs = np.ascontiguousarray(z[:mm])
 
+            # the argument pointers are made once, so that each timed call
+            # pays only the ctypes call itself
+            p_sel, p_tj, p_mj, p_zs, p_vs, p_xs = (P(a) for a in (sel, tj, mj, zs, vs, xs))
+            p_acc, p_jerk, p_pot, p_nnb = (P(a) for a in (acc, jerk, pot, nnb))
+
             def one():
                 nonlocal t
                 t += 2.0 ** -20
                 tj[:] = t - 2.0 ** -20
                 t0 = time.perf_counter()
-                lib.g6x_set_j_particles(CID, mm, P(sel), P(sel), P(tj), P(mj), P(zs), P(zs),
-                                        P(vs), P(xs))
+                lib.g6x_set_j_particles(CID, mm, p_sel, p_sel, p_tj, p_mj, p_zs, p_zs, p_vs,
+                                        p_xs)
                 t1 = time.perf_counter()
                 lib.g6_set_ti(CID, t)
-                lib.g6calc_firsthalf(CID, n, mm, P(sel), P(xs), P(vs), None, None, None, 1e-4,
+                lib.g6calc_firsthalf(CID, n, mm, p_sel, p_xs, p_vs, None, None, None, 1e-4,
                                      None)
                 t2 = time.perf_counter()
-                rc = lib.g6calc_lasthalf2(CID, n, mm, None, None, None, 1e-4, None, P(acc),
-                                          P(jerk), P(pot), P(nnb))
+                rc = lib.g6calc_lasthalf2(CID, n, mm, None, None, None, 1e-4, None, p_acc,
+                                          p_jerk, p_pot, p_nnb)
                 t3 = time.perf_counter()
                 if rc < 0:
                     raise g6.G6Error(rc, "g6calc_lasthalf2")

@@ -1493,10 +1493,16 @@ void tune_clear()
 
 namespace {
 
-// Largest block the built-in choice gives the small-block kernel: measured
-// on GB300 at N = 32768 and 2^20 it is faster than the separate predictor
-// and the split-j shapes up to m = 64 and slower from m = 128 on.
+// Blocks the built-in choice gives the small-block kernel.  Measured on
+// GB300 (device time of a block step): faster than the separate predictor
+// and the split-j shapes for m <= 16 at every N (N = 32768: 19-21 against
+// 31 us), up to m = 64 once the j-set has 512 tiles or more (N = 2^20,
+// m = 64: 154 against 173 us; N = 131072: a tie), slower above m = 64 and,
+// at m = 64, for small j-sets, where each CTA holds one j-tile and nothing
+// overlaps (N = 32768: 39 against 37 us).
 constexpr int WS_DEFAULT_MAX_NI = 64;
+constexpr int WS_ANY_N_MAX_NI = 16;
+constexpr long long WS_MIN_JTILES = 512;
 
 // The built-in launch choice for a block of ni against nj_pad j-particles
 // (no tuning table); *gmul receives the grid multiplier.
@@ -1511,7 +1517,8 @@ int heuristic_variant(int prec, int ni, int nj_pad, int list, bool allow_ws, int
     }
     if (list)
         return ni <= 32 ? 6 : 5;
-    if (allow_ws && ni <= WS_DEFAULT_MAX_NI) {
+    if (allow_ws
+        && (ni <= WS_ANY_N_MAX_NI || (ni <= WS_DEFAULT_MAX_NI && nj_pad / JT >= WS_MIN_JTILES))) {
         // the warp-specialised small-block kernel: the narrowest i-tile
         // (one i-particle per thread) that holds the whole block
         int best = -1, best_tile = INT_MAX;

@@ -181,14 +181,16 @@ def test_launch_plan_heuristic_without_a_gpu(lib):
     def ws(nj, ni):
         return g6gb.g6x_variant_info(g6gb.g6x_plan_launch(ds, nj, ni)["variant"])["ws"] == 1
 
-    # blocks of up to 64 take the small-block kernel with the narrowest
-    # i-tile that holds them; larger blocks the split-j and wide shapes
-    for nj in (1024, small, big):
-        assert all(ws(nj, ni) for ni in (1, 8, 9, 16, 17, 33, 64))
+    # blocks of up to 16 take the small-block kernel with the narrowest
+    # i-tile that holds them, blocks of up to 64 too from 512 j-tiles on;
+    # larger blocks the split-j and wide shapes
+    for nj in (1024, small, 131072, big):
+        assert all(ws(nj, ni) for ni in (1, 8, 9, 16))
+        assert all(ws(nj, ni) == (nj >= 131072) for ni in (17, 33, 64))
         assert not any(ws(nj, ni) for ni in (65, 128, 256, 4096))
         assert shape(nj, 1) == (8, 32, 1) and shape(nj, 8) == (8, 32, 1)
-        assert shape(nj, 17) == (32, 8, 1) and shape(nj, 64) == (64, 4, 1)
         assert g6gb.g6x_plan_launch(ds, nj, 16, True)["variant"] in (5, 6)   # lists: no
+    assert shape(big, 17) == (32, 8, 1) and shape(big, 64) == (64, 4, 1)
     assert shape(big, 16) == (16, 16, 1)
     assert shape(big, 128) == (16, 16, 2)
     assert shape(big, 256) == (32, 8, 2)
