@@ -25,6 +25,37 @@ __device__ __forceinline__ float rsqrt_approx(float x)
     return y;
 }
 
+// 1/x on the multi-function unit (the pair loops take r^-2 from here rather
+// than as r^-1 * r^-1, one operation less on the FP32 pipe): +inf -> 0.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Softened |r|^2 = dx^2 + dy^2 + dz^2 + eps^2 of a j-pair (packed FP32x2),
+// eps^2 folded into the first fused multiply-add.  The pair loops use it as
+// the nearest-neighbour and list key (in exact arithmetic the same order as
+// |r|^2, eps^2 being one constant per call); the rescans that find the
+// winning j use the scalar form, whose lanes round identically.
+__device__ __forceinline__ float2 soft_r2(float2 dx, float2 dy, float2 dz, float2 e2)
+{
+    return __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, e2)));
+}
+
+__device__ __forceinline__ float soft_r2(float dx, float dy, float dz, float e2)
+{
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmaf_rn(dx, dx, e2)));
+}
+
+// A partial record's nearest-neighbour distance without the softening
+// (+inf stays +inf; rounding is monotone, so no two records change order).
+__device__ __forceinline__ float unsoftened(float key, float e2)
+{
+    return fmaxf(__fsub_rn(key, e2), 0.f);
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -288,12 +288,14 @@ __device__ __forceinline__ float2 ds_sep2(float2 h, float2 l, float2 nh, float2 
 
 // Pair forces in FP32 with the DS separation of Eq. 3 (Sect. 2.3).  Per pair:
 //   dx   = (xj_hi - xi_hi) + (xj_lo - xi_lo)                       Eq. 3
-//   r2u  = |dx|^2  (nearest neighbour and lists use it unsoftened)
-//   key  = r2u, or +inf for the i-particle's own j (index match)
-//   1/r  = rsqrt(key + eps2)            (+inf -> 0: the pair adds nothing)
+//   r2   = |dx|^2 + eps2, or +inf for the i-particle's own j (index match)
+//   1/r  = rsqrt(r2), 1/r^2 = rcp(r2)    (+inf -> 0: the pair adds nothing)
 //   acc  += m r^-3 dx
 //   jerk += m r^-3 (dv - 3 (dx.dv) r^-2 dx)
 //   pot  += m r^-1                      (negated in K3)
+// The softened r2 is also the key of the nearest neighbour and of the lists
+// (against h2 + eps2); the partial records carry the neighbour's distance
+// with eps2 taken off again.  32 FP32 lane operations per pair.
 // Each thread holds NI i-particles and walks its share of every j-tile two
 // j-particles at a time: the pair of j values of one component is one float2
 // and the arithmetic uses the packed FP32x2 instructions of sm_100+, which
@@ -533,7 +535,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                         w[3 + d] = __double2float_rn(x - (double)hi);
                         w[6 + d] = (float)r.v[d];
                     }
-                    w[9] = (float)r.h2;
+                    w[9] = (float)(r.h2 + (double)eps2.x);
                     w[10] = __int_as_float(r.index);
                 } else {
 #pragma unroll
@@ -574,7 +576,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                     float w = -(float)r.v[d];
                     nv[k][d] = make_float2(w, w);
                 }
-                h2[k] = (float)r.h2;
+                h2[k] = (float)(r.h2 + (double)eps2.x);
                 iid[k] = r.index;
             } else {
 #pragma unroll
@@ -650,7 +652,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                                 dd[d] = __fadd_rn(__fadd_rn(ph[d], nxh[k][d].x),
                                                   __fadd_rn(pl[d], nxl[k][d].x));
                         }
-                        r2u = __fmaf_rn(dd[2], dd[2], __fmaf_rn(dd[1], dd[1], __fmul_rn(dd[0], dd[0])));
+                        r2u = soft_r2(dd[0], dd[1], dd[2], eps2.x);
                     }
                     key[2 * u + h] = (id == iid[k]) ? INF : r2u;
                 }
@@ -775,7 +777,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                     P->jerk[d] = cslot(k, 3 + d);
                 }
                 P->pot = cslot(k, 6);
-                P->nnr2 = nnr[k];
+                P->nnr2 = unsoftened(nnr[k], eps2.x);
                 P->nnj = nn_rescan(k);
                 if constexpr (LIST) {
                     a.nbc[(size_t)seg * ITILE + il] = nbn[k];
@@ -825,7 +827,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                     P->jerk[d] = make_float2(sh[3 + d], sl[3 + d]);
                 }
                 P->pot = make_float2(sh[6], sl[6]);
-                P->nnr2 = br;
+                P->nnr2 = unsoftened(br, eps2.x);
                 P->nnj = bj;
             }
             __syncthreads();
@@ -875,17 +877,17 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                 const float2 ux = __fadd2_rn(vx, nv[k][0]);
                 const float2 uy = __fadd2_rn(vy, nv[k][1]);
                 const float2 uz = __fadd2_rn(vz, nv[k][2]);
-                float2 key = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                float2 key = soft_r2(dx, dy, dz, eps2);
                 if constexpr (SELF) {
                     key.x = (id.x == iid[k]) ? INF : key.x;
                     key.y = (id.y == iid[k]) ? INF : key.y;
                 }
-                const float2 r2 = __fadd2_rn(key, eps2);
-                float2 ri;
-                ri.x = rsqrt_approx(r2.x);
-                ri.y = rsqrt_approx(r2.y);
+                float2 ri, ri2;
+                ri.x = rsqrt_approx(key.x);
+                ri.y = rsqrt_approx(key.y);
+                ri2.x = rcp_approx(key.x);
+                ri2.y = rcp_approx(key.y);
                 const float2 rv = __ffma2_rn(dz, uz, __ffma2_rn(dy, uy, __fmul2_rn(dx, ux)));
-                const float2 ri2 = __fmul2_rn(ri, ri);
                 const float2 mr = __fmul2_rn(mj, ri);
                 const float2 mr3 = __fmul2_rn(mr, ri2);
                 const float2 sc = __fmul2_rn(__fmul2_rn(rv, ri2), m3);

@@ -342,8 +342,8 @@ __global__ void __launch_bounds__(TI * TJ + 32, MINB) k_force_ws(const ForceArgs
             }
     };
 
-    // The key (unsoftened |r|^2, +inf for the i-particle's own j) of j-pair
-    // jp of a predicted tile, with the pair loop's own packed operations.
+    // The key (softened |r|^2, +inf for the i-particle's own j) of j-pair jp
+    // of a predicted tile, with the pair loop's own packed operations.
     auto pair_key = [&](const float *S, int jp, int k) -> float2 {
         const float2 xh = reinterpret_cast<const float2 *>(S + W_XH * JT)[jp];
         const float2 yh = reinterpret_cast<const float2 *>(S + W_YH * JT)[jp];
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(TI * TJ + 32, MINB) k_force_ws(const ForceArgs
         const float2 dx = __fadd2_rn(__fadd2_rn(xh, nxh[k][0]), __fadd2_rn(xl, nxl[k][0]));
         const float2 dy = __fadd2_rn(__fadd2_rn(yh, nxh[k][1]), __fadd2_rn(yl, nxl[k][1]));
         const float2 dz = __fadd2_rn(__fadd2_rn(zh, nxh[k][2]), __fadd2_rn(zl, nxl[k][2]));
-        float2 key = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        float2 key = soft_r2(dx, dy, dz, eps2);
         key.x = (id.x == iid[k]) ? INF : key.x;
         key.y = (id.y == iid[k]) ? INF : key.y;
         return key;
@@ -393,17 +393,17 @@ __global__ void __launch_bounds__(TI * TJ + 32, MINB) k_force_ws(const ForceArgs
                 const float2 ux = __fadd2_rn(vx, nv[k][0]);
                 const float2 uy = __fadd2_rn(vy, nv[k][1]);
                 const float2 uz = __fadd2_rn(vz, nv[k][2]);
-                float2 key = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                float2 key = soft_r2(dx, dy, dz, eps2);
                 if constexpr (SELF) {
                     key.x = (id.x == iid[k]) ? INF : key.x;
                     key.y = (id.y == iid[k]) ? INF : key.y;
                 }
-                const float2 r2 = __fadd2_rn(key, eps2);
-                float2 ri;
-                ri.x = rsqrt_approx(r2.x);
-                ri.y = rsqrt_approx(r2.y);
+                float2 ri, ri2;
+                ri.x = rsqrt_approx(key.x);
+                ri.y = rsqrt_approx(key.y);
+                ri2.x = rcp_approx(key.x);
+                ri2.y = rcp_approx(key.y);
                 const float2 rv = __ffma2_rn(dz, uz, __ffma2_rn(dy, uy, __fmul2_rn(dx, ux)));
-                const float2 ri2 = __fmul2_rn(ri, ri);
                 const float2 mr = __fmul2_rn(mj, ri);
                 const float2 mr3 = __fmul2_rn(mr, ri2);
                 const float2 sc = __fmul2_rn(__fmul2_rn(rv, ri2), m3);
@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(TI * TJ + 32, MINB) k_force_ws(const ForceArgs
                 P->jerk[d] = make_float2(sh[3 + d], sl[3 + d]);
             }
             P->pot = make_float2(sh[6], sl[6]);
-            P->nnr2 = br;
+            P->nnr2 = unsoftened(br, eps2.x);
             P->nnj = bj;
         }
     } else {
@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(TI * TJ + 32, MINB) k_force_ws(const ForceArgs
                 P->jerk[d] = cslot(k, 3 + d);
             }
             P->pot = cslot(k, 6);
-            P->nnr2 = nnr[k];
+            P->nnr2 = unsoftened(nnr[k], eps2.x);
             P->nnj = nnj[k];
         }
     }
