@@ -518,6 +518,9 @@ def main():
     probe_tf, probe_ms = g6.g6x_fp32_probe(10000)
     probe64_tf, probe64_ms = g6.g6x_fp64_probe(400)
 
+    # the legs below take the built-in launch choice for their own precision
+    if args.variant >= 0 or args.grid > 0:
+        g6.g6x_set_variant(CID, -1, 0)
     # all-FP64 kernel on a subset of the block (its rate is flat in m)
     m64 = min(args.fp64_m, m)
     d_i64 = to_dev(irec[:m64])

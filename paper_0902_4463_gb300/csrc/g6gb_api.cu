@@ -1608,7 +1608,10 @@ extern "C" int g6x_autotune(int cid, int nj, int m_max, const char *path)
             if (occ < 1)
                 continue;
             int last_grid = -1;
-            for (int gm = 1; gm <= 2 && e == cudaSuccess; ++gm) {
+            for (int gm = 1; gm <= 8 && e == cudaSuccess; gm *= 2) {
+                // more than two waves only for the widest tiles on long work lines
+                if (gm > 2 && (vi.ti * vi.nper < 256 || m < 16384))
+                    break;
                 ForceConfig cfg = g6::choose_config(c->prec, m, nj_pad, 0, c->sm_count, v,
                                                     c->sm_count * occ * gm, true);
                 if (cfg.grid == last_grid)

@@ -1544,7 +1544,7 @@ int heuristic_variant(int prec, int ni, int nj_pad, int list, bool allow_ws, int
         long long min_units;
     };
     static constexpr Shape shapes[] = {
-        {0, 256, INT_MAX, 16384},  // 128 threads, two i each, whole j-tiles
+        {9, 256, INT_MAX, 16384},  // 128 threads, two i each, whole j-tiles, 4 CTAs per SM
         {16, 128, 2048, 4096},     // 64 x 4 threads, two i each
         {15, 64, 256, 2048},       // 32 x 8 threads, two i each
         {14, 32, 128, 2048},       // 16 x 16 threads, two i each
@@ -1557,7 +1557,18 @@ int heuristic_variant(int prec, int ni, int nj_pad, int list, bool allow_ws, int
                || (long long)((ni + shapes[k].itile - 1) / shapes[k].itile) * jtl
                       < shapes[k].min_units))
         ++k;
-    *gmul = shapes[k].v == 0 ? 2 : 1;
+    *gmul = 1;
+    if (shapes[k].v == 9) {
+        // Several waves of CTAs per SM: the warp schedulers favour the
+        // oldest CTAs, so equal shares of the work line finish at different
+        // times, and with one wave the SMs run their last stretch with few
+        // warps.  Later waves fill those slots.  More CTAs also mean more
+        // partial records and i-tile loads, so the count follows the length
+        // of the work line (measured at N = 2^20: 1, 2, 2, 4, 8 waves best
+        // for m = 4096, 16384, 65536, 262144, 2^20).
+        const long long units = (long long)((ni + 255) / 256) * jtl;
+        *gmul = units < (1LL << 18) ? 1 : units < (1LL << 21) ? 2 : units < (1LL << 23) ? 4 : 8;
+    }
     return shapes[k].v;
 }
 

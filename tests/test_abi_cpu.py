@@ -197,6 +197,11 @@ def test_launch_plan_heuristic_without_a_gpu(lib):
     assert shape(big, 2048) == (64, 4, 2)
     assert shape(big, 4096) == (128, 1, 2)
     assert shape(big, big) == (128, 1, 2)
+    # the widest tiles run 4 CTAs per SM (the occupancy query needs a GPU:
+    # one without), in more waves on longer work lines
+    for ni, waves in ((4096, 1), (16384, 2), (65536, 2), (262144, 4), (big, 8)):
+        p = g6gb.g6x_plan_launch(ds, big, ni)
+        assert p["variant"] == 9 and p["grid"] in (152 * waves, 152 * 4 * waves), (ni, p)
     assert shape(small, 256) == (16, 16, 1)
     assert shape(small, 1024) == (32, 8, 2)
     assert shape(small, 4096) == (64, 4, 2)
@@ -251,7 +256,7 @@ def test_tuning_table_is_consulted_and_loads_all_or_nothing(lib, tmp_path):
         g6gb.g6x_load_tuning(str(tmp_path / "missing.txt"))
     g6gb.g6x_clear_tuning()
     assert g6gb.g6x_plan_launch(ds, big, 16)["variant"] == ws16
-    assert g6gb.g6x_plan_launch(ds, big, 4096)["variant"] == 0
+    assert g6gb.g6x_plan_launch(ds, big, 4096)["variant"] == 9
 
 
 def test_driver_setters_refuse_bad_arguments_without_a_gpu(lib):

@@ -67,7 +67,7 @@ def test_full_size_sampled_in_bench_configuration(open_ctx, orc):
     idx = np.arange(n)
     acc, jerk, pot, nnb = sweep(cid, n, st["x0"], st["v0"], idx, eps2, t_blk)
     cfg = g6.g6x_last_config(cid)
-    assert cfg["variant"] == 0 and cfg["grid"] % 152 == 0
+    assert cfg["variant"] == 9 and cfg["grid"] == 152 * 4 * 8
     sample = ics.permutation(n, 99)[:256]
     xp, vp = orc.predict(st["x0"], st["v0"], st["a0"], st["j0"], st["tj"], t_blk)
     oa, oj, op, onn, onr = orc.force(st["x0"][sample], st["v0"][sample], sample, xp, vp,
