@@ -41,7 +41,7 @@ T_BLK = 2.0 ** -10
 SEED = 3
 CID = 0
 KERNEL_SRC = os.path.join(ROOT, "paper_0902_4463_gb300", "csrc", "g6gb_kernels.cu")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_force_ds_plummer_n262144.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_force_ds_plummer_n262144_and_n1048576.md")
 
 
 def parse():
