@@ -290,6 +290,8 @@ __device__ __forceinline__ float2 ds_sep2(float2 h, float2 l, float2 nh, float2 
 //   dx   = (xj_hi - xi_hi) + (xj_lo - xi_lo)                       Eq. 3
 //   r2   = |dx|^2 + eps2, or +inf for the i-particle's own j (index match)
 //   1/r  = rsqrt(r2), 1/r^2 = rcp(r2)    (+inf -> 0: the pair adds nothing)
+//          (the reciprocal rounds once where 1/r * 1/r compounds the error
+//          of the approximate rsqrt, and takes one FMA-pipe operation off)
 //   acc  += m r^-3 dx
 //   jerk += m r^-3 (dv - 3 (dx.dv) r^-2 dx)
 //   pot  += m r^-1                      (negated in K3)
@@ -323,6 +325,12 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     constexpr int ITILE = TI * NI;
     constexpr int PPT = JT / 2 / TJ;                  // j-pairs per thread per tile
     constexpr int FLUSH = (256 + PPT - 1) / PPT;      // tiles between flushes (>= 512 j)
+    // The split-j shapes (small m) also note which chunk of CHP j-pairs
+    // lowered a tile's minimum, so the rescan at the end of a segment reads
+    // one chunk of the winning tile, not the thread's whole share of it.
+    constexpr bool NNC = TJ > 1;
+    constexpr int CHP = PPT < 4 ? PPT : 4;
+    static_assert(PPT % CHP == 0, "whole chunks per tile");
     constexpr unsigned TILE_BYTES = JW * JT * sizeof(float);
     // FP: a stage holds one tile of the raw j-store arrays (RAW_* offsets),
     // predicted by the CTA into pbuf before the pair loop
@@ -492,6 +500,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     float2 ta[NI][7];
     float tmin[NI], nnr[NI];
     int nnt[NI], nbn[NI];
+    int tchk[NI], nnc[NI];              // NNC: chunk of the tile / of tile nnt
     int cur_t = -1;
     int since_flush = 0;
 
@@ -597,6 +606,8 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
             nnr[k] = INF;
             nnt[k] = -1;
             nbn[k] = 0;
+            tchk[k] = 0;
+            nnc[k] = 0;
         }
         since_flush = 0;
         if constexpr (TJ > 1)
@@ -611,8 +622,9 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         if (!(nnr[k] < INF) || nnt[k] < 0)
             return -1;
         const float *T = a.pt + (size_t)nnt[k] * JW * JT;
-        constexpr int CH = 4;                       // j-pairs per chunk
-        for (int kk0 = 0; kk0 < PPT; kk0 += CH) {
+        constexpr int CH = CHP;                     // j-pairs per chunk
+        const int kb = NNC ? nnc[k] * CH : 0, ke = NNC ? kb + CH : PPT;
+        for (int kk0 = kb; kk0 < ke; kk0 += CH) {
             float key[2 * CH];
 #pragma unroll
             for (int u = 0; u < CH; ++u) {
@@ -853,8 +865,9 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         const float2 *VY = reinterpret_cast<const float2 *>(S + W_VY * JT);
         const float2 *VZ = reinterpret_cast<const float2 *>(S + W_VZ * JT);
         const int2 *ID = reinterpret_cast<const int2 *>(S + W_ID * JT);
-#pragma unroll UNR
-        for (int kk = 0; kk < PPT; ++kk) {
+        // j-pair kk of the thread's share against its NI i-particles; mins[k]
+        // receives the smaller key
+        auto jpair = [&](int kk, float (&mins)[NI]) {
             const int jp = tj + kk * TJ;
             const float2 xh = XH[jp], yh = YH[jp], zh = ZH[jp], mj = MM[jp];
             const float2 xl = XL[jp], yl = YL[jp], zl = ZL[jp];
@@ -898,7 +911,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                 ta[k][3] = __ffma2_rn(mr3, __ffma2_rn(sc, dx, ux), ta[k][3]);
                 ta[k][4] = __ffma2_rn(mr3, __ffma2_rn(sc, dy, uy), ta[k][4]);
                 ta[k][5] = __ffma2_rn(mr3, __ffma2_rn(sc, dz, uz), ta[k][5]);
-                tmin[k] = fminf(tmin[k], fminf(key.x, key.y));
+                mins[k] = fminf(mins[k], fminf(key.x, key.y));
                 if constexpr (LIST) {
                     const int il = k * TI + ti;
                     const int j0 = jt * JT + 2 * jp;
@@ -915,6 +928,27 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                     }
                 }
             }
+        };
+        if constexpr (NNC) {
+            for (int ch = 0; ch < PPT / CHP; ++ch) {
+                float cm[NI];
+#pragma unroll
+                for (int k = 0; k < NI; ++k)
+                    cm[k] = INF;
+#pragma unroll UNR
+                for (int u = 0; u < CHP; ++u)
+                    jpair(ch * CHP + u, cm);
+#pragma unroll
+                for (int k = 0; k < NI; ++k)
+                    if (cm[k] < tmin[k]) {      // the first chunk that reaches the minimum
+                        tmin[k] = cm[k];
+                        tchk[k] = ch;
+                    }
+            }
+        } else {
+#pragma unroll UNR
+            for (int kk = 0; kk < PPT; ++kk)
+                jpair(kk, tmin);
         }
     };
 
@@ -951,6 +985,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                 if (tmin[k] < nnr[k]) {
                     nnr[k] = tmin[k];
                     nnt[k] = jt;
+                    nnc[k] = tchk[k];
                 }
                 tmin[k] = INF;
             }
@@ -1546,8 +1581,8 @@ int heuristic_variant(int prec, int ni, int nj_pad, int list, bool allow_ws, int
     static constexpr Shape shapes[] = {
         {9, 256, INT_MAX, 16384},  // 128 threads, two i each, whole j-tiles, 4 CTAs per SM
         {16, 128, 2048, 4096},     // 64 x 4 threads, two i each
-        {15, 64, 256, 2048},       // 32 x 8 threads, two i each
-        {14, 32, 128, 2048},       // 16 x 16 threads, two i each
+        {15, 64, 128, 2048},       // 32 x 8 threads, two i each
+        {14, 32, 64, 2048},        // 16 x 16 threads, two i each
         {4, 16, 32, 0},            // 16 x 16 threads, one i each
     };
     const long long jtl = nj_pad / JT;

@@ -192,8 +192,8 @@ def test_launch_plan_heuristic_without_a_gpu(lib):
         assert g6gb.g6x_plan_launch(ds, nj, 16, True)["variant"] in (5, 6)   # lists: no
     assert shape(big, 17) == (32, 8, 1) and shape(big, 64) == (64, 4, 1)
     assert shape(big, 16) == (16, 16, 1)
-    assert shape(big, 128) == (16, 16, 2)
-    assert shape(big, 256) == (32, 8, 2)
+    assert shape(big, 128) == (32, 8, 2)
+    assert shape(big, 256) == (64, 4, 2)
     assert shape(big, 2048) == (64, 4, 2)
     assert shape(big, 4096) == (128, 1, 2)
     assert shape(big, big) == (128, 1, 2)
