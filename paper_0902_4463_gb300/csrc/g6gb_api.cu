@@ -766,7 +766,7 @@ int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_
         e = g6::launch_force_ws(cfg, d_irec, ni, eps2, nj, c.d_part, c.d_tcnt, d_out, c.js.idx,
                                 c.d_err, fpa, c.stream, pdl);
         c.launches += 1;
-    } else if (!cfg.list && cfg.prec == G6X_PREC_DS && seg_per_tile <= 4) {
+    } else if (!cfg.list && cfg.prec == G6X_PREC_DS && seg_per_tile <= g6::FUSED_MAX_SEGS) {
         // one launch: the last CTA of each i-tile reduces it (K3 fused into
         // K2) when every tile has only a few partials (large blocks); with
         // many partials per tile that serial tail costs more than the

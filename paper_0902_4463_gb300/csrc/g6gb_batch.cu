@@ -6,7 +6,9 @@
 // block) and computes all of them in one launch sequence -- one copy of the
 // step's geometry tables to the device, the j-store update fused into the
 // per-cluster prediction (Eq. 1, Eq. 2), the force kernels, and the
-// reductions.  The kernels read the geometry from device memory, so the
+// reductions (an i-tile whose work spans a few CTAs is reduced by the last of
+// them inside the force launch, the others by the reduction kernel, which
+// skips the former).  The kernels read the geometry from device memory, so the
 // sequence is captured once in a CUDA graph and replayed every step (only
 // the size of the table copy is updated before a replay).  For comparison
 // the same kernels can run as plain launches or as one launch sequence per
@@ -52,6 +54,7 @@ namespace {
 struct WorkClass {
     int variant = -1, grid_mul = 1, grid = 0, itile = 0, gt_cap = 0, k3_blocks = 1;
     void *d_part = nullptr;
+    unsigned *d_cnt = nullptr;     // per entry of the line: arrivals (inside d_part's block)
 };
 
 constexpr size_t HDR_WORDS = 4;     // per work line: W, entries, first entry, unused
@@ -201,10 +204,19 @@ int setup_class(g6x_batch *b, int c, int v, int gm)
     for (int k = 0; k < b->ncl; ++k)
         w.gt_cap += (b->nj[k] + w.itile - 1) / w.itile;
     w.k3_blocks = std::max(1, std::min(b->sms * 16, (w.gt_cap * w.itile * 32 + 255) / 256));
-    w.d_part = g6::dev_alloc_hooked((size_t)(w.grid + w.gt_cap) * w.itile * g6::PARTIAL_BYTES);
+    // the partial records, then one arrival counter per entry (zero between
+    // launches: the CTA that completes a count resets it)
+    const size_t pbytes = (size_t)(w.grid + w.gt_cap) * w.itile * g6::PARTIAL_BYTES;
+    w.d_part = g6::dev_alloc_hooked(pbytes + (size_t)w.gt_cap * sizeof(unsigned));
     if (!w.d_part) {
         free_class(w);
         return G6_ENOMEM;
+    }
+    w.d_cnt = reinterpret_cast<unsigned *>(static_cast<char *>(w.d_part) + pbytes);
+    if (cudaMemset(w.d_cnt, 0, (size_t)w.gt_cap * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        free_class(w);
+        return G6_EIO;
     }
     return 0;
 }
@@ -366,10 +378,10 @@ cudaError_t enqueue_class(g6x_batch *b, int c, cudaStream_t s)
     const WorkClass &w = b->wc[c];
     const g6::BatchTables bt = line_tables(b, c);
     cudaError_t e = g6::launch_force_batch(w.variant, w.grid, b->pred, b->d_irec, w.d_part,
-                                           b->d_err, bt, s);
+                                           b->d_err, bt, s, w.d_cnt, b->d_out, b->js.idx);
     if (e == cudaSuccess)
         e = g6::launch_reduce_batch(w.variant, w.grid, w.d_part, b->js.idx, b->d_out, bt,
-                                    w.k3_blocks, s);
+                                    w.k3_blocks, s, true);
     return e;
 }
 
@@ -539,11 +551,11 @@ int run_per_cluster(g6x_batch *b, const int ni[])
         const int grid = (int)std::min<long long>(w.grid, (long long)nit * b->ntile[k]);
         if (e == cudaSuccess)
             e = g6::launch_force_batch(w.variant, grid, b->pred, b->d_irec, w.d_part, b->d_err,
-                                       bt, b->stream);
+                                       bt, b->stream, w.d_cnt, b->d_out, b->js.idx);
         if (e == cudaSuccess)
             e = g6::launch_reduce_batch(w.variant, grid, w.d_part, b->js.idx, b->d_out, bt,
                                         std::max(1, (nit * w.itile * 32 + 255) / 256),
-                                        b->stream);
+                                        b->stream, true);
         b->launches += 3;
     }
     return cuda_code(e);
@@ -830,6 +842,12 @@ int g6x_batch_calc(g6x_batch *b, const double t_blk[], const double eps2[], cons
     if (*(volatile int *)b->h_err) {
         const int code = *b->h_err;
         *(volatile int *)b->h_err = 0;
+        // a launch that gave up may have left arrival counts behind
+        for (int c = 0; c < b->nclass; ++c)
+            if (b->wc[c].d_cnt
+                && cudaMemset(b->wc[c].d_cnt, 0, (size_t)b->wc[c].gt_cap * sizeof(unsigned))
+                       != cudaSuccess)
+                cudaGetLastError();
         return code < 0 ? code : G6_EIO;
     }
     return 0;

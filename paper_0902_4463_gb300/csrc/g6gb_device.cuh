@@ -174,6 +174,19 @@ __device__ __forceinline__ long long work_owner(long long p, long long W, long l
     return ((p + 1) * G - 1) / W;
 }
 
+// Whether the i-tile owned by CTAs clo .. chi is reduced by the last of them
+// inside the force launch: few of them, and every one with work (a line
+// shorter than the grid leaves CTAs without work, which never arrive).
+__device__ __forceinline__ bool fused_span(long long clo, long long chi, long long W, long long G)
+{
+    if (chi - clo + 1 > FUSED_MAX_SEGS)
+        return false;
+    for (long long c = clo; c <= chi; ++c)
+        if (work_begin(c, W, G) == work_begin(c + 1, W, G))
+            return false;
+    return true;
+}
+
 // Far-away massless stand-in for padding and empty j-slots: every pair term
 // it produces is exactly zero (r^2 overflows to +inf, rsqrt(+inf) = 0).
 constexpr double FAR = 1e30;

@@ -16,6 +16,11 @@ namespace g6 {
 // each thread block stages j-particles in shared memory and loops over them).
 constexpr int JT = 256;
 
+// An i-tile whose work is spread over at most this many CTAs is reduced by
+// the last of them inside the force launch; more partials go to K3, whose
+// many CTAs beat the serial tail of one.
+constexpr int FUSED_MAX_SEGS = 4;
+
 // One partial result of a (work segment, i-particle) pair: sums over the
 // j-range the segment covers (Sect. 2.3: partial forces of the P blocks are
 // reduced on the GPU before the copy back).
@@ -177,11 +182,18 @@ int batch_variant_occupancy(int v);
 cudaError_t launch_predict_batch(int kind, JStore js, Pred p, BatchPredTables bp,
                                  const g6x_jrec *rec, const int *toff, int tile0, int ntiles,
                                  int sm_count, cudaStream_t s);
+// tcnt (one zeroed counter per entry of the line, left zeroed): the force
+// kernel reduces the entries whose work spans at most FUSED_MAX_SEGS CTAs,
+// all with work,
+// itself (into out, nearest neighbours mapped through jidx), and the
+// reduction launched with fused = true skips them.
 cudaError_t launch_force_batch(int v, int grid, const Pred &p, const g6x_irec *d_irec,
-                               void *part, int *d_err, const BatchTables &bt, cudaStream_t s);
+                               void *part, int *d_err, const BatchTables &bt, cudaStream_t s,
+                               unsigned *tcnt = nullptr, g6x_out *out = nullptr,
+                               const int *jidx = nullptr);
 cudaError_t launch_reduce_batch(int v, int grid, const void *part, const int *jidx,
                                 g6x_out *d_out, const BatchTables &bt, int blocks,
-                                cudaStream_t s);
+                                cudaStream_t s, bool fused = false);
 
 // The warp-specialised small-block variants (g6gb_small.cu) follow the
 // others in one numbering: variant_count() covers both tables.

@@ -755,10 +755,15 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     // for the next launch.  (A launch that gives up early leaves counts
     // behind; the host clears all counters after any reported error.)
     auto tile_done = [&](int t) {
-        __threadfence();
-        __syncthreads();
         const long long clo = work_owner(g_start(t), W, G);
         const long long chi = work_owner(g_start(t + 1) - 1, W, G);
+        // a batch line mixes entries of every span: only those with a few
+        // partials are reduced here, the others by K3 (the same test there)
+        if constexpr (BATCH)
+            if (!fused_span(clo, chi, W, G))
+                return;
+        __threadfence();
+        __syncthreads();
         if (tid == 0) {
             const unsigned need = (unsigned)(chi - clo + 1);
             const unsigned prev = atomicAdd(&a.tcnt[t], 1u);
@@ -1164,6 +1169,7 @@ struct ReduceArgs {
     long long W;
     int J, G, ni, itile, list;
     int maxnb, nbseg;                 // list length kept; entries per list partial
+    int fused;                        // batch: entries with few partials were reduced by K2
 };
 
 
@@ -1282,6 +1288,8 @@ __global__ void __launch_bounds__(256) k_reduce_batch(const ReduceArgs a, BatchT
             continue;                                  // uniform within the warp
         const long long clo = work_owner(gt[g].start, W, a.G);
         const long long chi = work_owner(gt[g + 1].start - 1, W, a.G);
+        if (a.fused && fused_span(clo, chi, W, a.G))
+            continue;                                  // reduced by the force kernel
         PartialSum<PT> acc;
         acc.init();
 #pragma unroll 4
@@ -1864,6 +1872,7 @@ cudaError_t launch_reduce(const ForceConfig &cfg, const void *part,
     a.list = cfg.list;
     a.maxnb = lists ? lists->maxnb : 0;
     a.nbseg = lists ? lists->nbseg : 0;
+    a.fused = 0;
     if (cfg.list && !lists)
         return cudaErrorInvalidValue;
     // many partials per i-particle (small blocks spread over many CTAs):
@@ -1941,7 +1950,8 @@ cudaError_t launch_predict_batch(int kind, JStore js, Pred p, BatchPredTables bp
 }
 
 cudaError_t launch_force_batch(int v, int grid, const Pred &p, const g6x_irec *d_irec,
-                               void *part, int *d_err, const BatchTables &bt, cudaStream_t s)
+                               void *part, int *d_err, const BatchTables &bt, cudaStream_t s,
+                               unsigned *tcnt, g6x_out *out, const int *jidx)
 {
     if (v < 0 || v >= kNumBatchVariants || grid < 1)
         return cudaErrorInvalidValue;
@@ -1955,6 +1965,12 @@ cudaError_t launch_force_batch(int v, int grid, const Pred &p, const g6x_irec *d
     a.err = d_err;
     a.bt = bt;
     a.wait_ns = g_wait_ns;
+    if (tcnt) {
+        a.fused = 1;
+        a.tcnt = tcnt;
+        a.out = out;
+        a.jidx = jidx;
+    }
     const Variant &bv = kBatchVariants[v];
     bv.fn<<<grid, bv.threads, bv.smem, s>>>(a);
     return cudaGetLastError();
@@ -1974,7 +1990,7 @@ cudaError_t launch_wait_probe(int *d_err, cudaStream_t s)
 
 cudaError_t launch_reduce_batch(int v, int grid, const void *part, const int *jidx,
                                 g6x_out *d_out, const BatchTables &bt, int blocks,
-                                cudaStream_t s)
+                                cudaStream_t s, bool fused)
 {
     if (v < 0 || v >= kNumBatchVariants)
         return cudaErrorInvalidValue;
@@ -1984,6 +2000,7 @@ cudaError_t launch_reduce_batch(int v, int grid, const void *part, const int *ji
     a.out = d_out;
     a.G = grid;
     a.itile = kBatchVariants[v].info.ti * kBatchVariants[v].info.nper;
+    a.fused = fused ? 1 : 0;
     pin_carveout(k_reduce_batch<PartialDS>);
     k_reduce_batch<PartialDS><<<blocks, 256, 0, s>>>(a, bt);
     return cudaGetLastError();
