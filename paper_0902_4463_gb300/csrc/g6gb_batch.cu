@@ -50,6 +50,13 @@ using g6::JT;
 
 namespace {
 
+// A staged j-record whose default construction leaves it uninitialised: a
+// block's records are reserved in one resize and every field is written
+// right after, so the reservation costs no zeroing.
+struct StagedRec : g6x_jrec {
+    StagedRec() {}
+};
+
 // One work class of a schedule: its force kernel, grid and partial sums.
 struct WorkClass {
     int variant = -1, grid_mul = 1, grid = 0, itile = 0, gt_cap = 0, k3_blocks = 1;
@@ -91,7 +98,7 @@ struct g6x_batch {
     g6x_out *h_out = nullptr, *d_out = nullptr;
     // j staging: per cluster, at most one record per slot; sorted by tile
     // into the mapped buffer at launch
-    std::vector<std::vector<g6x_jrec>> stage;
+    std::vector<std::vector<StagedRec>> stage;
     std::vector<int> slot_of;
     std::vector<int> base;
     g6x_jrec *h_jsort = nullptr, *d_jsort = nullptr;
@@ -319,14 +326,16 @@ void stage_sorted(g6x_batch *b)
     g6::parallel_run(b->ncl, [b](int k) {
         const int t0 = b->jtile[k], nt = b->ntile[k];
         int *off = b->h_toff + t0;
-        std::vector<g6x_jrec> &st = b->stage[k];
+        std::vector<StagedRec> &st = b->stage[k];
         if (st.empty()) {
             for (int t = 0; t < nt; ++t)
                 off[t] = b->base[k];
             return;
         }
-        // counting sort by tile within the cluster's tile range
-        std::vector<int> cnt(nt + 1, 0);
+        // counting sort by tile within the cluster's tile range (one count
+        // buffer per host thread, kept between calls)
+        thread_local std::vector<int> cnt;
+        cnt.assign(nt + 1, 0);
         for (const g6x_jrec &r : st)
             ++cnt[r.address / JT - t0 + 1];
         int acc = b->base[k];
@@ -751,7 +760,7 @@ int g6x_batch_set_j(g6x_batch *b, int cl, int address, int index, double tj, dou
         || !j6 || !a2 || !v || !x)
         return G6_EINVAL;
     const int slot = b->jtile[cl] * JT + address;
-    std::vector<g6x_jrec> &st = b->stage[cl];
+    std::vector<StagedRec> &st = b->stage[cl];
     int s = b->slot_of[slot];
     if (s < 0) {
         try {
@@ -1099,7 +1108,7 @@ void hb_unstage(g6hb_sim &s)
 {
     g6x_batch *b = s.b;
     for (int k = 0; k < s.ncl; ++k) {
-        std::vector<g6x_jrec> &st = b->stage[k];
+        std::vector<StagedRec> &st = b->stage[k];
         for (size_t i = s.sbase[k]; i < st.size(); ++i) {
             const int slot = b->jtile[k] * JT + s.act[k][i - s.sbase[k]];
             if (b->slot_of[slot] == (int)i)

@@ -17,8 +17,13 @@
 namespace g6 {
 
 // Persistent host worker pool: run(n, f) calls f(0..n-1) on the workers and
-// the calling thread and returns when all calls have finished.  Workers spin
-// briefly for the next job, then sleep on a condition variable.
+// the calling thread and returns when all calls have finished.  A job is
+// published by writing it and then advancing the generation counter
+// (release); a worker that sees the new generation (acquire) reads the job
+// without a lock.  Workers wait for the next job by spinning on the counter
+// for a short while (a block step posts several jobs tens of microseconds
+// apart), then by yielding, then sleep on a condition variable; the caller
+// wakes sleepers only when there are any.
 class HostPool {
 public:
     explicit HostPool(int threads)
@@ -28,10 +33,10 @@ public:
     }
     ~HostPool()
     {
+        quit_.store(true, std::memory_order_seq_cst);
+        gen_.fetch_add(1, std::memory_order_seq_cst);
         {
             std::lock_guard<std::mutex> lk(mu_);
-            quit_ = true;
-            gen_.fetch_add(1);
         }
         cv_.notify_all();
         for (std::thread &t : th_)
@@ -45,57 +50,77 @@ public:
                 f(i);
             return;
         }
-        {
+        // every worker has finished the previous job (busy_ reached 0), so
+        // none still reads job_ or count_
+        job_ = &f;
+        count_ = n;
+        grab_ = std::max(1, n / (8 * size()));     // indices taken per claim
+        next_.store(0, std::memory_order_relaxed);
+        busy_.store((int)th_.size(), std::memory_order_relaxed);
+        gen_.fetch_add(1, std::memory_order_seq_cst);
+        if (sleepers_.load(std::memory_order_seq_cst) > 0) {
             std::lock_guard<std::mutex> lk(mu_);
-            job_ = &f;
-            count_ = n;
-            next_.store(0);
-            busy_.store((int)th_.size());
-            gen_.fetch_add(1);
+            cv_.notify_all();
         }
-        cv_.notify_all();
-        for (int i; (i = next_.fetch_add(1)) < n;)
-            f(i);
-        while (busy_.load() != 0)
-            std::this_thread::yield();
+        take(f, n, grab_);
+        for (int spins = 0; busy_.load(std::memory_order_acquire) != 0;)
+            if (++spins > SPIN_TIGHT)
+                std::this_thread::yield();
     }
 
 private:
+    static constexpr int SPIN_TIGHT = 20000;   // polls before yielding (tens of us)
+    static constexpr int SPIN_YIELD = 2000;    // yields before sleeping
+
+    // claim indices `grab` at a time until none are left
+    void take(const std::function<void(int)> &f, int n, int grab)
+    {
+        for (int i; (i = next_.fetch_add(grab, std::memory_order_relaxed)) < n;)
+            for (int k = i, ke = std::min(n, i + grab); k < ke; ++k)
+                f(k);
+    }
+
     // Workers are started before any run(), when the generation is 0.
     void worker()
     {
         unsigned seen = 0;
         for (;;) {
+            unsigned g;
             int spins = 0;
-            while (gen_.load() == seen && ++spins < 4096)
-                std::this_thread::yield();
-            if (gen_.load() == seen) {
-                std::unique_lock<std::mutex> lk(mu_);
-                cv_.wait(lk, [&] { return gen_.load() != seen; });
+            while ((g = gen_.load(std::memory_order_acquire)) == seen) {
+                ++spins;
+                if (spins <= SPIN_TIGHT)
+                    continue;
+                if (spins <= SPIN_TIGHT + SPIN_YIELD) {
+                    std::this_thread::yield();
+                    continue;
+                }
+                // sleep until the generation moves (the caller notifies when
+                // it sees a sleeper; the predicate is checked after the
+                // sleeper count is raised, so no wake-up is lost)
+                sleepers_.fetch_add(1, std::memory_order_seq_cst);
+                {
+                    std::unique_lock<std::mutex> lk(mu_);
+                    cv_.wait(lk, [&] { return gen_.load(std::memory_order_seq_cst) != seen; });
+                }
+                sleepers_.fetch_sub(1, std::memory_order_seq_cst);
+                spins = 0;
             }
-            seen = gen_.load();
-            const std::function<void(int)> *f;
-            int n;
-            {
-                std::lock_guard<std::mutex> lk(mu_);
-                if (quit_)
-                    return;
-                f = job_;
-                n = count_;
-            }
-            for (int i; (i = next_.fetch_add(1)) < n;)
-                (*f)(i);
-            busy_.fetch_sub(1);
+            seen = g;
+            if (quit_.load(std::memory_order_acquire))
+                return;
+            take(*job_, count_, grab_);
+            busy_.fetch_sub(1, std::memory_order_release);
         }
     }
     std::vector<std::thread> th_;
     std::mutex mu_;
     std::condition_variable cv_;
     std::atomic<unsigned> gen_{0};
-    std::atomic<int> next_{0}, busy_{0};
+    std::atomic<int> next_{0}, busy_{0}, sleepers_{0};
+    std::atomic<bool> quit_{false};
     const std::function<void(int)> *job_ = nullptr;
-    int count_ = 0;
-    bool quit_ = false;
+    int count_ = 0, grab_ = 1;
 };
 
 inline int host_threads()
