@@ -17,9 +17,10 @@
 //     stages with bulk asynchronous copies; the compute warps predict each
 //     tile into one of two predicted-tile buffers (the K1 arithmetic, so the
 //     tiles are bit-identical to K1's), one tile ahead of the pair loop that
-//     reads the other buffer.  Stages and buffers are handed over with
-//     mbarriers, so no CTA-wide barrier separates the tiles and the copies of
-//     later tiles stay in flight while the compute warps work;
+//     reads the other buffer.  The raw stages pass between the producer and
+//     the compute warps on mbarriers, so the copies of later tiles stay in
+//     flight while the compute warps work; the compute warps alone meet at
+//     one named barrier per tile, which releases both predicted buffers;
 //   * the staged j-records of the CTA's own tiles (the j-store update of
 //     Sect. 2.1) are stored by the producer warp before its first copy;
 //   * the partial sums of the CTAs are reduced inside the launch in two
@@ -29,8 +30,11 @@
 //     order is fixed by CTA and group index, so results do not depend on which
 //     CTA finishes last.
 //
-// The pair arithmetic, the compensated accumulation and the lazy nearest
-// neighbour are those of K2 (k_force_ds).  Every wait is bounded; a wait that
+// The pair arithmetic and the compensated accumulation are those of K2
+// (k_force_ds); the nearest neighbour is found from the tile still in
+// shared memory whenever a tile lowers a thread's smallest key, instead of
+// K2's rescan of the winning tile from global memory at the end.  Every wait
+// is bounded; a wait that
 // runs out records G6_ETIMEDOUT in the error word and makes the other warps
 // give up at their next wait, and the producer warp keeps the CTA alive until
 // every copy it issued has landed.
