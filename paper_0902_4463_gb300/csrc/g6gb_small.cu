@@ -34,10 +34,9 @@
 // (k_force_ds); the nearest neighbour is found from the tile still in
 // shared memory whenever a tile lowers a thread's smallest key, instead of
 // K2's rescan of the winning tile from global memory at the end.  Every wait
-// is bounded; a wait that
-// runs out records G6_ETIMEDOUT in the error word and makes the other warps
-// give up at their next wait, and the producer warp keeps the CTA alive until
-// every copy it issued has landed.
+// is bounded; a wait that runs out records G6_ETIMEDOUT in the error word and
+// makes the other warps give up at their next wait, and the producer warp
+// keeps the CTA alive until every copy it issued has landed.
 #include "g6gb_device.cuh"
 
 #include <climits>
