@@ -1539,15 +1539,17 @@ void tune_clear()
 namespace {
 
 // Blocks the built-in choice gives the small-block kernel.  Measured on
-// GB300 (device time of a block step): faster than the separate predictor
-// and the split-j shapes for m <= 16 at every N (N = 32768: 19-21 against
-// 31 us), up to m = 64 once the j-set has 512 tiles or more (N = 2^20,
-// m = 64: 154 against 173 us; N = 131072: a tie), slower above m = 64 and,
-// at m = 64, for small j-sets, where each CTA holds one j-tile and nothing
-// overlaps (N = 32768: 39 against 37 us).
-constexpr int WS_DEFAULT_MAX_NI = 64;
+// GB300 as the host wall time of a block step through the GRAPE calls
+// (the separate predictor and split-j shapes overlap their three launches):
+// faster for m <= 16 at every N (N = 131072, m = 16: 36 against 42 us);
+// for m <= 32 once the j-set has 512 tiles (N = 32768: a tie; N = 2^20:
+// 92 against 122 us); for m <= 64 only from about 1500 tiles on (N =
+// 262144: 72 against 67 us; N = 2^20: 142 against 173 us); never above.
 constexpr int WS_ANY_N_MAX_NI = 16;
-constexpr long long WS_MIN_JTILES = 512;
+constexpr int WS_MID_MAX_NI = 32;
+constexpr long long WS_MID_MIN_JTILES = 512;
+constexpr int WS_DEFAULT_MAX_NI = 64;
+constexpr long long WS_MIN_JTILES = 2048;
 
 // The built-in launch choice for a block of ni against nj_pad j-particles
 // (no tuning table); *gmul receives the grid multiplier.
@@ -1563,7 +1565,9 @@ int heuristic_variant(int prec, int ni, int nj_pad, int list, bool allow_ws, int
     if (list)
         return ni <= 32 ? 6 : 5;
     if (allow_ws
-        && (ni <= WS_ANY_N_MAX_NI || (ni <= WS_DEFAULT_MAX_NI && nj_pad / JT >= WS_MIN_JTILES))) {
+        && (ni <= WS_ANY_N_MAX_NI
+            || (ni <= WS_MID_MAX_NI && nj_pad / JT >= WS_MID_MIN_JTILES)
+            || (ni <= WS_DEFAULT_MAX_NI && nj_pad / JT >= WS_MIN_JTILES))) {
         // the warp-specialised small-block kernel: the narrowest i-tile
         // (one i-particle per thread) that holds the whole block
         int best = -1, best_tile = INT_MAX;

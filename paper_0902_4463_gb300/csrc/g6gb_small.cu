@@ -126,6 +126,8 @@ __global__ void __launch_bounds__(TI * TJ + 32, MINB) k_force_ws(const ForceArgs
     constexpr int ITILE = TI * NI;
     constexpr int PPT = JT / 2 / TJ;                  // j-pairs per thread per tile
     constexpr int FLUSH = (256 + PPT - 1) / PPT;      // tiles between flushes (>= 512 j)
+    constexpr int CHP = PPT < 4 ? PPT : 4;            // j-pairs per neighbour-search chunk
+    static_assert(PPT % CHP == 0, "whole chunks per tile");
     constexpr int PT_WORDS = JW * JT;                 // one predicted tile
     static_assert(NT == JT, "one j-particle per compute thread when a tile is predicted");
     static_assert(JT % (2 * TJ) == 0, "j-tile must split into j-pairs evenly");
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(TI * TJ + 32, MINB) k_force_ws(const ForceArgs
     int iid[NI];
     float2 ta[NI][7];
     float tmin[NI], nnr[NI];
-    int nnj[NI];
+    int nnj[NI], tchk[NI];
     auto cslot = [&](int k, int q) -> float2 & { return comp[(k * 7 + q) * NT + tid]; };
 #pragma unroll
     for (int k = 0; k < NI; ++k) {
@@ -290,6 +292,7 @@ __global__ void __launch_bounds__(TI * TJ + 32, MINB) k_force_ws(const ForceArgs
         tmin[k] = INF;
         nnr[k] = INF;
         nnj[k] = -1;
+        tchk[k] = 0;
     }
 
     // Eq. 1 and Eq. 2 for tile q (raw stage q % SR) into predicted buffer
@@ -379,8 +382,9 @@ __global__ void __launch_bounds__(TI * TJ + 32, MINB) k_force_ws(const ForceArgs
         const float2 *VY = reinterpret_cast<const float2 *>(S + W_VY * JT);
         const float2 *VZ = reinterpret_cast<const float2 *>(S + W_VZ * JT);
         const int2 *ID = reinterpret_cast<const int2 *>(S + W_ID * JT);
-#pragma unroll UNR
-        for (int kk = 0; kk < PPT; ++kk) {
+        // j-pair kk of the thread's share against its NI i-particles; mins[k]
+        // receives the smaller key
+        auto jpair = [&](int kk, float (&mins)[NI]) {
             const int jp = tj + kk * TJ;
             const float2 xh = XH[jp], yh = YH[jp], zh = ZH[jp], mj = MM[jp];
             const float2 xl = XL[jp], yl = YL[jp], zl = ZL[jp];
@@ -417,8 +421,25 @@ __global__ void __launch_bounds__(TI * TJ + 32, MINB) k_force_ws(const ForceArgs
                 ta[k][3] = __ffma2_rn(mr3, __ffma2_rn(sc, dx, ux), ta[k][3]);
                 ta[k][4] = __ffma2_rn(mr3, __ffma2_rn(sc, dy, uy), ta[k][4]);
                 ta[k][5] = __ffma2_rn(mr3, __ffma2_rn(sc, dz, uz), ta[k][5]);
-                tmin[k] = fminf(tmin[k], fminf(key.x, key.y));
+                mins[k] = fminf(mins[k], fminf(key.x, key.y));
             }
+        };
+        // by chunks of CHP j-pairs, noting the first chunk that reaches the
+        // tile's minimum, so the neighbour search reads one chunk
+        for (int ch = 0; ch < PPT / CHP; ++ch) {
+            float cm[NI];
+#pragma unroll
+            for (int k = 0; k < NI; ++k)
+                cm[k] = INF;
+#pragma unroll UNR
+            for (int u = 0; u < CHP; ++u)
+                jpair(ch * CHP + u, cm);
+#pragma unroll
+            for (int k = 0; k < NI; ++k)
+                if (cm[k] < tmin[k]) {
+                    tmin[k] = cm[k];
+                    tchk[k] = ch;
+                }
         }
     };
 
@@ -426,8 +447,9 @@ __global__ void __launch_bounds__(TI * TJ + 32, MINB) k_force_ws(const ForceArgs
     // Tile q+1 is predicted while tile q's pairs run, into the other buffer;
     // one barrier per tile then releases both buffers.  Where a tile lowers
     // an i-particle's smallest key, the first j of the thread's share with
-    // that key is found at once from the tile still in shared memory (ties
-    // to the lower j-slot: tiles and shares are walked in ascending j).
+    // that key is found at once from the tile still in shared memory, in the
+    // chunk the pair loop noted (ties to the lower j-slot: tiles, chunks and
+    // shares are walked in ascending j).
     bool ok = ntile <= 0 || predict_into(0);
     cta_bar();
     int since_flush = 0;
@@ -457,7 +479,7 @@ __global__ void __launch_bounds__(TI * TJ + 32, MINB) k_force_ws(const ForceArgs
             for (int k = 0; k < NI; ++k) {
                 if (tmin[k] < nnr[k]) {
                     nnr[k] = tmin[k];
-                    for (int kk = 0; kk < PPT; ++kk) {
+                    for (int kk = tchk[k] * CHP; kk < (tchk[k] + 1) * CHP; ++kk) {
                         const float2 key = pair_key(S, tj + kk * TJ, k);
                         if (key.x == nnr[k] || key.y == nnr[k]) {
                             nnj[k] = (jb + q) * JT + 2 * (tj + kk * TJ) + (key.x == nnr[k] ? 0 : 1);

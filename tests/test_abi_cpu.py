@@ -182,11 +182,13 @@ def test_launch_plan_heuristic_without_a_gpu(lib):
         return g6gb.g6x_variant_info(g6gb.g6x_plan_launch(ds, nj, ni)["variant"])["ws"] == 1
 
     # blocks of up to 16 take the small-block kernel with the narrowest
-    # i-tile that holds them, blocks of up to 64 too from 512 j-tiles on;
-    # larger blocks the split-j and wide shapes
-    for nj in (1024, small, 131072, big):
+    # i-tile that holds them, blocks of up to 32 too from 512 j-tiles on,
+    # blocks of up to 64 from 2048 j-tiles on; larger blocks the split-j
+    # and wide shapes
+    for nj in (1024, small, 131072, 524288, big):
         assert all(ws(nj, ni) for ni in (1, 8, 9, 16))
-        assert all(ws(nj, ni) == (nj >= 131072) for ni in (17, 33, 64))
+        assert all(ws(nj, ni) == (nj >= 131072) for ni in (17, 32))
+        assert all(ws(nj, ni) == (nj >= 524288) for ni in (33, 64))
         assert not any(ws(nj, ni) for ni in (65, 128, 256, 4096))
         assert shape(nj, 1) == (8, 32, 1) and shape(nj, 8) == (8, 32, 1)
         assert g6gb.g6x_plan_launch(ds, nj, 16, True)["variant"] in (5, 6)   # lists: no
