@@ -961,12 +961,20 @@ struct g6hb_sim {
     double noise = 0;                        // relative force error for the time steps
     std::vector<int> n, off;                 // particles per cluster, offset into arrays
     std::vector<double> eps2;
-    std::vector<double> m, x, v, a, j, t, dt;
+    // One particle's state in one record: the host phases visit the active
+    // particles of many clusters in scattered order, and a record costs them
+    // three cache lines where separate arrays cost eight.
+    struct Part {
+        double x[3], v[3], a[3], j[3];       // at its time t
+        double xp[3], vp[3];                 // predicted to its block time
+        double t, dt;
+    };
+    std::vector<double> m;
+    std::vector<Part> ps;
     std::vector<std::map<double, std::vector<int>>> due;
     std::vector<std::vector<int>> act;
     std::vector<double> tblk;
     std::vector<int> ni, rc;
-    std::vector<double> xp, vp;               // predicted i (per particle slot)
     std::vector<int> hist;                    // recent ni patterns [HIST][ncl]
     int hist_n = 0, hist_pos = 0;
     // host work items: particles [i0, i1) of cluster k's active block
@@ -989,12 +997,13 @@ double nrm(const double *p) { return std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] 
 int hb_send(g6hb_sim &s, int k, int q)
 {
     const int p = s.off[k] + q;
+    const g6hb_sim::Part &P = s.ps[p];
     double a2[3], j6[3];
     for (int d = 0; d < 3; ++d) {
-        a2[d] = 0.5 * s.a[3 * p + d];
-        j6[d] = s.j[3 * p + d] / 6.0;
+        a2[d] = 0.5 * P.a[d];
+        j6[d] = P.j[d] / 6.0;
     }
-    return g6x_batch_set_j(s.b, k, q, q, s.t[p], s.m[p], j6, a2, &s.v[3 * p], &s.x[3 * p]);
+    return g6x_batch_set_j(s.b, k, q, q, P.t, s.m[p], j6, a2, P.v, P.x);
 }
 
 // Cluster k's next block: its earliest due time, if not past t_end.
@@ -1021,14 +1030,14 @@ void hb_predict(g6hb_sim &s, const g6hb_sim::Chunk &c)
     g6x_irec *ir = g6x_batch_irecs(s.b, k);
     for (int i = c.i0; i < c.i1; ++i) {
         const int q = s.act[k][i];
-        const int p = s.off[k] + q;
-        const double h = tb - s.t[p];
+        g6hb_sim::Part &P = s.ps[s.off[k] + q];
+        const double h = tb - P.t;
         for (int d = 0; d < 3; ++d) {
-            const double aa = s.a[3 * p + d], jj = s.j[3 * p + d];
-            s.xp[3 * p + d] = s.x[3 * p + d] + h * (s.v[3 * p + d] + h * (aa / 2.0 + h * jj / 6.0));
-            s.vp[3 * p + d] = s.v[3 * p + d] + h * (aa + h * jj / 2.0);
-            ir[i].x[d] = s.xp[3 * p + d];
-            ir[i].v[d] = s.vp[3 * p + d];
+            const double aa = P.a[d], jj = P.j[d];
+            P.xp[d] = P.x[d] + h * (P.v[d] + h * (aa / 2.0 + h * jj / 6.0));
+            P.vp[d] = P.v[d] + h * (aa + h * jj / 2.0);
+            ir[i].x[d] = P.xp[d];
+            ir[i].v[d] = P.vp[d];
         }
         ir[i].h2 = 0.0;
         ir[i].index = q;
@@ -1049,26 +1058,26 @@ int hb_correct(g6hb_sim &s, const g6hb_sim::Chunk &c)
     for (int i = c.i0; i < c.i1; ++i) {
         const int q = s.act[k][i];
         const int p = s.off[k] + q;
-        double t0[1] = {s.t[p]}, dtv[1] = {s.dt[p]}, dn[1];
-        const int rc = g6h_correct_block_ex(1, tb, t0, dtv, s.eta, s.dt_max, s.dt_min,
-                                            &s.xp[3 * p], &s.vp[3 * p], &s.a[3 * p], &s.j[3 * p],
-                                            o[i].acc, o[i].jerk, dn, s.noise);
+        g6hb_sim::Part &P = s.ps[p];
+        double t0[1] = {P.t}, dtv[1] = {P.dt}, dn[1];
+        const int rc = g6h_correct_block_ex(1, tb, t0, dtv, s.eta, s.dt_max, s.dt_min, P.xp, P.vp,
+                                            P.a, P.j, o[i].acc, o[i].jerk, dn, s.noise);
         if (rc != 0)
             return rc < 0 ? rc : G6_EINVAL;
         const size_t si = s.sbase[k] + i;
         g6x_jrec &r = b->stage[k][si];
         for (int d = 0; d < 3; ++d) {
-            s.x[3 * p + d] = s.xp[3 * p + d];
-            s.v[3 * p + d] = s.vp[3 * p + d];
-            s.a[3 * p + d] = o[i].acc[d];
-            s.j[3 * p + d] = o[i].jerk[d];
-            r.x[d] = s.x[3 * p + d];
-            r.v[d] = s.v[3 * p + d];
-            r.a2[d] = 0.5 * s.a[3 * p + d];
-            r.j6[d] = s.j[3 * p + d] / 6.0;
+            P.x[d] = P.xp[d];
+            P.v[d] = P.vp[d];
+            P.a[d] = o[i].acc[d];
+            P.j[d] = o[i].jerk[d];
+            r.x[d] = P.x[d];
+            r.v[d] = P.v[d];
+            r.a2[d] = 0.5 * P.a[d];
+            r.j6[d] = P.j[d] / 6.0;
         }
-        s.t[p] = tb;
-        s.dt[p] = dn[0];
+        P.t = tb;
+        P.dt = dn[0];
         const int slot = b->jtile[k] * JT + q;
         r.mass = s.m[p];
         r.tj = tb;
@@ -1089,7 +1098,7 @@ int hb_file(g6hb_sim &s, int k)
     try {
         for (int q : s.act[k]) {
             const int p = s.off[k] + q;
-            const double tn = s.t[p] + s.dt[p];
+            const double tn = s.ps[p].t + s.ps[p].dt;
             if (!last || tn != last_t) {
                 last = &s.due[k][tn];
                 last_t = tn;
@@ -1167,19 +1176,21 @@ g6hb_sim *g6hb_create(int ncl, const int n[], const double *m, const double *x,
         }
         s->eps2.assign(eps2, eps2 + ncl);
         s->m.assign(m, m + tot);
-        s->x.assign(x, x + 3 * (size_t)tot);
-        s->v.assign(v, v + 3 * (size_t)tot);
-        s->a.assign(3 * (size_t)tot, 0.0);
-        s->j.assign(3 * (size_t)tot, 0.0);
-        s->t.assign(tot, 0.0);
-        s->dt.assign(tot, dt_max);
+        s->ps.assign(tot, g6hb_sim::Part{});
+        for (int p = 0; p < tot; ++p) {
+            g6hb_sim::Part &P = s->ps[p];
+            for (int d = 0; d < 3; ++d) {
+                P.x[d] = x[3 * (size_t)p + d];
+                P.v[d] = v[3 * (size_t)p + d];
+            }
+            P.t = 0.0;
+            P.dt = dt_max;
+        }
         s->due.resize(ncl);
         s->act.resize(ncl);
         s->tblk.assign(ncl, 0.0);
         s->ni.assign(ncl, 0);
         s->rc.assign(ncl, 0);
-        s->xp.resize(3 * (size_t)tot);
-        s->vp.resize(3 * (size_t)tot);
         s->hist.assign((size_t)HIST * ncl, 0);
         s->sbase.assign(ncl, 0);
     } catch (...) {
@@ -1196,10 +1207,10 @@ g6hb_sim *g6hb_create(int ncl, const int n[], const double *m, const double *x,
     for (int k = 0; !rc && k < ncl; ++k) {
         g6x_irec *ir = g6x_batch_irecs(s->b, k);
         for (int q = 0; q < n[k]; ++q) {
-            const int p = s->off[k] + q;
+            const g6hb_sim::Part &P = s->ps[s->off[k] + q];
             for (int d = 0; d < 3; ++d) {
-                ir[q].x[d] = s->x[3 * p + d];
-                ir[q].v[d] = s->v[3 * p + d];
+                ir[q].x[d] = P.x[d];
+                ir[q].v[d] = P.v[d];
             }
             ir[q].h2 = 0.0;
             ir[q].index = q;
@@ -1212,18 +1223,18 @@ g6hb_sim *g6hb_create(int ncl, const int n[], const double *m, const double *x,
     for (int k = 0; !rc && k < ncl; ++k) {
         const g6x_out *o = g6x_batch_results(s->b, k);
         for (int q = 0; q < n[k]; ++q) {
-            const int p = s->off[k] + q;
+            g6hb_sim::Part &P = s->ps[s->off[k] + q];
             for (int d = 0; d < 3; ++d) {
-                s->a[3 * p + d] = o[q].acc[d];
-                s->j[3 * p + d] = o[q].jerk[d];
+                P.a[d] = o[q].acc[d];
+                P.j[d] = o[q].jerk[d];
             }
-            const double req = s->eta_s * nrm(&s->a[3 * p]) / nrm(&s->j[3 * p]);
+            const double req = s->eta_s * nrm(P.a) / nrm(P.j);
             double d = dt_max;
             while (d > req)
                 d *= 0.5;
             if (d < dt_min)
                 rc = G6_EINVAL;
-            s->dt[p] = d;
+            P.dt = d;
             s->due[k][d].push_back(q);
         }
     }
@@ -1357,12 +1368,17 @@ int g6hb_get_state(const g6hb_sim *s, double *x, double *v, double *t)
     if (!s)
         return G6_EINVAL;
     const size_t tot = s->m.size();
-    if (x)
-        std::memcpy(x, s->x.data(), 3 * tot * sizeof(double));
-    if (v)
-        std::memcpy(v, s->v.data(), 3 * tot * sizeof(double));
-    if (t)
-        std::memcpy(t, s->t.data(), tot * sizeof(double));
+    for (size_t p = 0; p < tot; ++p) {
+        const g6hb_sim::Part &P = s->ps[p];
+        for (int d = 0; d < 3; ++d) {
+            if (x)
+                x[3 * p + d] = P.x[d];
+            if (v)
+                v[3 * p + d] = P.v[d];
+        }
+        if (t)
+            t[p] = P.t;
+    }
     return 0;
 }
 
@@ -1373,12 +1389,17 @@ int g6hb_get_state_ex(const g6hb_sim *s, double *x, double *v, double *acc, doub
     if (rc)
         return rc;
     const size_t tot = s->m.size();
-    if (acc)
-        std::memcpy(acc, s->a.data(), 3 * tot * sizeof(double));
-    if (jerk)
-        std::memcpy(jerk, s->j.data(), 3 * tot * sizeof(double));
-    if (dt)
-        std::memcpy(dt, s->dt.data(), tot * sizeof(double));
+    for (size_t p = 0; p < tot; ++p) {
+        const g6hb_sim::Part &P = s->ps[p];
+        for (int d = 0; d < 3; ++d) {
+            if (acc)
+                acc[3 * p + d] = P.a[d];
+            if (jerk)
+                jerk[3 * p + d] = P.j[d];
+        }
+        if (dt)
+            dt[p] = P.dt;
+    }
     return 0;
 }
 
