@@ -189,9 +189,14 @@ struct Ctx {
 
 Ctx g_ctx[G6_MAX_CLUSTERS];
 
-// Host loops over at least this many particles run on the host threads.
-constexpr int PAR_MIN = 8192;
-constexpr int PAR_CHUNK = 4096;
+// Host loops over at least this many particles run on the host threads, in
+// chunks of PAR_CHUNK (a fork and join of the pool costs a few microseconds,
+// a chunk's copies about as much); the staging sort, whose parallel form
+// keeps and sums per-chunk tile counts, only from PAR_MIN_SORT records and
+// twice as many records as tiles on.
+constexpr int PAR_MIN = 1024;
+constexpr int PAR_CHUNK = 512;
+constexpr int PAR_MIN_SORT = 2048;
 
 // f(k0, k1) over [0, n): serially for small n, else in chunks on the host threads.
 template <class F>
@@ -469,7 +474,7 @@ int predict_if_stale(Ctx &c, int nj)
 bool sort_by_tile(Ctx &c, int ntiles)
 {
     const int n = c.n_jst;
-    g6::HostPool *pool = n < PAR_MIN ? nullptr : g6::shared_pool();
+    g6::HostPool *pool = n < std::max(PAR_MIN_SORT, 2 * ntiles) ? nullptr : g6::shared_pool();
     if (!pool) {
         try {
             c.tcur.assign(ntiles + 1, 0);
