@@ -137,7 +137,8 @@ struct Ctx {
     size_t tcnt_cap = 0;
     bool tcnt_dirty = false;          // a launch may have stopped mid-count
     int *d_nbl_part = nullptr, *d_nbc_part = nullptr;
-    size_t nbp_cap = 0;
+    size_t nbp_cap = 0;               // list counts of d_nbc_part
+    size_t nbl_ints = 0;              // ints of d_nbl_part
     int nbp_seg = 0;                  // entries per list partial of d_nbl_part
     int *d_nbl = nullptr, *d_nblen = nullptr, *h_nbl = nullptr, *h_nblen = nullptr;
     size_t nbo_cap = 0;
@@ -320,10 +321,10 @@ void free_ctx(Ctx &c)
     if (c.stream)
         cudaStreamSynchronize(c.stream);
     g6::JStore &js = c.js;
-    // d_jst, d_irec, d_out and d_err are device aliases of mapped host
-    // buffers, freed with them below
+    // d_jst, d_irec, d_out, d_nbl, d_nblen and d_err are device aliases of
+    // mapped host buffers, freed with them below
     void *dptrs[] = {js.x0, js.raw, js.v64, js.a264, js.j664, js.idx, c.pred.pt, c.pred.trange, c.pred.p64, c.pred.v64,
-                     c.d_part, c.d_tcnt, c.d_nbl_part, c.d_nbc_part, c.d_nbl, c.d_nblen};
+                     c.d_part, c.d_tcnt, c.d_nbl_part, c.d_nbc_part};
     for (void *p : dptrs)
         dev_free(p);
     void *hptrs[] = {c.h_jst, c.h_jsort, c.h_toff, c.h_irec, c.h_out, c.h_nbl, c.h_nblen,
@@ -616,29 +617,26 @@ int update_and_predict(Ctx &c, int nj, bool predict = true, int fold_jtiles = 0,
     return 0;
 }
 
-// Output neighbour lists for ni i-particles (device and pinned host copies).
+// Output neighbour lists for ni i-particles, in mapped host memory: the
+// reduction writes each list's entries and its length there directly, so a
+// read moves only the entries found, not ni x maxnb slots.
 int grow_nb_out(Ctx &c, int ni)
 {
     if ((size_t)ni <= c.nbo_cap && c.d_nbl && c.nbo_maxnb == c.maxnb)
         return 0;
     size_t n = (size_t)(ni > 16 ? ni : 16);
-    int *dl = (int *)dev_alloc(n * c.maxnb * sizeof(int));
-    int *dn = (int *)dev_alloc(n * sizeof(int));
-    int *hl = (int *)host_alloc(n * c.maxnb * sizeof(int));
-    int *hn = (int *)host_alloc(n * sizeof(int));
-    if (!dl || !dn || !hl || !hn) {
-        dev_free(dl);
-        dev_free(dn);
+    void *dl = nullptr, *dn = nullptr;
+    int *hl = (int *)host_alloc_mapped(n * c.maxnb * sizeof(int), &dl);
+    int *hn = (int *)host_alloc_mapped(n * sizeof(int), &dn);
+    if (!hl || !hn) {
         host_free(hl);
         host_free(hn);
         return G6_ENOMEM;
     }
-    dev_free(c.d_nbl);
-    dev_free(c.d_nblen);
     host_free(c.h_nbl);
     host_free(c.h_nblen);
-    c.d_nbl = dl;
-    c.d_nblen = dn;
+    c.d_nbl = (int *)dl;
+    c.d_nblen = (int *)dn;
     c.h_nbl = hl;
     c.h_nblen = hn;
     c.nbo_cap = n;
@@ -731,23 +729,15 @@ int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_
     if (cfg.list) {
         // each list partial (one CTA's segment of one i-particle) has room
         // for la.nbseg entries, not for a whole list: the partials take
-        // slots x nbseg ints instead of slots x maxnb
-        size_t cap_old = c.nbp_cap;
+        // slots x nbseg ints instead of slots x maxnb (the split-j shapes
+        // also keep one run per j-group)
         rc = grow_dev(c.d_nbc_part, c.nbp_cap, slots);
         if (rc)
             return rc;
-        if (c.nbp_cap != cap_old || !c.d_nbl_part || c.nbp_seg != la.nbseg) {
-            dev_free(c.d_nbl_part);
-            c.d_nbl_part = (int *)dev_alloc(c.nbp_cap * la.nbseg * sizeof(int));
-            c.nbp_seg = la.nbseg;
-            if (!c.d_nbl_part) {
-                c.nbp_cap = 0;
-                c.nbp_seg = 0;
-                dev_free(c.d_nbc_part);
-                c.d_nbc_part = nullptr;
-                return G6_ENOMEM;
-            }
-        }
+        rc = grow_dev(c.d_nbl_part, c.nbl_ints, g6::list_part_ints(cfg, la.nbseg));
+        if (rc)
+            return rc;
+        c.nbp_seg = la.nbseg;
         rc = grow_nb_out(c, ni);
         if (rc)
             return rc;
@@ -1109,10 +1099,8 @@ void g6calc_firsthalf(int cid, int nj, int ni, const int index[],
     if (!rc && ni > 0) {
         if (!rc && h2 && !list) {
             // every radius is <= 0: no list can have entries; skip the list
-            // kernel and publish empty lists
+            // kernel; the read publishes empty lists
             rc = grow_nb_out(*c, ni);
-            if (!rc)
-                rc = cuda_err(cudaMemsetAsync(c->d_nblen, 0, sizeof(int) * ni, c->stream));
             if (!rc) {
                 c->lists_ready = true;
                 c->list_ni = ni;
@@ -1235,15 +1223,10 @@ int g6_read_neighbour_list(int cid)
             return code < 0 ? code : G6_EIO;
         }
     }
-    e = cudaMemcpyAsync(c->h_nblen, c->d_nblen, sizeof(int) * n, cudaMemcpyDeviceToHost,
-                        c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->h_nbl, c->d_nbl, sizeof(int) * (size_t)n * c->maxnb,
-                            cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess)
-        e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess)
-        return cuda_err(e);
+    // the reduction wrote the lists into mapped host memory; a calculation
+    // whose radii were all <= 0 ran no list kernel and has empty lists
+    if (!c->list_cfg.list)
+        std::memset(c->h_nblen, 0, sizeof(int) * n);
     c->lists_host = true;
     for (int k = 0; k < n; ++k)
         if (c->h_nblen[k] > c->maxnb)

@@ -304,6 +304,7 @@ struct ForceArgs {
     const g6x_irec *irec;
     void *part;                       // PartialDS (DS kernels) or Partial64 (FP64)
     int *nbl;                         // list entries  [slot][nbseg]
+    int *nbr;                         // split-j shapes: runs of the j-groups [slot][TJ][nbseg]
     int *nbc;                         // list counts   [slot]
     int maxnb;                        // list length kept per i-particle (Sect. 4)
     int nbseg;                        // entries a list partial has room for (<= maxnb)

@@ -218,6 +218,9 @@ ForceConfig choose_config(int prec, int ni, int nj_pad, int list, int sm_count,
 extern bool g_ws_default;
 // Number of Partial slots a launch with this configuration writes.
 size_t partial_slots(const ForceConfig &cfg);
+// Ints of list-partial storage a list launch needs with nbseg entries per
+// partial: the partials, and for the split-j shapes the runs of their j-groups.
+size_t list_part_ints(const ForceConfig &cfg, int nbseg);
 // Arrival counters a launch with this configuration needs (zero before it).
 size_t counter_slots(const ForceConfig &cfg);
 

@@ -309,7 +309,12 @@ __device__ __forceinline__ float2 ds_sep2(float2 h, float2 l, float2 nh, float2 
 // The nearest neighbour is tracked lazily: a running minimum of the key per
 // tile and the tile that lowered it; when a segment ends, that one tile is
 // scanned again with the same arithmetic to find the first j that attains
-// the minimum (ties to the lower j-slot).
+// the minimum (ties to the lower j-slot).  Lists (Sect. 4) use the same
+// minimum: the loop keeps it per chunk of 4 j-pairs, and only a chunk whose
+// minimum is below h2 + eps2 is scanned again, from the staged tile, for
+// its members, so the pair loop is the same with and without lists.  With
+// TJ j-groups each group keeps its own ascending run of members, and the
+// runs are merged when a segment ends.
 //
 // Sums run in FP32 over one flush interval (>= 512 j per thread) and are
 // then folded into compensated (TwoSum) FP32 pairs kept in shared memory, so
@@ -336,7 +341,6 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     // predicted by the CTA into pbuf before the pair loop
     constexpr unsigned STAGE_BYTES = FP ? RAW_TILE_BYTES : TILE_BYTES;
     constexpr int NS = FP ? FP_NSTAGE : NSTAGE;         // stages in the ring
-    static_assert(!LIST || TJ == 1, "neighbour lists need whole j-tiles per thread");
     static_assert(JT % (2 * TJ) == 0, "j-tile must split into j-pairs evenly");
     // nothing is read before the predecessor (prediction, or an earlier
     // reduction of the same partial buffers) has completed
@@ -353,6 +357,11 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     __shared__ int s_abort;
     __shared__ float s_nnr[TJ > 1 ? NI * NT : 1];
     __shared__ int s_nnj[TJ > 1 ? NI * NT : 1];
+    // split-j lists: each thread's run of entries (its count, then the head
+    // of the run during the merge at the end of a segment)
+    constexpr bool LRUN = LIST && TJ > 1;
+    __shared__ int s_nbn[LRUN ? NI * NT : 1];
+    __shared__ int s_nbh[LRUN ? NI * NT : 1];
     __shared__ float s_ibuf[TJ > 1 ? 11 * ITILE : 1];
 
     const int tid = threadIdx.x;
@@ -779,6 +788,17 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         __syncthreads();
     };
 
+    // Where a thread's list entries for slot il of segment seg go: with whole
+    // j-tiles per thread, the list partial itself; with TJ j-groups, the
+    // group's own run (ascending j, as the group walks its j-pairs in
+    // order), merged into the list partial when the segment ends.
+    auto list_run = [&](long long seg, int il, int g) -> int * {
+        if constexpr (LRUN)
+            return a.nbr + (((size_t)seg * ITILE + il) * TJ + g) * a.nbseg;
+        else
+            return a.nbl + ((size_t)seg * ITILE + il) * a.nbseg;
+    };
+
     auto finalize = [&](int t) {
         flush();
         const long long seg = c + t;
@@ -811,6 +831,8 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
             for (int k = 0; k < NI; ++k) {
                 s_nnr[k * NT + tid] = nnr[k];
                 s_nnj[k * NT + tid] = nn_rescan(k);
+                if constexpr (LRUN)
+                    s_nbn[k * NT + tid] = nbn[k];
             }
             __syncthreads();
             for (int il = tid; il < ITILE; il += NT) {
@@ -846,6 +868,43 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                 P->pot = make_float2(sh[6], sl[6]);
                 P->nnr2 = unsoftened(br, eps2.x);
                 P->nnj = bj;
+                if constexpr (LRUN) {
+                    // merge the TJ ascending runs into the list partial;
+                    // a run keeps its first nbseg entries, and a total above
+                    // nbseg makes the host compute the lists again with more
+                    // room, unless nbseg is already the list length (then
+                    // the lowest maxnb j of the runs are the lowest overall)
+                    int tot = 0;
+                    for (int g = 0; g < TJ; ++g)
+                        tot += s_nbn[k * NT + g * TI + ii];
+                    const int keep = min(tot, a.nbseg);
+                    if (keep > 0) {
+                        int *dst = a.nbl + ((size_t)seg * ITILE + il) * a.nbseg;
+                        for (int g = 0; g < TJ; ++g) {
+                            const int o = k * NT + g * TI + ii;
+                            s_nnj[o] = 0;               // read position in the run
+                            s_nbh[o] = s_nbn[o] > 0 ? list_run(seg, il, g)[0] : INT_MAX;
+                        }
+                        for (int e = 0; e < keep; ++e) {
+                            int best = INT_MAX, bg = 0;
+                            for (int g = 0; g < TJ; ++g) {
+                                const int h = s_nbh[k * NT + g * TI + ii];
+                                if (h < best) {
+                                    best = h;
+                                    bg = g;
+                                }
+                            }
+                            dst[e] = best;
+                            const int o = k * NT + bg * TI + ii;
+                            const int pos = ++s_nnj[o];
+                            s_nbh[o] = pos < min(s_nbn[o], a.nbseg) ? list_run(seg, il, bg)[pos]
+                                                                    : INT_MAX;
+                        }
+                    }
+                    a.nbc[(size_t)seg * ITILE + il] = tot;
+                    if (tot > 0)
+                        atomicMax(a.nbmax, min(tot, a.maxnb));
+                }
             }
             __syncthreads();
         }
@@ -917,24 +976,45 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                 ta[k][4] = __ffma2_rn(mr3, __ffma2_rn(sc, dy, uy), ta[k][4]);
                 ta[k][5] = __ffma2_rn(mr3, __ffma2_rn(sc, dz, uz), ta[k][5]);
                 mins[k] = fminf(mins[k], fminf(key.x, key.y));
-                if constexpr (LIST) {
-                    const int il = k * TI + ti;
-                    const int j0 = jt * JT + 2 * jp;
-                    int *dst = a.nbl + ((size_t)(c + t) * ITILE + il) * a.nbseg;
-                    if (key.x < h2[k]) {
-                        if (nbn[k] < a.nbseg)
-                            dst[nbn[k]] = j0;
-                        ++nbn[k];
+            }
+        };
+        // Lists: the entries of chunk ch against i-particle k, the keys
+        // computed again with the loop's arithmetic (packed lanes round like
+        // the scalar operations used here), in ascending j.  Called only for
+        // chunks whose smallest key is below the radius, so the pair loop
+        // itself carries no list test.
+        auto list_chunk = [&](int ch, int k) {
+            int *dst = list_run(c + t, k * TI + ti, tj);
+            for (int u = 0; u < CHP; ++u) {
+                const int jp = tj + (ch * CHP + u) * TJ;
+                const float2 xh = XH[jp], yh = YH[jp], zh = ZH[jp];
+                const float2 xl = XL[jp], yl = YL[jp], zl = ZL[jp];
+                const int2 id = ID[jp];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float dd[3];
+                    const float xs[3] = {h ? xh.y : xh.x, h ? yh.y : yh.x, h ? zh.y : zh.x};
+                    const float xt[3] = {h ? xl.y : xl.x, h ? yl.y : yl.x, h ? zl.y : zl.x};
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        if constexpr (DSS)
+                            dd[d] = ds_sep1(xs[d], xt[d], nxh[k][d].x, nxl[k][d].x);
+                        else
+                            dd[d] = __fadd_rn(__fadd_rn(xs[d], nxh[k][d].x),
+                                              __fadd_rn(xt[d], nxl[k][d].x));
                     }
-                    if (key.y < h2[k]) {
+                    float key = soft_r2(dd[0], dd[1], dd[2], eps2.x);
+                    if ((h ? id.y : id.x) == iid[k])
+                        key = INF;
+                    if (key < h2[k]) {
                         if (nbn[k] < a.nbseg)
-                            dst[nbn[k]] = j0 + 1;
+                            dst[nbn[k]] = jt * JT + 2 * jp + h;
                         ++nbn[k];
                     }
                 }
             }
         };
-        if constexpr (NNC) {
+        if constexpr (NNC || LIST) {
             for (int ch = 0; ch < PPT / CHP; ++ch) {
                 float cm[NI];
 #pragma unroll
@@ -944,11 +1024,15 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                 for (int u = 0; u < CHP; ++u)
                     jpair(ch * CHP + u, cm);
 #pragma unroll
-                for (int k = 0; k < NI; ++k)
+                for (int k = 0; k < NI; ++k) {
+                    if constexpr (LIST)
+                        if (cm[k] < h2[k])
+                            list_chunk(ch, k);
                     if (cm[k] < tmin[k]) {      // the first chunk that reaches the minimum
                         tmin[k] = cm[k];
                         tchk[k] = ch;
                     }
+                }
             }
         } else {
 #pragma unroll UNR
@@ -1032,9 +1116,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
             pairs_of_tile(pbuf, self_test(rg));
             __syncthreads();                     // pbuf is rewritten by the next tile
         } else {
-            bool self_tile = LIST;
-            if constexpr (!LIST)
-                self_tile = self_test(a.trange[jt]);
+            const bool self_tile = self_test(a.trange[jt]);
             const bool ready = mbar_wait_bounded(&bar[s], par, a.wait_ns);
             if (!ready)
                 s_abort = 1;
@@ -1383,6 +1465,12 @@ const Variant kVariants[] = {
      128, ds_smem(128, 2)},
     {{16, 16, 1, 0, G6X_PREC_DS_DSSUB}, k_force_ds<16, 16, 1, false, 1, 2, false, false, true>,
      256, ds_smem(256, 1)},
+    // neighbour lists: the twins of variants 9, 4, 14, 15 and 16
+    {{128, 1, 2, 1, G6X_PREC_DS}, k_force_ds<128, 1, 2, true, 4, 2>, 128, ds_smem(128, 2)},
+    {{16, 16, 1, 1, G6X_PREC_DS}, k_force_ds<16, 16, 1, true>, 256, ds_smem(256, 1)},
+    {{16, 16, 2, 1, G6X_PREC_DS}, k_force_ds<16, 16, 2, true, 2, 2>, 256, ds_smem(256, 2)},
+    {{32, 8, 2, 1, G6X_PREC_DS}, k_force_ds<32, 8, 2, true, 2, 2>, 256, ds_smem(256, 2)},
+    {{64, 4, 2, 1, G6X_PREC_DS}, k_force_ds<64, 4, 2, true, 2, 2>, 256, ds_smem(256, 2)},
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
@@ -1562,9 +1650,7 @@ int heuristic_variant(int prec, int ni, int nj_pad, int list, bool allow_ws, int
         *gmul = ni > 2048 ? 2 : 1;
         return ni <= 32 ? 22 : 21;
     }
-    if (list)
-        return ni <= 32 ? 6 : 5;
-    if (allow_ws
+    if (allow_ws && !list
         && (ni <= WS_ANY_N_MAX_NI
             || (ni <= WS_MID_MAX_NI && nj_pad / JT >= WS_MID_MIN_JTILES)
             || (ni <= WS_DEFAULT_MAX_NI && nj_pad / JT >= WS_MIN_JTILES))) {
@@ -1590,13 +1676,24 @@ int heuristic_variant(int prec, int ni, int nj_pad, int list, bool allow_ws, int
         int v, itile, max_ni;
         long long min_units;
     };
-    static constexpr Shape shapes[] = {
+    static constexpr Shape plain_shapes[] = {
         {9, 256, INT_MAX, 16384},  // 128 threads, two i each, whole j-tiles, 4 CTAs per SM
         {16, 128, 2048, 4096},     // 64 x 4 threads, two i each
         {15, 64, 128, 2048},       // 32 x 8 threads, two i each
         {14, 32, 64, 2048},        // 16 x 16 threads, two i each
         {4, 16, 32, 0},            // 16 x 16 threads, one i each
     };
+    // their twins with neighbour lists (the wide shape only on longer work
+    // lines: at N = 131072 the 64 x 4 twin is 10 % faster for m = 16384 and
+    // even for m = 65536)
+    static constexpr Shape list_shapes[] = {
+        {23, 256, INT_MAX, 65536},
+        {27, 128, 2048, 4096},
+        {26, 64, 128, 2048},
+        {25, 32, 64, 2048},
+        {24, 16, 32, 0},
+    };
+    const Shape *shapes = list ? list_shapes : plain_shapes;
     const long long jtl = nj_pad / JT;
     int k = 0;
     while (shapes[k].min_units > 0
@@ -1605,7 +1702,7 @@ int heuristic_variant(int prec, int ni, int nj_pad, int list, bool allow_ws, int
                       < shapes[k].min_units))
         ++k;
     *gmul = 1;
-    if (shapes[k].v == 9) {
+    if (shapes[k].v == 9 || shapes[k].v == 23) {
         // Several waves of CTAs per SM: the warp schedulers favour the
         // oldest CTAs, so equal shares of the work line finish at different
         // times, and with one wave the SMs run their last stretch with few
@@ -1683,6 +1780,11 @@ size_t partial_slots(const ForceConfig &cfg)
     if (cfg.ws)
         return ws_partial_slots(cfg.grid, cfg.itile);
     return (size_t)(cfg.grid + cfg.n_itile) * cfg.itile;
+}
+
+size_t list_part_ints(const ForceConfig &cfg, int nbseg)
+{
+    return partial_slots(cfg) * (size_t)nbseg * (cfg.tj > 1 ? 1 + cfg.tj : 1);
 }
 
 size_t counter_slots(const ForceConfig &cfg)
@@ -1803,6 +1905,8 @@ cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
     }
     if (cfg.list && (!lists || !lists->nbmax || lists->nbseg < 1 || lists->nbseg > lists->maxnb))
         return cudaErrorInvalidValue;
+    if (cfg.list && cfg.tj > 1)
+        a.nbr = nbl_part + partial_slots(cfg) * (size_t)lists->nbseg;
     a.err = d_err;
     a.W = cfg.work;
     a.J = cfg.jtiles;

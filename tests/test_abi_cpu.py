@@ -191,7 +191,9 @@ def test_launch_plan_heuristic_without_a_gpu(lib):
         assert all(ws(nj, ni) == (nj >= 524288) for ni in (33, 64))
         assert not any(ws(nj, ni) for ni in (65, 128, 256, 4096))
         assert shape(nj, 1) == (8, 32, 1) and shape(nj, 8) == (8, 32, 1)
-        assert g6gb.g6x_plan_launch(ds, nj, 16, True)["variant"] in (5, 6)   # lists: no
+        lp = g6gb.g6x_plan_launch(ds, nj, 16, True)                      # lists: no
+        assert g6gb.g6x_variant_info(lp["variant"])["ws"] == 0
+        assert g6gb.g6x_variant_info(lp["variant"])["list"] == 1
     assert shape(big, 17) == (32, 8, 1) and shape(big, 64) == (64, 4, 1)
     assert shape(big, 16) == (16, 16, 1)
     assert shape(big, 128) == (32, 8, 2)
@@ -215,8 +217,20 @@ def test_launch_plan_heuristic_without_a_gpu(lib):
     # other modes keep their own kernels
     assert g6gb.g6x_plan_launch(g6gb.G6X_PREC_FP64, big, 4096)["variant"] == 7
     assert g6gb.g6x_plan_launch(g6gb.G6X_PREC_FP64, big, 4096, True)["variant"] == 8
-    assert g6gb.g6x_plan_launch(ds, big, 4096, True)["variant"] == 5
-    assert g6gb.g6x_plan_launch(ds, big, 16, True)["variant"] == 6
+    # lists take the twins of the three-kernel path's shapes, the widest
+    # only from 65536 (i-tile, j-tile) units on
+    for nj in (small, 131072, big):
+        for ni in (16, 32, 64, 128, 256, 1000, 4096, 20000, nj):
+            lp = g6gb.g6x_plan_launch(ds, nj, ni, True)
+            info = g6gb.g6x_variant_info(lp["variant"])
+            assert info["list"] == 1 and info["prec"] == ds and info["ws"] == 0
+            if ni > 64:
+                wl, wp = shape(nj, ni, ds, True), shape(nj, ni)
+                assert wl == wp or (wp == (128, 1, 2) and wl == (64, 4, 2)), (nj, ni)
+                assert (wl == (128, 1, 2)) == (-(-ni // 256) * (nj // 256) >= 65536), (nj, ni)
+    assert shape(big, 16, ds, True) == (16, 16, 1)
+    assert shape(131072, 16384, ds, True) == (64, 4, 2)
+    assert shape(big, 4096, ds, True) == (128, 1, 2)
     assert g6gb.g6x_plan_launch(g6gb.G6X_PREC_DS_DSSUB, big, 16)["variant"] == 22
     assert g6gb.g6x_plan_launch(g6gb.G6X_PREC_DS_DSSUB, big, 4096)["variant"] == 21
     out = np.zeros(6, dtype=np.int32)

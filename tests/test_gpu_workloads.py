@@ -137,6 +137,50 @@ def test_neighbour_lists_plummer_with_binaries(open_ctx, orc, prec, maxnb):
     assert np.median(ea) <= lim[0] and ea.max() <= lim[1]
 
 
+@pytest.mark.parametrize("m", [16, 300])
+def test_neighbour_lists_every_list_shape(open_ctx, orc, m):
+    # Every DS list shape, forced, against the oracle's lists: the split-j
+    # shapes merge the ascending runs of their j-groups at the end of each
+    # segment, so contents, order, truncation at the list length (the lowest
+    # j-slots) and the counts must match whatever the shape.
+    n, eps2, maxnb = 8192, 1e-8, 256
+    m_, x, v, pairs = ics.plummer_with_binaries(n, 6)
+    idx = np.arange(n)
+    cid = open_ctx(n, n)
+    load_j(cid, x, v, m_)
+    act = np.sort(ics.permutation(n, 6)[:m])
+    h2 = np.full(act.size, 1e-4)
+    h2[::5] = 0.05 ** 2
+    h2[::7] = 0.3 ** 2                        # past the list length
+    h2[::9] = 1.0
+    nblen, nbl, nov = orc.neighbours(x[act], act, x, idx, h2, maxnb=maxnb)
+    oa, *_ = orc.force(x[act], v[act], act, x, v, m_, idx, eps2)
+    shapes = [k for k in range(g6.g6x_variant_count())
+              if g6.g6x_variant_info(k)["list"] == 1
+              and g6.g6x_variant_info(k)["prec"] == g6.G6X_PREC_DS]
+    assert len(shapes) >= 7
+    try:
+        for k in shapes:
+            g6.g6x_set_variant(cid, k, 0)
+            acc, jerk, pot, nnb = sweep(cid, n, x[act], v[act], act, eps2, 0.0, h2=h2)
+            assert g6.g6x_last_config(cid)["variant"] == k
+            rc = g6.g6_read_neighbour_list(cid)
+            assert rc == (g6.G6_EOVERFLOW if nov else 0), k
+            for q in range(act.size):
+                rc_q, ln, ids = g6.g6_get_neighbour_list(cid, q)
+                assert list(ids) == sorted(ids), (k, q)
+                if nblen[q] <= maxnb:
+                    assert abs(ln - nblen[q]) <= 2, (k, q)
+                    _list_ok(ids, nbl[q, :nblen[q]], idx, x[act[q]], x, h2[q])
+                else:
+                    assert ln > maxnb and rc_q == g6.G6_EOVERFLOW and len(ids) == maxnb
+                    _list_ok(ids, nbl[q, :maxnb], idx, x[act[q]], x, h2[q])
+            ea = rel_err_vec(acc, oa)
+            assert np.median(ea) <= 1e-6 and ea.max() <= 1e-5, k
+    finally:
+        g6.g6x_set_variant(cid, -1, 0)
+
+
 def test_list_length_setting_is_validated(open_ctx):
     cid = open_ctx(1024, 64)
     assert g6.g6x_max_neighbours(cid) == g6.G6_MAXNB
