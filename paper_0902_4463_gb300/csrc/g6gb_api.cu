@@ -761,17 +761,22 @@ int run_force(Ctx &c, const ForceConfig &cfg, int nj, int ni, const g6x_irec *d_
         e = g6::launch_force_ws(cfg, d_irec, ni, eps2, nj, c.d_part, c.d_tcnt, d_out, c.js.idx,
                                 c.d_err, fpa, c.stream, pdl);
         c.launches += 1;
-    } else if (!cfg.list && cfg.prec == G6X_PREC_DS && seg_per_tile <= g6::FUSED_MAX_SEGS) {
+    } else if (cfg.prec == G6X_PREC_DS && seg_per_tile <= g6::FUSED_MAX_SEGS) {
         // one launch: the last CTA of each i-tile reduces it (K3 fused into
-        // K2) when every tile has only a few partials (large blocks); with
-        // many partials per tile that serial tail costs more than the
-        // separate K3, which spreads the sums over many CTAs
+        // K2), lists included, when every tile has only a few partials
+        // (large blocks); with many partials per tile that serial tail
+        // costs more than the separate K3, which spreads the sums over many
+        // CTAs
         rc = ensure_counters(c, g6::counter_slots(cfg));
         if (rc)
             return rc;
+        la.nbl_part = c.d_nbl_part;
+        la.nbc_part = c.d_nbc_part;
+        la.nbl_out = c.d_nbl;
+        la.nblen_out = c.d_nblen;
         PhaseTimer pt(c, PH_FORCE);
         e = g6::launch_force_fused(cfg, c.pred, d_irec, ni, eps2, c.d_part, c.d_err, d_out,
-                                   c.js.idx, c.d_tcnt, c.stream, fpp, pdl);
+                                   c.js.idx, c.d_tcnt, c.stream, fpp, pdl, &la);
         c.launches += 1;
     } else {
         {

@@ -309,6 +309,7 @@ struct ForceArgs {
     int maxnb;                        // list length kept per i-particle (Sect. 4)
     int nbseg;                        // entries a list partial has room for (<= maxnb)
     int *nbmax;                       // largest min(count, maxnb) of any list partial
+    int *nbl_out, *nblen_out;         // fused reduction: the lists [i][maxnb], their lengths
     int *err;
     long long W;
     int J;

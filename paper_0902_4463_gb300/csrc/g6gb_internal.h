@@ -256,20 +256,23 @@ cudaError_t launch_update_predict(int kind, JStore js, Pred p, int nj, int nj_pa
 struct ListArgs {
     int maxnb, nbseg;
     int *nbmax;
+    // the fused launch also takes the list partials and the output lists
+    int *nbl_part = nullptr, *nbc_part = nullptr, *nbl_out = nullptr, *nblen_out = nullptr;
 };
 cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
                          const g6x_irec *d_irec, int ni, double eps2,
                          void *part, int *nbl_part, int *nbc_part,
                          int *d_err, cudaStream_t s, const FusedPred *fp = nullptr,
                          bool pdl = false, const ListArgs *lists = nullptr);
-// DS force with the reduction fused in (no neighbour lists): the last CTA
-// to finish an i-tile writes its results to out.  tcnt holds one counter per
-// i-tile, zero before the launch and left zero by a launch that completes.
+// DS force with the reduction fused in: the last CTA to finish an i-tile
+// writes its results to out (and with lists, every field of *lists set, the
+// concatenated lists).  tcnt holds one counter per i-tile, zero before the
+// launch and left zero by a launch that completes.
 cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
                                const g6x_irec *d_irec, int ni, double eps2, void *part,
                                int *d_err, g6x_out *out, const int *jidx, unsigned *tcnt,
                                cudaStream_t s, const FusedPred *fp = nullptr,
-                               bool pdl = false);
+                               bool pdl = false, const ListArgs *lists = nullptr);
 // One small-block launch (cfg.ws; cfg.grid <= cfg.jtiles, ni <= cfg.itile):
 // the j-store update of fp.rec (if any), prediction, force and reduction
 // into out; part holds partial_slots(cfg) records, cnt counter_slots(cfg)

@@ -310,7 +310,7 @@ __device__ __forceinline__ float2 ds_sep2(float2 h, float2 l, float2 nh, float2 
 // tile and the tile that lowered it; when a segment ends, that one tile is
 // scanned again with the same arithmetic to find the first j that attains
 // the minimum (ties to the lower j-slot).  Lists (Sect. 4) use the same
-// minimum: the loop keeps it per chunk of 4 j-pairs, and only a chunk whose
+// minimum: the loop keeps it per chunk of j-pairs, and only a chunk whose
 // minimum is below h2 + eps2 is scanned again, from the staged tile, for
 // its members, so the pair loop is the same with and without lists.  With
 // TJ j-groups each group keeps its own ascending run of members, and the
@@ -333,8 +333,11 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
     // The split-j shapes (small m) also note which chunk of CHP j-pairs
     // lowered a tile's minimum, so the rescan at the end of a segment reads
     // one chunk of the winning tile, not the thread's whole share of it.
+    // Lists test each chunk's minimum against the radius: whole j-tiles per
+    // thread take chunks of 16 j-pairs (4 cost the loop 8 %).
     constexpr bool NNC = TJ > 1;
-    constexpr int CHP = PPT < 4 ? PPT : 4;
+    constexpr int CHW = NNC ? 4 : 16;
+    constexpr int CHP = PPT < CHW ? PPT : CHW;
     static_assert(PPT % CHP == 0, "whole chunks per tile");
     constexpr unsigned TILE_BYTES = JW * JT * sizeof(float);
     // FP: a stage holds one tile of the raw j-store arrays (RAW_* offsets),
@@ -755,6 +758,22 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
                 o.nnb = bj >= 0 ? a.jidx[bj] : -1;
                 o.nnr2 = bj >= 0 ? br : INF;
                 a.out[gi] = o;
+                if constexpr (LIST) {
+                    // the list partials in segment order (ascending j),
+                    // truncated at the list length; the count is the total
+                    long long pos = 0, total = 0;
+                    for (int q = 0; q < nseg; ++q) {
+                        const size_t slot = (size_t)(clo + q + t) * ITILE + il;
+                        const int cnt = __ldcg(&a.nbc[slot]);
+                        const int kept = min(cnt, a.nbseg);
+                        const int *src = a.nbl + slot * a.nbseg;
+                        for (int e = 0; e < kept && pos + e < a.maxnb; ++e)
+                            a.nbl_out[(size_t)gi * a.maxnb + pos + e] = a.jidx[__ldcg(&src[e])];
+                        pos += kept;
+                        total += cnt;
+                    }
+                    a.nblen_out[gi] = (int)min(total, (long long)INT_MAX);
+                }
             }
         }
     };
@@ -908,10 +927,8 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
             }
             __syncthreads();
         }
-        if constexpr (!LIST) {
-            if (a.fused)
-                tile_done(t);
-        }
+        if (a.fused)
+            tile_done(t);
     };
 
     // All pairs of the thread's share of one staged tile.  SELF: apply the
@@ -1348,6 +1365,52 @@ __global__ void __launch_bounds__(256) k_reduce_wide(const ReduceArgs a)
         if (lane == 0)
             a.out[i] = result_of(acc, a.jidx);
     }
+    if (!a.list)
+        return;
+    // Lists: the partials' entries in segment order (ascending j), 256
+    // partials per pass, each placed by a block-wide scan of the counts
+    // kept; truncated at the list length, the total count kept apart.
+    __shared__ int s_kept[8];
+    __shared__ long long s_cnt[8];
+    long long base = 0, total = 0;
+    for (long long c0 = clo; c0 <= chi; c0 += 256) {
+        const long long cc = c0 + tid;
+        const int cnt = cc <= chi ? a.nbc[(size_t)(cc + t) * a.itile + il] : 0;
+        const int kept = min(cnt, a.nbseg);
+        int incl = kept;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off)
+                incl += v;
+        }
+        long long ctot = cnt;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            ctot += __shfl_xor_sync(0xffffffffu, ctot, off);
+        __syncthreads();                    // the previous pass has read s_kept
+        if (lane == 31)
+            s_kept[warp] = incl;
+        if (lane == 0)
+            s_cnt[warp] = ctot;
+        __syncthreads();
+        int woff = 0, pass_kept = 0;
+        long long pass_cnt = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            woff += w < warp ? s_kept[w] : 0;
+            pass_kept += s_kept[w];
+            pass_cnt += s_cnt[w];
+        }
+        const long long pos0 = base + woff + incl - kept;
+        const int *src = a.nbl + ((size_t)(cc + t) * a.itile + il) * a.nbseg;
+        for (int e = 0; e < kept && pos0 + e < a.maxnb; ++e)
+            a.nbl_out[(size_t)i * a.maxnb + pos0 + e] = a.jidx[src[e]];
+        base += pass_kept;
+        total += pass_cnt;
+    }
+    if (tid == 0)
+        a.nblen_out[i] = (int)min(total, (long long)INT_MAX);
 }
 
 // K3 for a batch: one warp per (global i-tile, slot) with an active
@@ -1467,7 +1530,7 @@ const Variant kVariants[] = {
      256, ds_smem(256, 1)},
     // neighbour lists: the twins of variants 9, 4, 14, 15 and 16
     {{128, 1, 2, 1, G6X_PREC_DS}, k_force_ds<128, 1, 2, true, 4, 2>, 128, ds_smem(128, 2)},
-    {{16, 16, 1, 1, G6X_PREC_DS}, k_force_ds<16, 16, 1, true>, 256, ds_smem(256, 1)},
+    {{16, 16, 1, 1, G6X_PREC_DS}, k_force_ds<16, 16, 1, true, 2, 2>, 256, ds_smem(256, 1)},
     {{16, 16, 2, 1, G6X_PREC_DS}, k_force_ds<16, 16, 2, true, 2, 2>, 256, ds_smem(256, 2)},
     {{32, 8, 2, 1, G6X_PREC_DS}, k_force_ds<32, 8, 2, true, 2, 2>, 256, ds_smem(256, 2)},
     {{64, 4, 2, 1, G6X_PREC_DS}, k_force_ds<64, 4, 2, true, 2, 2>, 256, ds_smem(256, 2)},
@@ -1683,11 +1746,11 @@ int heuristic_variant(int prec, int ni, int nj_pad, int list, bool allow_ws, int
         {14, 32, 64, 2048},        // 16 x 16 threads, two i each
         {4, 16, 32, 0},            // 16 x 16 threads, one i each
     };
-    // their twins with neighbour lists (the wide shape only on longer work
-    // lines: at N = 131072 the 64 x 4 twin is 10 % faster for m = 16384 and
-    // even for m = 65536)
+    // their twins with neighbour lists (the wide shape only on long work
+    // lines: at N = 131072 the 64 x 4 twin is 6 % faster for m = 16384 and
+    // 4 % for m = 65536, where the plain wide shape is the faster one)
     static constexpr Shape list_shapes[] = {
-        {23, 256, INT_MAX, 65536},
+        {23, 256, INT_MAX, 1LL << 18},
         {27, 128, 2048, 4096},
         {26, 64, 128, 2048},
         {25, 32, 64, 2048},
@@ -1922,12 +1985,16 @@ cudaError_t launch_force(const ForceConfig &cfg, const Pred &p,
 cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
                                const g6x_irec *d_irec, int ni, double eps2, void *part,
                                int *d_err, g6x_out *out, const int *jidx, unsigned *tcnt,
-                               cudaStream_t s, const FusedPred *fp, bool pdl)
+                               cudaStream_t s, const FusedPred *fp, bool pdl,
+                               const ListArgs *lists)
 {
     if (cfg.work <= 0)
         return cudaSuccess;
-    if (cfg.list || cfg.prec != G6X_PREC_DS || cfg.ws || cfg.variant < 0
-        || cfg.variant >= kNumVariants)
+    if (cfg.prec != G6X_PREC_DS || cfg.ws || cfg.variant < 0 || cfg.variant >= kNumVariants)
+        return cudaErrorInvalidValue;
+    if (cfg.list
+        && (!lists || !lists->nbmax || lists->nbseg < 1 || lists->nbseg > lists->maxnb
+            || !lists->nbl_part || !lists->nbc_part || !lists->nbl_out || !lists->nblen_out))
         return cudaErrorInvalidValue;
     cudaError_t e = prepare_variant(cfg.variant);
     if (e != cudaSuccess)
@@ -1949,6 +2016,17 @@ cudaError_t launch_force_fused(const ForceConfig &cfg, const Pred &p,
     a.tcnt = tcnt;
     a.fused = 1;
     a.wait_ns = g_wait_ns;
+    if (cfg.list) {
+        a.maxnb = lists->maxnb;
+        a.nbseg = lists->nbseg;
+        a.nbmax = lists->nbmax;
+        a.nbl = lists->nbl_part;
+        a.nbc = lists->nbc_part;
+        a.nbl_out = lists->nbl_out;
+        a.nblen_out = lists->nblen_out;
+        if (cfg.tj > 1)
+            a.nbr = lists->nbl_part + partial_slots(cfg) * (size_t)lists->nbseg;
+    }
     if (!set_fused_pred(a, cfg, fp))
         return cudaErrorInvalidValue;
     const Variant &v = kVariants[cfg.variant];
@@ -1986,7 +2064,7 @@ cudaError_t launch_reduce(const ForceConfig &cfg, const void *part,
     // many partials per i-particle (small blocks spread over many CTAs):
     // one CTA per i-particle; otherwise one warp per i-particle
     const long long per_i = (long long)cfg.grid / cfg.n_itile + 1;
-    const bool wide = !cfg.list && per_i >= 64;
+    const bool wide = per_i >= 64;
     const int blocks = wide ? ni : (int)(((long long)ni * 32 + 255) / 256);
     if (cfg.prec == G6X_PREC_FP64) {
         if (wide) {

@@ -218,7 +218,7 @@ def test_launch_plan_heuristic_without_a_gpu(lib):
     assert g6gb.g6x_plan_launch(g6gb.G6X_PREC_FP64, big, 4096)["variant"] == 7
     assert g6gb.g6x_plan_launch(g6gb.G6X_PREC_FP64, big, 4096, True)["variant"] == 8
     # lists take the twins of the three-kernel path's shapes, the widest
-    # only from 65536 (i-tile, j-tile) units on
+    # only from 2^18 (i-tile, j-tile) units on
     for nj in (small, 131072, big):
         for ni in (16, 32, 64, 128, 256, 1000, 4096, 20000, nj):
             lp = g6gb.g6x_plan_launch(ds, nj, ni, True)
@@ -227,10 +227,11 @@ def test_launch_plan_heuristic_without_a_gpu(lib):
             if ni > 64:
                 wl, wp = shape(nj, ni, ds, True), shape(nj, ni)
                 assert wl == wp or (wp == (128, 1, 2) and wl == (64, 4, 2)), (nj, ni)
-                assert (wl == (128, 1, 2)) == (-(-ni // 256) * (nj // 256) >= 65536), (nj, ni)
+                assert (wl == (128, 1, 2)) == (-(-ni // 256) * (nj // 256) >= 1 << 18), (nj, ni)
     assert shape(big, 16, ds, True) == (16, 16, 1)
     assert shape(131072, 16384, ds, True) == (64, 4, 2)
-    assert shape(big, 4096, ds, True) == (128, 1, 2)
+    assert shape(big, 4096, ds, True) == (64, 4, 2)
+    assert shape(big, 65536, ds, True) == (128, 1, 2)
     assert g6gb.g6x_plan_launch(g6gb.G6X_PREC_DS_DSSUB, big, 16)["variant"] == 22
     assert g6gb.g6x_plan_launch(g6gb.G6X_PREC_DS_DSSUB, big, 4096)["variant"] == 21
     out = np.zeros(6, dtype=np.int32)

@@ -142,8 +142,13 @@ def test_neighbour_lists_every_list_shape(open_ctx, orc, m):
     # Every DS list shape, forced, against the oracle's lists: the split-j
     # shapes merge the ascending runs of their j-groups at the end of each
     # segment, so contents, order, truncation at the list length (the lowest
-    # j-slots) and the counts must match whatever the shape.
-    n, eps2, maxnb = 8192, 1e-8, 256
+    # j-slots) and the counts must match whatever the shape.  Each shape runs
+    # twice: with its own grid (many partials per i-tile: the separate
+    # reduction concatenates the lists) and with two CTAs per i-tile (the
+    # last CTA of each i-tile concatenates them inside the force launch).
+    # At m = 16 the separate reduction takes one CTA per i-particle (more
+    # than 64 partials each), at m = 300 one warp for most shapes.
+    n, eps2, maxnb = 32768, 1e-8, 256
     m_, x, v, pairs = ics.plummer_with_binaries(n, 6)
     idx = np.arange(n)
     cid = open_ctx(n, n)
@@ -159,11 +164,23 @@ def test_neighbour_lists_every_list_shape(open_ctx, orc, m):
               if g6.g6x_variant_info(k)["list"] == 1
               and g6.g6x_variant_info(k)["prec"] == g6.G6X_PREC_DS]
     assert len(shapes) >= 7
+    sweep(cid, n, x[act], v[act], act, eps2, 0.0, h2=h2)     # the prediction, once
     try:
-        for k in shapes:
-            g6.g6x_set_variant(cid, k, 0)
+        for k, fused in ((k, f) for k in shapes for f in (False, True)):
+            info = g6.g6x_variant_info(k)
+            n_itile = -(-m // (info["ti"] * info["ni_per"]))
+            g6.g6x_set_variant(cid, k, 2 * n_itile if fused else 0)
+            l0 = g6.g6x_launch_count(cid)
             acc, jerk, pot, nnb = sweep(cid, n, x[act], v[act], act, eps2, 0.0, h2=h2)
-            assert g6.g6x_last_config(cid)["variant"] == k
+            launches = g6.g6x_launch_count(cid) - l0
+            cfg = g6.g6x_last_config(cid)
+            assert cfg["variant"] == k
+            if fused:
+                assert cfg["grid"] == 2 * n_itile and launches == base - 1, (k, launches)
+            else:
+                base = launches
+                if m == 16:
+                    assert cfg["grid"] // n_itile + 1 >= 64      # the wide reduction
             rc = g6.g6_read_neighbour_list(cid)
             assert rc == (g6.G6_EOVERFLOW if nov else 0), k
             for q in range(act.size):
