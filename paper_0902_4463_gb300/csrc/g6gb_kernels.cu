@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(TI * TJ, MINB) k_force_ds(const ForceArgs a)
         if (!(nnr[k] < INF) || nnt[k] < 0)
             return -1;
         const float *T = a.pt + (size_t)nnt[k] * JW * JT;
-        constexpr int CH = CHP;                     // j-pairs per chunk
+        constexpr int CH = NNC ? CHP : 4;           // j-pairs loaded together
         const int kb = NNC ? nnc[k] * CH : 0, ke = NNC ? kb + CH : PPT;
         for (int kk0 = kb; kk0 < ke; kk0 += CH) {
             float key[2 * CH];
