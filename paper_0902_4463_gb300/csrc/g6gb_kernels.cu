@@ -1734,13 +1734,17 @@ int heuristic_variant(int prec, int ni, int nj_pad, int list, bool allow_ws, int
     // The widest i-tile the block size allows, narrowed while the work
     // line would hold too few (i-tile, j-tile) units for the SMs: wide
     // tiles need many j-tiles to keep every CTA busy, so small j-sets
-    // take narrower tiles at the same m.
+    // take narrower tiles at the same m.  (The 256-wide tile from 65536
+    // units on, measured with Plummer spheres: at N = 131072 the 128-wide
+    // split-j tile is 9 % faster for m = 8192 and 2 % for m = 32768, the
+    // wide one 4 % faster for m = 65536; at N = 32768, m = N the split-j
+    // tile is 16 % faster; at N = 2^20, m = 4096 the wide one by 1 %.)
     struct Shape {
         int v, itile, max_ni;
         long long min_units;
     };
     static constexpr Shape plain_shapes[] = {
-        {9, 256, INT_MAX, 16384},  // 128 threads, two i each, whole j-tiles, 4 CTAs per SM
+        {9, 256, INT_MAX, 65536},  // 128 threads, two i each, whole j-tiles, 4 CTAs per SM
         {16, 128, 2048, 4096},     // 64 x 4 threads, two i each
         {15, 64, 128, 2048},       // 32 x 8 threads, two i each
         {14, 32, 64, 2048},        // 16 x 16 threads, two i each

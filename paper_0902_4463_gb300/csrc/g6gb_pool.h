@@ -23,7 +23,9 @@ namespace g6 {
 // without a lock.  Workers wait for the next job by spinning on the counter
 // for a short while (a block step posts several jobs tens of microseconds
 // apart), then by yielding, then sleep on a condition variable; the caller
-// wakes sleepers only when there are any.
+// wakes sleepers only when there are any.  A job of a few pieces posted
+// while workers sleep runs on the caller alone: the job is complete only
+// when every worker has seen it, so it would wait for all of them to wake.
 class HostPool {
 public:
     explicit HostPool(int threads)
@@ -45,7 +47,8 @@ public:
     int size() const { return (int)th_.size() + 1; }
     void run(int n, const std::function<void(int)> &f)
     {
-        if (th_.empty() || n <= 1) {
+        if (th_.empty() || n <= 1
+            || (n < WAKE_MIN && sleepers_.load(std::memory_order_relaxed) > 0)) {
             for (int i = 0; i < n; ++i)
                 f(i);
             return;
@@ -71,6 +74,7 @@ public:
 private:
     static constexpr int SPIN_TIGHT = 20000;   // polls before yielding (tens of us)
     static constexpr int SPIN_YIELD = 2000;    // yields before sleeping
+    static constexpr int WAKE_MIN = 8;         // pieces worth waking sleepers for
 
     // claim indices `grab` at a time until none are left
     void take(const std::function<void(int)> &f, int n, int grab)

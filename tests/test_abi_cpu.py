@@ -209,7 +209,8 @@ def test_launch_plan_heuristic_without_a_gpu(lib):
     assert shape(small, 256) == (16, 16, 1)
     assert shape(small, 1024) == (32, 8, 2)
     assert shape(small, 4096) == (64, 4, 2)
-    assert shape(small, small) == (128, 1, 2)
+    assert shape(small, small) == (64, 4, 2)        # 16384 units: below the wide tile's 65536
+    assert shape(131072, 16384) == (64, 4, 2) and shape(131072, 65536) == (128, 1, 2)
     # a smaller j-set never gets a wider i-tile at the same block size
     for ni in (16, 64, 200, 1000, 3000, 20000):
         widths = [np.prod(shape(nj, ni)[::2]) for nj in (4096, 32768, 131072, 1 << 20)]
