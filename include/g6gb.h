@@ -141,15 +141,16 @@ int g6calc_lasthalf2(int clusterid, int nj, int ni, const int index[],
                      const double h2[], double acc[][3], double jerk[][3],
                      double pot[], int nnbindex[]);
 
-/* Copy the neighbour lists of the last calculation to the host (Sect. 4):
- * for each i the j-particles with unsoftened |r|^2 < h2[i], excluding
- * itself, in ascending j-slot order, at most the context's list length of
- * them (G6_MAXNB unless g6x_set_max_neighbours chose another).  Synchronous.
- * The force kernel keeps each CTA's part of a list in a slot with room for a
- * few entries, grown as lists grow: when a part had more entries than its
- * slot held, this call computes that calculation's lists once more with
- * larger slots (the j-memory must not have changed since: G6_EBUSY), so the
- * lists returned are always complete.  Returns 0, G6_EOVERFLOW (1) if some
+/* Make the neighbour lists of the last calculation readable on the host
+ * (Sect. 4): for each i the j-particles with unsoftened |r|^2 < h2[i],
+ * excluding itself, in ascending j-slot order, at most the context's list
+ * length of them (G6_MAXNB unless g6x_set_max_neighbours chose another).
+ * Synchronous.  The reduction writes the lists straight into pinned host
+ * memory, so no copy is made here.  The force kernel keeps each CTA's part
+ * of a list in a slot with room for a few entries, grown as lists grow: when
+ * a part had more entries than its slot held, this call computes that
+ * calculation's lists once more with larger slots (the j-memory must not
+ * have changed since: G6_EBUSY), so the lists returned are always complete.  Returns 0, G6_EOVERFLOW (1) if some
  * list was longer than the list length (it is truncated), or a negative
  * error.  Lists exist only if firsthalf got h2 != NULL (or g6x_calc_dev
  * nl != 0, whose d_irec must then stay unchanged until this call). */
@@ -167,8 +168,8 @@ int g6_get_neighbour_list(int clusterid, int ipipe, int maxlength, int *nblen,
 /* Neighbour-list length of the context, 1 .. G6X_MAXNB_LIMIT entries per
  * i-particle (default G6_MAXNB = 256, the paper's choice, Sect. 4; the paper
  * fixes it at compile time, here it is a setting).  Longer lists cost more
- * host memory and read-back; the force kernel's cost depends on the number
- * of entries found, not on this length.  Applies to later calculations;
+ * pinned host memory (ni_max x length x 4 B); the force kernel's cost
+ * depends on the number of entries found, not on this length.  Applies to later calculations;
  * lists already computed are dropped.  Returns 0 or G6_EINVAL. */
 #define G6X_MAXNB_LIMIT 4096
 int g6x_set_max_neighbours(int clusterid, int maxnb);
