@@ -168,7 +168,7 @@ int g6_get_neighbour_list(int clusterid, int ipipe, int maxlength, int *nblen,
 /* Neighbour-list length of the context, 1 .. G6X_MAXNB_LIMIT entries per
  * i-particle (default G6_MAXNB = 256, the paper's choice, Sect. 4; the paper
  * fixes it at compile time, here it is a setting).  Longer lists cost more
- * pinned host memory (ni_max x length x 4 B); the force kernel's cost
+ * pinned host memory (block size x length x 4 B); the force kernel's cost
  * depends on the number of entries found, not on this length.  Applies to later calculations;
  * lists already computed are dropped.  Returns 0 or G6_EINVAL. */
 #define G6X_MAXNB_LIMIT 4096
