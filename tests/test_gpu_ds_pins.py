@@ -28,7 +28,7 @@ import pytest
 
 from paper_0902_4463_gb300 import g6gb as g6
 from paper_0902_4463_gb300 import ics
-from tests.ds_restate import ds_split, restated_prediction, rn32
+from tests.ds_restate import ds_split, fma32, restated_prediction, rn32
 from tests.gpu_helpers import load_j
 
 pytestmark = pytest.mark.gpu
@@ -100,3 +100,58 @@ def test_eq3_separation_bound_from_predicted_words(ctx, orc):
     # plain single precision fails the tight bound for the close pairs
     dx_sp = (rn32(xp) - rn32(xi)).astype(np.float64)
     assert np.any(np.abs(dx_sp - dx)[:32] > bound[:32])
+
+
+def test_list_membership_is_bit_exact(ctx):
+    # Sect. 4 lists decided in the kernel's own precision: the key is the
+    # single-precision softened r^2, fma(dz, dz, fma(dy, dy, fma(dx, dx,
+    # eps2))), of the Eq. 3 separations between the predicted DS words of j
+    # and the DS pair of x_i, and the radius is h2 + eps2 rounded to float
+    # once.  Every DS list shape must return exactly the j with key < radius
+    # (self excluded), in ascending j-slot order, the lowest j-slots where a
+    # list is longer than its length, and the full count.  Each radius is
+    # the squared FP64 distance of the i-particle's k-th nearest j, so one
+    # member sits on the boundary of every list.
+    n, t_blk, eps2, m, maxnb = 8192, 0.625, 1e-8, 256, 256
+    st = ics.taylor_state(n, 73, t_blk)
+    load_j(ctx, st["x0"], st["v0"], st["m"], st["a0"], st["j0"], st["tj"])
+    act = np.sort(ics.permutation(n, 73)[:m])
+    rng = np.random.default_rng(73)
+    xi = st["x0"][act] + rng.normal(scale=1e-3, size=(m, 3))
+    vi = st["v0"][act]
+    # the restated words and decision
+    jh, jl, _ = restated_prediction(st, t_blk)
+    xj = jh.astype(np.float64) + jl.astype(np.float64)
+    r64 = [np.sum((xj - xi[q]) ** 2, axis=1) for q in range(m)]
+    kth = rng.integers(0, 400, size=m)
+    h2 = np.array([np.sort(r64[q])[kth[q]] for q in range(m)])
+    ih, il = ds_split(xi)
+    e2 = rn32(eps2)
+    radius = rn32(h2 + e2.astype(np.float64))
+    want, flips = [], 0
+    for q in range(m):
+        d = [(jh[:, c] + (-ih[q, c])) + (jl[:, c] + (-il[q, c])) for c in range(3)]
+        key = fma32(d[2], d[2], fma32(d[1], d[1], fma32(d[0], d[0], np.full(n, e2))))
+        key[act[q]] = np.inf
+        r64[q][act[q]] = np.inf
+        want.append(np.nonzero(key < radius[q])[0])
+        flips += np.count_nonzero((key < radius[q]) != (r64[q] < h2[q]))
+    lens = np.array([w.size for w in want])
+    assert lens.min() == 0 and np.count_nonzero(lens > maxnb) > 10 and np.median(lens) > 100
+    assert flips > 10          # decisions that FP64 distances would take the other way
+    shapes = [k for k in range(g6.g6x_variant_count())
+              if g6.g6x_variant_info(k)["list"] == 1
+              and g6.g6x_variant_info(k)["prec"] == g6.G6X_PREC_DS]
+    try:
+        for k in [-1] + shapes:
+            g6.g6x_set_variant(ctx, k, 0)
+            g6.g6_set_ti(ctx, t_blk)
+            g6.g6calc_firsthalf(ctx, n, m, act, xi, vi, eps2, h2)
+            g6.g6calc_lasthalf2(ctx, n, m, eps2)
+            assert g6.g6_read_neighbour_list(ctx) == g6.G6_EOVERFLOW
+            for q in range(m):
+                rc, ln, ids = g6.g6_get_neighbour_list(ctx, q)
+                assert ln == lens[q], (k, q, ln, lens[q])
+                assert np.array_equal(ids, want[q][:maxnb]), (k, q)
+    finally:
+        g6.g6x_set_variant(ctx, -1, 0)
