@@ -111,7 +111,10 @@ def test_list_membership_is_bit_exact(ctx):
     # (self excluded), in ascending j-slot order, the lowest j-slots where a
     # list is longer than its length, and the full count.  Each radius is
     # the squared FP64 distance of the i-particle's k-th nearest j, so one
-    # member sits on the boundary of every list.
+    # member sits on the boundary of every list.  The nearest neighbour comes
+    # from the same key: the j returned must attain the smallest key with
+    # eps2 taken off again in float (partials compare that value, so among j
+    # whose values tie any may be returned).
     n, t_blk, eps2, m, maxnb = 8192, 0.625, 1e-8, 256, 256
     st = ics.taylor_state(n, 73, t_blk)
     load_j(ctx, st["x0"], st["v0"], st["m"], st["a0"], st["j0"], st["tj"])
@@ -128,13 +131,14 @@ def test_list_membership_is_bit_exact(ctx):
     ih, il = ds_split(xi)
     e2 = rn32(eps2)
     radius = rn32(h2 + e2.astype(np.float64))
-    want, flips = [], 0
+    want, flips, unsoft = [], 0, []
     for q in range(m):
         d = [(jh[:, c] + (-ih[q, c])) + (jl[:, c] + (-il[q, c])) for c in range(3)]
         key = fma32(d[2], d[2], fma32(d[1], d[1], fma32(d[0], d[0], np.full(n, e2))))
         key[act[q]] = np.inf
         r64[q][act[q]] = np.inf
         want.append(np.nonzero(key < radius[q])[0])
+        unsoft.append(np.maximum(key - e2, np.float32(0)))
         flips += np.count_nonzero((key < radius[q]) != (r64[q] < h2[q]))
     lens = np.array([w.size for w in want])
     assert lens.min() == 0 and np.count_nonzero(lens > maxnb) > 10 and np.median(lens) > 100
@@ -147,7 +151,9 @@ def test_list_membership_is_bit_exact(ctx):
             g6.g6x_set_variant(ctx, k, 0)
             g6.g6_set_ti(ctx, t_blk)
             g6.g6calc_firsthalf(ctx, n, m, act, xi, vi, eps2, h2)
-            g6.g6calc_lasthalf2(ctx, n, m, eps2)
+            nnb = g6.g6calc_lasthalf2(ctx, n, m, eps2)[3]
+            for q in range(m):
+                assert unsoft[q][nnb[q]] == unsoft[q].min(), (k, q)
             assert g6.g6_read_neighbour_list(ctx) == g6.G6_EOVERFLOW
             for q in range(m):
                 rc, ln, ids = g6.g6_get_neighbour_list(ctx, q)
