@@ -2,7 +2,8 @@
 // every run is processed exactly once, for pool sizes 1 .. 16 and for long
 // series of back-to-back runs; nested and concurrent parallel_run calls fall
 // back to serial loops without deadlock; a pool whose workers have gone to
-// sleep on its condition variable still runs jobs and joins on destruction.
+// sleep on its condition variable still runs jobs (small ones on the caller
+// alone) and joins on destruction.
 // Exit status 0 on success; the first failure is printed.
 #include "g6gb_pool.h"
 
@@ -51,6 +52,20 @@ int main()
         once_each(p, 64);
         std::this_thread::sleep_for(std::chrono::milliseconds(100));
         once_each(p, 64);
+        // a job of a few pieces posted while they sleep runs on the caller
+        // alone, each index once; a larger one wakes them and still runs
+        // every index once, and the pool joins afterwards
+        std::this_thread::sleep_for(std::chrono::milliseconds(300));
+        const std::thread::id me = std::this_thread::get_id();
+        std::atomic<int> others{0};
+        p.run(3, [&](int) {
+            if (std::this_thread::get_id() != me)
+                others.fetch_add(1);
+        });
+        CHECK(others.load() == 0);
+        once_each(p, 3);
+        std::this_thread::sleep_for(std::chrono::milliseconds(100));
+        once_each(p, 1000);
     }
     {
         // nested use of the process-wide pool runs serially inside
